@@ -1,0 +1,204 @@
+"""FP64 CPU oracle for the FDBB Euler building blocks (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The
+product library (``paper_1809_09851_gb300``) never imports it, and it imports
+nothing from the product library.
+
+All fields are lists of 1-D float64 numpy arrays, one array per component
+plane, in the paper's component order (section 2.2): conservative
+U = (rho, m_1..m_D, rhoE), primitive V = (rho, v_1..v_D, p).
+
+Every function returns ``out`` or, with ``scale=True``, ``(out, S)`` where S
+holds, per output plane, the first-order running-error scale of the oracle's
+formula (|computed - exact| <~ 2^-53 * S); parity tolerances are ``tol * S``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import build as _build, library_path
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build()
+        lib = ctypes.CDLL(path)
+        i64, dbl, vp = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+        ci = ctypes.c_int
+        sig = {
+            "oracle_v_mag2": [ci, i64, vp, vp, vp],
+            "oracle_prim_from_cons": [ci, dbl, i64, vp, vp, vp],
+            "oracle_cons_from_prim": [ci, dbl, i64, vp, vp, vp],
+            "oracle_eos": [ci, dbl, i64, vp, vp, vp],
+            "oracle_riemann_inv": [ci, ci, dbl, i64, vp, vp, vp],
+            "oracle_flux": [ci, ci, dbl, i64, vp, vp, vp],
+            "oracle_flux_jac": [ci, ci, dbl, i64, vp, vp, vp],
+            "oracle_char_transform": [ci, ci, dbl, ci, i64, vp, vp, vp, vp],
+            "oracle_flux_vjp": [ci, ci, dbl, i64, vp, vp, vp, vp],
+            "oracle_euler_fused": [ci, ci, dbl, i64, vp, vp, vp, vp],
+            "oracle_eig": [ci, ci, dbl, i64, vp, vp, vp, vp],
+            "oracle_rusanov_step": [ci, dbl, dbl, vp, vp],
+            "oracle_rusanov_run": [ci, dbl, dbl, ci, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ci
+        lib.oracle_rusanov_dt.argtypes = [ci, dbl, dbl, vp]
+        lib.oracle_rusanov_dt.restype = dbl
+        _lib = lib
+    return _lib
+
+
+def _planes(arrs, n=None):
+    """Validate a list of planes and return (ctypes pointer array, arrays, n)."""
+    out = []
+    for a in arrs:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.ndim != 1:
+            raise ValueError("planes must be 1-D")
+        if n is None:
+            n = a.shape[0]
+        elif a.shape[0] != n:
+            raise ValueError("planes differ in length")
+        out.append(a)
+    ptrs = (ctypes.c_void_p * len(out))(*[a.ctypes.data for a in out])
+    return ptrs, out, n
+
+
+def _new(k, n):
+    arrs = [np.empty(n, dtype=np.float64) for _ in range(k)]
+    ptrs = (ctypes.c_void_p * k)(*[a.ctypes.data for a in arrs])
+    return ptrs, arrs
+
+
+def _call(fn, nout, n, args, scale):
+    po, out = _new(nout, n)
+    ps, sc = _new(nout, n) if scale else (None, None)
+    rc = fn(*args, po, ps)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments ({fn.__name__})")
+    return (out, sc) if scale else out
+
+
+def nv(D: int) -> int:
+    return D + 2
+
+
+def v_mag2(D, U, scale=False):
+    """|v|^2 = sum m_i^2 / rho^2 (paper section 3, Eq. (2))."""
+    pu, Uk, n = _planes(U[: D + 1])
+    return _call(_load().oracle_v_mag2, 1, n, (D, n, pu), scale)
+
+
+def prim_from_cons(D, gamma, U, scale=False):
+    pu, Uk, n = _planes(U)
+    return _call(_load().oracle_prim_from_cons, nv(D), n, (D, gamma, n, pu), scale)
+
+
+def cons_from_prim(D, gamma, V, scale=False):
+    pv, Vk, n = _planes(V)
+    return _call(_load().oracle_cons_from_prim, nv(D), n, (D, gamma, n, pv), scale)
+
+
+def eos(D, gamma, U, scale=False):
+    """[p, c]."""
+    pu, Uk, n = _planes(U)
+    return _call(_load().oracle_eos, 2, n, (D, gamma, n, pu), scale)
+
+
+def riemann_inv(D, d, gamma, U, scale=False):
+    """[w-, w+, s] along direction d."""
+    pu, Uk, n = _planes(U)
+    return _call(_load().oracle_riemann_inv, 3, n, (D, d, gamma, n, pu), scale)
+
+
+def flux(D, d, gamma, U, scale=False):
+    """F_d (nv planes) or, for d == -1, all directions (D*nv planes)."""
+    pu, Uk, n = _planes(U)
+    k = nv(D) * (D if d < 0 else 1)
+    return _call(_load().oracle_flux, k, n, (D, d, gamma, n, pu), scale)
+
+
+def flux_jac(D, d, gamma, U, scale=False):
+    """A_d row-major, nv*nv planes."""
+    pu, Uk, n = _planes(U)
+    return _call(_load().oracle_flux_jac, nv(D) ** 2, n, (D, d, gamma, n, pu), scale)
+
+
+def char_transform(D, d, gamma, U, W, inverse=False, scale=False):
+    """Forward L_d(U) W or inverse R_d(U) W."""
+    pu, Uk, n = _planes(U)
+    pw, Wk, _ = _planes(W, n)
+    return _call(_load().oracle_char_transform, nv(D), n,
+                 (D, d, gamma, int(bool(inverse)), n, pu, pw), scale)
+
+
+def flux_vjp(D, d, gamma, U, G, scale=False):
+    """A_d(U)^T G."""
+    pu, Uk, n = _planes(U)
+    pg, Gk, _ = _planes(G, n)
+    return _call(_load().oracle_flux_vjp, nv(D), n, (D, d, gamma, n, pu, pg), scale)
+
+
+def euler_fused(D, dj, gamma, U, W, scale=False):
+    """[F_0..F_{D-1} (D*nv), A_dj (nv*nv), L_dj W (nv)]."""
+    pu, Uk, n = _planes(U)
+    pw, Wk, _ = _planes(W, n)
+    k = D * nv(D) + nv(D) ** 2 + nv(D)
+    return _call(_load().oracle_euler_fused, k, n, (D, dj, gamma, n, pu, pw), scale)
+
+
+def eig(D, d, gamma, U):
+    """(R, L, lam): R columns are right eigenvectors, L = R^-1, as plane lists."""
+    pu, Uk, n = _planes(U)
+    k = nv(D)
+    pr, R = _new(k * k, n)
+    pl, L = _new(k * k, n)
+    pm, lam = _new(k, n)
+    if _load().oracle_eig(D, d, gamma, n, pu, pr, pl, pm) != 0:
+        raise ValueError("oracle rejected the arguments (oracle_eig)")
+    return R, L, lam
+
+
+def rusanov_dt(n, gamma, cfl, U):
+    pu, Uk, N = _planes(U)
+    assert N == n ** 3
+    return _load().oracle_rusanov_dt(n, gamma, cfl, pu)
+
+
+def rusanov_step(n, gamma, dt, U):
+    pu, Uk, N = _planes(U)
+    assert N == n ** 3
+    po, out = _new(5, N)
+    if _load().oracle_rusanov_step(n, gamma, dt, pu, po) != 0:
+        raise ValueError("oracle rejected the arguments (oracle_rusanov_step)")
+    return out
+
+
+def rusanov_run(n, gamma, cfl, steps, U):
+    """Run `steps` Rusanov steps; returns (U_final, dts)."""
+    _, Uk, N = _planes(U)
+    Uk = [a.copy() for a in Uk]
+    pu = (ctypes.c_void_p * 5)(*[a.ctypes.data for a in Uk])
+    pw, work = _new(5, N)
+    dts = np.empty(max(steps, 1), dtype=np.float64)
+    rc = _load().oracle_rusanov_run(n, gamma, cfl, steps, pu, pw,
+                                    ctypes.c_void_p(dts.ctypes.data))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments (oracle_rusanov_run)")
+    return Uk, dts[:steps]
+
+
+__all__ = [
+    "v_mag2", "prim_from_cons", "cons_from_prim", "eos", "riemann_inv", "flux",
+    "flux_jac", "char_transform", "flux_vjp", "euler_fused", "eig", "rusanov_dt",
+    "rusanov_step", "rusanov_run", "library_path", "nv",
+]
