@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""Benchmark: fused 3D Euler building blocks on GB300.
+
+One step = one fdbb_euler_fused launch over N = 2^26 points of a 3D field:
+reads U (5 planes) and W (5 planes), writes F_x, F_y, F_z (15 planes), the
+x-Jacobian A_x (25 planes) and L_x(U) W (5 planes) -- 440 B/point in FP64.
+The headline value is FP64 Gpoints/s; FP32 and BF16 storage are measured on
+the same field and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fdbb|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank evaluates its own
+N-point field (weak scaling, no data-path collective); the time is the max
+over ranks and the value is the points of all ranks / that time.
+
+--impl reference times the FP64 CPU oracle on the host cores (rank 0 only)
+on a bounded sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoints/s & % HBM peak, fused 3D flux+Jacobian, FP64 vs mixed at stated err; p99"
+UNIT = "Gpoints/s"
+N_POINTS = 1 << 26
+GAMMA = 1.4
+D = 3
+NV = 5
+PLANES_IN, PLANES_OUT = 2 * NV, D * NV + NV * NV + NV  # 10 read, 45 written
+BYTES = {"f64": 8, "f32": 4, "bf16": 2}
+L2_BYTES = 129 * 2 ** 20
+
+# DRAM traffic per point of the fused FP64 kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum per launch / points), valid only
+# for the kernel sources whose hash is recorded beside it.
+NCU_TRAFFIC = {"source_hash": None, "bytes_per_point": None}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1809_09851_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(os.path.basename(p).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            js = json.load(fh)
+        return float(js["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Each rank evaluates its own independent field."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def make_fields(n, seed, dev):
+    import torch
+    from paper_1809_09851_gb300 import blocks, synth
+    V = [torch.from_numpy(v).to(dev) for v in synth.euler3d(n, seed=seed)]
+    U = blocks.cons_from_prim(V, GAMMA)  # conservative state built on the GPU
+    del V
+    W = [torch.from_numpy(w).to(dev) for w in synth.char_weights(n, NV, seed=seed + 1)]
+    return U, W
+
+
+def time_fused(U, W, out, steps, warmup, stream):
+    """Per-launch CUDA-event durations (ms) and the wall of the whole timed loop."""
+    import torch
+    from paper_1809_09851_gb300 import blocks
+    F, A, Y = out
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            blocks.euler_fused(U, W, 0, GAMMA, out=(F, A, Y))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for i in range(steps):
+            blocks.euler_fused(U, W, 0, GAMMA, out=(F, A, Y))
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    total = ev[0].elapsed_time(ev[steps])
+    return per, total
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    k = max(0, min(len(xs) - 1, int(math.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[k]
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1809_09851_gb300 import blocks, build
+    build.build()
+    n = args.n
+    seed = shard_seed(1809, rank)
+    stream = torch.cuda.Stream(dev)
+    hbm_peak, peak_kind = measured_peaks()
+
+    U64, W64 = make_fields(n, seed, dev)
+    alloc = lambda k, dt: [torch.empty(n, dtype=dt, device=dev) for _ in range(k)]
+    out64 = (alloc(D * NV, torch.float64), alloc(NV * NV, torch.float64), alloc(NV, torch.float64))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- headline: FP64 storage and arithmetic --------------------------------
+    barrier()
+    with ClockSampler(local) as clk:
+        per64, total64 = time_fused(U64, W64, out64, args.steps, args.warmup, stream)
+    barrier()
+    clocks = clk.summary()
+    t_max = max_over_ranks(total64 / 1e3, world, dev)
+    value = world * n * args.steps / t_max / 1e9
+    avg64 = sum(per64) / len(per64) / 1e3
+    bytes64 = (PLANES_IN + PLANES_OUT) * BYTES["f64"] * n
+    achieved = bytes64 / avg64 / 1e9
+    traffic = None
+    if NCU_TRAFFIC["source_hash"] == kernel_source_hash() and NCU_TRAFFIC["bytes_per_point"]:
+        traffic = NCU_TRAFFIC["bytes_per_point"] * n
+
+    # ---- FP32 and BF16 storage (float arithmetic, compensated recovery) -------
+    extra = {}
+    for tag, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        U = [u.to(dt) for u in U64]
+        W = [w.to(dt) for w in W64]
+        out = (alloc(D * NV, dt), alloc(NV * NV, dt), alloc(NV, dt))
+        barrier()
+        per, total = time_fused(U, W, out, args.steps, args.warmup, stream)
+        barrier()
+        t = max_over_ranks(total / 1e3, world, dev)
+        avg = sum(per) / len(per) / 1e3
+        b = (PLANES_IN + PLANES_OUT) * BYTES[tag] * n
+        extra[tag] = {"value": round(world * n * args.steps / t / 1e9, 3), "unit": UNIT,
+                      "ms_per_step": round(t * 1e3 / args.steps, 4),
+                      "p50_ms": round(pct(per, 50), 4), "p99_ms": round(pct(per, 99), 4),
+                      "hbm_gbs": round(b / avg / 1e9, 1), "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3),
+                      "bytes_per_point": (PLANES_IN + PLANES_OUT) * BYTES[tag]}
+        del U, W, out
+        torch.cuda.empty_cache()
+
+    # ---- end to end through host buffers ---------------------------------------
+    e2e = run_e2e(args, U64, W64, out64, stream, dev, world)
+
+    result = None
+    if rank == 0:
+        cpu = cpu_baseline(args) if world == 1 and not args.no_cpu else None
+        result = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_max * 1e3 / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"euler3d_fused N=2^{int(math.log2(n))} per GPU, f64 SoA, gamma=1.4, "
+                                   "outputs F_x,F_y,F_z + A_x + L_x W",
+                       "points_per_gpu": n, "parallelism": f"dp{world} (independent fields per GPU)",
+                       "l2": f"inputs+outputs {bytes64 / 1e9:.1f} GB >> L2 {L2_BYTES / 2**20:.0f} MiB: no flush needed"},
+            "p50_ms": round(pct(per64, 50), 4), "p99_ms": round(pct(per64, 99), 4),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                         "unit": "GB/s", "frac": round(achieved / hbm_peak, 3), "traffic": traffic,
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_point": (PLANES_IN + PLANES_OUT) * 8},
+            "mixed": extra,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def run_e2e(args, U, W, out, stream, dev, world):
+    """Same metric through the public API with pinned host buffers: every step
+    copies U and W host->device, runs the fused pass and copies all 45 output
+    planes device->host."""
+    import torch
+    from paper_1809_09851_gb300 import blocks
+    n = U[0].shape[0]
+    steps = max(1, min(args.e2e_steps, args.steps))
+    hU = [u.cpu().pin_memory() for u in U]
+    hW = [w.cpu().pin_memory() for w in W]
+    F, A, Y = out
+    outs = [*F, *A, *Y]
+    hO = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in outs]
+    h2d = sum(t.numel() * t.element_size() for t in hU + hW)
+    d2h = sum(t.numel() * t.element_size() for t in hO)
+
+    def step():
+        for d, h in zip(U + W, hU + hW):
+            d.copy_(h, non_blocking=True)
+        blocks.euler_fused(U, W, 0, GAMMA, out=(F, A, Y))
+        for h, d in zip(hO, outs):
+            h.copy_(d, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+    del hU, hW, hO
+    return {"value": round(world * n * steps / t / 1e9, 4), "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": round(t * 1e3 / steps, 3)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(n_sample, seed=1809):
+    import oracle
+    from paper_1809_09851_gb300 import synth
+    U = oracle.cons_from_prim(D, GAMMA, synth.euler3d(n_sample, seed=seed))
+    W = synth.char_weights(n_sample, NV, seed=seed + 1)
+    return U, W
+
+
+def cpu_baseline(args):
+    """FP64 oracle, single thread, on the first `cpu_sample` points of the same
+    field, repeated for about `cpu_seconds` of CPU time."""
+    import oracle
+    ns = args.cpu_sample
+    U, W = oracle_sample(ns)
+    oracle.euler_fused(D, 0, GAMMA, U, W)  # warm (load, page in)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.euler_fused(D, 0, GAMMA, U, W)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= args.cpu_seconds:
+            break
+    return {"value": round(ns * reps / el / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {ns} points of the seeded 3D field, fused pass repeated {reps}x "
+                      f"({el:.1f} s, 1 thread, g++ -O2 -ffp-contract=off)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle  # noqa: F401
+    ns = args.ref_sample
+    U, W = oracle_sample(ns)
+    import oracle as orc
+    for _ in range(args.warmup):
+        orc.euler_fused(D, 0, GAMMA, U, W)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.euler_fused(D, 0, GAMMA, U, W)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = ns * args.steps / total / 1e9
+    res = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"euler3d_fused N=2^{int(math.log2(args.n))} per GPU, f64 SoA, gamma=1.4, "
+                               "outputs F_x,F_y,F_z + A_x + L_x W",
+                   "points_per_gpu": args.n, "parallelism": "oracle on host cores"},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: first {ns} points of the seeded 3D field "
+                                   f"(1 thread, g++ -O2 -ffp-contract=off)"},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(res), flush=True)
+    return res
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["fdbb", "reference"], default="fdbb")
+    ap.add_argument("--n", type=int, default=N_POINTS, help="points per GPU (default 2^26)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 18)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-sample", type=int, default=1 << 16)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        print("bench: warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * fdbb.h -- C ABI of the GB300 (sm_103a) Euler building-block library.
+ *
+ * The library evaluates the compressible-Euler "building blocks" of FDBB
+ * (M. Moeller, A. Jaeschke, "FDBB: Fluid Dynamics Building Blocks") point by
+ * point over structure-of-arrays fields resident in GPU memory.  Every entry
+ * point launches one fused CUDA kernel: it reads each input plane once, keeps
+ * all intermediate values in registers and writes each output plane once.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - dim D in {1,2,3}; nv = D + 2 components per point.
+ *  - Planes.  A field is an array of nv "planes"; plane k holds component k
+ *    of all n points contiguously.  Callers pass a HOST array of DEVICE plane
+ *    pointers.  Component order (paper, section 2.2, Figs. 7 and 9):
+ *      conservative U = (rho, m_1..m_D, rhoE),  m = rho v,
+ *      primitive    V = (rho, v_1..v_D, p).
+ *    Flux Jacobians are nv*nv planes in row-major block order A[r*nv + c]
+ *    (the default block storage order, paper section 2.1, "Block
+ *    Expressions").
+ *  - Storage type t applies to every plane of a call.  FDBB_F64 computes in
+ *    IEEE double.  FDBB_F32 / FDBB_F16 / FDBB_BF16 compute in float and
+ *    recover the internal energy rhoE - |m|^2/(2 rho) with compensated
+ *    (error-free-transform) float arithmetic, so p stays accurate near vacuum
+ *    and at high Mach; outputs are rounded to nearest-even into t.
+ *  - gamma is the ratio of specific heats c_p / c_v (1.4 in the paper,
+ *    section 2.2); derived constants (gamma - 1, 3 - gamma, 2/(gamma - 1))
+ *    are formed on the host in double and then rounded once to the compute
+ *    type.
+ *  - Every plane pointer must be 16-byte aligned (the kernels use 128-bit
+ *    loads and stores); n may be any value >= 0 (a ragged tail is handled).
+ *  - Ownership: the caller owns all memory.  Entry points never allocate,
+ *    free or synchronise; the kernel is enqueued on `stream` (NULL = the
+ *    legacy default stream) and the call returns immediately.
+ *  - Aliasing: an output plane may be the same pointer as an input plane of
+ *    the same point index (in-place update, e.g. V written over U); any other
+ *    overlap is undefined.
+ *  - A NULL output plane pointer means "do not compute / write this output".
+ *    Input plane pointers must not be NULL.
+ *  - Errors: arguments are checked before anything is enqueued; on an
+ *    argument error nothing is written and the corresponding status is
+ *    returned.  A failed launch returns FDBB_ERR_CUDA (the CUDA error is
+ *    consumed with cudaGetLastError).  n == 0 returns FDBB_OK without a
+ *    launch.
+ *  - Non-physical states (rho <= 0 or p < 0) are not clamped: the square
+ *    root of a negative number gives NaN, which propagates.
+ */
+#ifndef FDBB_H
+#define FDBB_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FDBB_API __attribute__((visibility("default")))
+#else
+#define FDBB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the CUDA runtime's stream handle). */
+typedef struct CUstream_st *fdbb_stream_t;
+
+typedef enum {
+  FDBB_OK = 0,
+  FDBB_ERR_ARG = 1,     /* dim not in {1,2,3}, dir out of range, n < 0, gamma <= 1 */
+  FDBB_ERR_NULLPTR = 2, /* a required plane array or input plane is NULL         */
+  FDBB_ERR_ALIGN = 3,   /* a plane pointer is not 16-byte aligned                */
+  FDBB_ERR_DTYPE = 4,   /* unknown storage type                                  */
+  FDBB_ERR_CUDA = 5,    /* the kernel launch failed                              */
+  FDBB_ERR_TIMEOUT = 6, /* a bounded host wait on the device ran out             */
+  FDBB_ERR_NOMEM = 7    /* a caller-supplied buffer or budget is too small       */
+} fdbb_status;
+
+typedef enum { FDBB_F64 = 0, FDBB_F32 = 1, FDBB_F16 = 2, FDBB_BF16 = 3 } fdbb_dtype;
+
+/* Human-readable name of a status code (static string, never NULL). */
+FDBB_API const char *fdbb_status_string(fdbb_status status);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+FDBB_API int fdbb_version(void);
+
+/*
+ * |v|^2 = (m_1^2 + .. + m_D^2) / rho^2, the kinetic-energy sub-expression
+ * used as micro-benchmark in the paper (section 3, Eq. (2)).
+ * U: the first D+1 planes of a conservative field (rho, m_1..m_D); y: 1 plane.
+ */
+FDBB_API fdbb_status fdbb_v_mag2(int dim, int64_t n, fdbb_dtype t, const void *const *U, void *y,
+                        fdbb_stream_t stream);
+
+/*
+ * Conservative -> primitive, V = (rho, v, p) with v = m / rho and
+ * p = (gamma - 1)(rhoE - |m|^2 / (2 rho)) (paper section 2.2, Fig. 9,
+ * V = varU::primitive(U)).  U: nv planes in; V: nv planes out.  If V[0] is
+ * NULL or equals U[0] the density plane is not written (no bandwidth is
+ * spent copying rho onto itself, as the paper notes for Fig. 9).
+ */
+FDBB_API fdbb_status fdbb_prim_from_cons(int dim, double gamma, int64_t n, fdbb_dtype t,
+                                const void *const *U, void *const *V, fdbb_stream_t stream);
+
+/*
+ * Primitive -> conservative, m = rho v, rhoE = p / (gamma - 1) + rho |v|^2 / 2
+ * (paper section 2.2, Fig. 9, U = varV::conservative(V)).  V: nv planes in;
+ * U: nv planes out (U[0] skipped when NULL or equal to V[0]).
+ */
+FDBB_API fdbb_status fdbb_cons_from_prim(int dim, double gamma, int64_t n, fdbb_dtype t,
+                                const void *const *V, void *const *U, fdbb_stream_t stream);
+
+/*
+ * Ideal-gas equation of state from conservative variables (paper section 2.2,
+ * Fig. 7, varU::p(U); "Equations of state"): pressure p = (gamma - 1) rho e
+ * and speed of sound c = sqrt(gamma p / rho).  U: nv planes; p, c: one plane
+ * each, either may be NULL.
+ */
+FDBB_API fdbb_status fdbb_eos(int dim, double gamma, int64_t n, fdbb_dtype t, const void *const *U,
+                     void *p, void *c, fdbb_stream_t stream);
+
+/*
+ * Riemann invariants along direction dir in [0, dim) (named in the paper,
+ * section 1 and Fig. 1): w- = u - 2c/(gamma - 1), w+ = u + 2c/(gamma - 1) with
+ * u = v_dir, and the entropy s = p / rho^gamma.  Each output may be NULL.
+ */
+FDBB_API fdbb_status fdbb_riemann_inv(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
+                             const void *const *U, void *wm, void *wp, void *s,
+                             fdbb_stream_t stream);
+
+/*
+ * Inviscid flux (paper section 2.2, "Inviscid Fluxes": the N_U x N_D tensor
+ * F(U) = [rho v; rho v (x) v + I p; v (rhoE + p)]).  dir in [0, dim) writes
+ * the column F_dir (nv planes); dir == -1 writes all columns, direction-major:
+ * plane d*nv + k is component k of F_d (dim*nv planes).
+ */
+FDBB_API fdbb_status fdbb_flux(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
+                      const void *const *U, void *const *F, fdbb_stream_t stream);
+
+/*
+ * Flux Jacobian A_dir = dF_dir / dU (named in the paper, section 1 and
+ * section 2.2, "Inviscid Fluxes", as forthcoming), nv*nv planes, row-major,
+ * rows and columns in U order.  Entries that are identically 0 or 1 are
+ * still written when their plane pointer is not NULL.
+ */
+FDBB_API fdbb_status fdbb_flux_jac(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
+                          const void *const *U, void *const *A, fdbb_stream_t stream);
+
+/*
+ * Characteristic transform at the local state (characteristic variables are
+ * named in the paper, section 1 and Fig. 1).  inverse == 0: Y = L_dir(U) W;
+ * inverse != 0: Y = R_dir(U) W, where the columns of R are the right
+ * eigenvectors of A_dir ordered by eigenvalue u - c, u (entropy), u (shear,
+ * tangential directions ascending), u + c:
+ *   r_1 = (1, v - c e_dir, H - u c), r_2 = (1, v, |v|^2/2),
+ *   r_{2+k} = (0, e_t, v_t), r_nv = (1, v + c e_dir, H + u c),
+ * H = (rhoE + p)/rho, and L = R^{-1}.  U, W: nv planes in; Y: nv planes out.
+ */
+FDBB_API fdbb_status fdbb_char_transform(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
+                                int inverse, const void *const *U, const void *const *W,
+                                void *const *Y, fdbb_stream_t stream);
+
+/*
+ * One pass computing all fluxes, one Jacobian and one characteristic
+ * transform (the paper's mini-app evaluates the 3D inviscid fluxes over
+ * initialised U repeatedly, section 3): F = all dim flux columns
+ * (dim*nv planes, direction-major as fdbb_flux with dir == -1),
+ * A = A_dir_jac (nv*nv planes), Y = L_dir_jac(U) W (nv planes).  U and W are
+ * read once.  F, A, Y (the arrays) or any plane in them may be NULL; W may be
+ * NULL only if Y is NULL.
+ */
+FDBB_API fdbb_status fdbb_euler_fused(int dim, int dir_jac, double gamma, int64_t n, fdbb_dtype t,
+                             const void *const *U, const void *const *W, void *const *F,
+                             void *const *A, void *const *Y, fdbb_stream_t stream);
+
+/*
+ * Vector-Jacobian product of the direction-dir flux: gU = A_dir(U)^T G
+ * (the reverse-mode derivative of F_dir, for automatic differentiation).
+ * U, G: nv planes in; gU: nv planes out.
+ */
+FDBB_API fdbb_status fdbb_flux_vjp(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
+                          const void *const *U, const void *const *G, void *const *gU,
+                          fdbb_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDBB_H */

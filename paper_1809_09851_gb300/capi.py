@@ -1,0 +1,88 @@
+"""ctypes binding of the C ABI in include/fdbb.h (argument marshalling only).
+
+``lib()`` loads ``libfdbb.so`` from the package directory.  There is no
+fallback: if the library has not been built (``paper_1809_09851_gb300.build``)
+every call raises.  The raw functions keep the C names (``fdbb_flux`` ...) and
+take plane-pointer arrays built with :func:`planes`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIBRARY
+
+FDBB_OK = 0
+STATUS = {
+    0: "FDBB_OK", 1: "FDBB_ERR_ARG", 2: "FDBB_ERR_NULLPTR", 3: "FDBB_ERR_ALIGN",
+    4: "FDBB_ERR_DTYPE", 5: "FDBB_ERR_CUDA", 6: "FDBB_ERR_TIMEOUT", 7: "FDBB_ERR_NOMEM",
+}
+FDBB_F64, FDBB_F32, FDBB_F16, FDBB_BF16 = 0, 1, 2, 3
+
+_i, _i64, _d, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> argument types (the return type is int status unless noted)
+SIGNATURES = {
+    "fdbb_v_mag2": [_i, _i64, _i, _PP, _vp, _vp],
+    "fdbb_prim_from_cons": [_i, _d, _i64, _i, _PP, _PP, _vp],
+    "fdbb_cons_from_prim": [_i, _d, _i64, _i, _PP, _PP, _vp],
+    "fdbb_eos": [_i, _d, _i64, _i, _PP, _vp, _vp, _vp],
+    "fdbb_riemann_inv": [_i, _i, _d, _i64, _i, _PP, _vp, _vp, _vp, _vp],
+    "fdbb_flux": [_i, _i, _d, _i64, _i, _PP, _PP, _vp],
+    "fdbb_flux_jac": [_i, _i, _d, _i64, _i, _PP, _PP, _vp],
+    "fdbb_char_transform": [_i, _i, _d, _i64, _i, _i, _PP, _PP, _PP, _vp],
+    "fdbb_euler_fused": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _PP, _PP, _vp],
+    "fdbb_flux_vjp": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _vp],
+}
+
+_lib = None
+
+
+class FdbbError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} returned {STATUS.get(status, status)}")
+        self.status = status
+
+
+def lib():
+    """Load libfdbb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBRARY):
+            raise RuntimeError(
+                f"{LIBRARY} is missing: build the CUDA library first "
+                "(python -m paper_1809_09851_gb300.build or __graft_entry__.build())")
+        L = ctypes.CDLL(LIBRARY)
+        for name, args in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = _i
+        L.fdbb_status_string.argtypes = [_i]
+        L.fdbb_status_string.restype = ctypes.c_char_p
+        L.fdbb_version.argtypes = []
+        L.fdbb_version.restype = _i
+        _lib = L
+    return _lib
+
+
+def planes(ptrs):
+    """Host array of device plane pointers (ints or None) for a C call."""
+    if ptrs is None:
+        return None
+    return (ctypes.c_void_p * max(1, len(ptrs)))(*[p if p else None for p in ptrs])
+
+
+def call(name: str, *args) -> None:
+    """Call fdbb_<name> and raise FdbbError on a non-zero status."""
+    st = getattr(lib(), name)(*args)
+    if st != FDBB_OK:
+        raise FdbbError(name, st)
+
+
+def status_string(status: int) -> str:
+    return lib().fdbb_status_string(status).decode()
+
+
+def exported_symbols():
+    return ["fdbb_status_string", "fdbb_version", *SIGNATURES.keys()]

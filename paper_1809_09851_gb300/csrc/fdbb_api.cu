@@ -1,0 +1,272 @@
+// fdbb_api.cu -- the C ABI declared in include/fdbb.h: argument checks,
+// parameter-block assembly and dispatch to the per-storage-type kernels.
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+
+#include "fdbb.h"
+#include "fdbb_internal.h"
+
+namespace fdbb {
+
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+  if (cached) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+}  // namespace fdbb
+
+namespace {
+
+using fdbb::KArgs;
+using fdbb::LaunchReq;
+using fdbb::OpKind;
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+fdbb_status check_dims(int dim, int64_t n) {
+  if (dim < 1 || dim > 3 || n < 0) return FDBB_ERR_ARG;
+  return FDBB_OK;
+}
+
+fdbb_status check_gamma(double gamma) {
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return FDBB_ERR_ARG;
+  return FDBB_OK;
+}
+
+fdbb_status check_dtype(fdbb_dtype t) {
+  return (t == FDBB_F64 || t == FDBB_F32 || t == FDBB_F16 || t == FDBB_BF16) ? FDBB_OK : FDBB_ERR_DTYPE;
+}
+
+// Required input planes: the array and every entry non-NULL and aligned.
+fdbb_status take_in(KArgs& a, int base, const void* const* P, int k) {
+  if (P == nullptr) return FDBB_ERR_NULLPTR;
+  for (int i = 0; i < k; ++i) {
+    if (P[i] == nullptr) return FDBB_ERR_NULLPTR;
+    if (!aligned16(P[i])) return FDBB_ERR_ALIGN;
+    a.in[base + i] = P[i];
+  }
+  return FDBB_OK;
+}
+
+// Optional output planes: a NULL array (when allowed) or NULL entries are
+// skipped; non-NULL entries must be aligned.
+fdbb_status take_out(KArgs& a, int base, void* const* P, int k, bool array_may_be_null) {
+  if (P == nullptr) return array_may_be_null ? FDBB_OK : FDBB_ERR_NULLPTR;
+  for (int i = 0; i < k; ++i) {
+    if (P[i] != nullptr && !aligned16(P[i])) return FDBB_ERR_ALIGN;
+    a.out[base + i] = P[i];
+  }
+  return FDBB_OK;
+}
+
+fdbb_status take_out1(KArgs& a, int slot, void* p) {
+  if (p != nullptr && !aligned16(p)) return FDBB_ERR_ALIGN;
+  a.out[slot] = p;
+  return FDBB_OK;
+}
+
+KArgs make_args(int64_t n, double gamma) {
+  KArgs a = {};
+  a.n = n;
+  const double g = gamma, a1 = gamma - 1.0;
+  const double kd[6] = {g, a1, 3.0 - g, 2.0 / a1, 1.0 / a1, -g};
+  for (int i = 0; i < 6; ++i) {
+    a.kd[i] = kd[i];
+    a.kf[i] = static_cast<float>(kd[i]);
+  }
+  return a;
+}
+
+fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, const KArgs& a, fdbb_stream_t stream) {
+  if (a.n == 0) return FDBB_OK;
+  const LaunchReq r{op, dim, dir, reinterpret_cast<cudaStream_t>(stream)};
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (t) {
+    case FDBB_F64: e = fdbb::dispatch_f64(r, a); break;
+    case FDBB_F32: e = fdbb::dispatch_f32(r, a); break;
+    case FDBB_F16: e = fdbb::dispatch_f16(r, a); break;
+    case FDBB_BF16: e = fdbb::dispatch_bf16(r, a); break;
+  }
+  return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
+}
+
+#define FDBB_TRY(expr)                   \
+  do {                                   \
+    const fdbb_status s_ = (expr);       \
+    if (s_ != FDBB_OK) return s_;        \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+const char* fdbb_status_string(fdbb_status s) {
+  switch (s) {
+    case FDBB_OK: return "ok";
+    case FDBB_ERR_ARG: return "invalid argument (dim, dir, n or gamma)";
+    case FDBB_ERR_NULLPTR: return "required plane pointer is NULL";
+    case FDBB_ERR_ALIGN: return "plane pointer is not 16-byte aligned";
+    case FDBB_ERR_DTYPE: return "unknown storage type";
+    case FDBB_ERR_CUDA: return "CUDA launch failed";
+    case FDBB_ERR_TIMEOUT: return "timed out waiting for the device";
+    case FDBB_ERR_NOMEM: return "buffer or memory budget too small";
+  }
+  return "unknown status";
+}
+
+int fdbb_version(void) { return 100; }
+
+fdbb_status fdbb_v_mag2(int dim, int64_t n, fdbb_dtype t, const void* const* U, void* y, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, 1.4);
+  FDBB_TRY(take_in(a, 0, U, dim + 1));
+  if (y == nullptr) return FDBB_ERR_NULLPTR;
+  FDBB_TRY(take_out1(a, 0, y));
+  return launch(t, OpKind::VMag2, dim, 0, a, stream);
+}
+
+fdbb_status fdbb_prim_from_cons(int dim, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
+                                void* const* V, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_out(a, 0, V, nv, false));
+  if (a.out[0] == a.in[0]) a.out[0] = nullptr;  // rho onto itself: no copy
+  return launch(t, OpKind::Prim, dim, 0, a, stream);
+}
+
+fdbb_status fdbb_cons_from_prim(int dim, double gamma, int64_t n, fdbb_dtype t, const void* const* V,
+                                void* const* U, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, V, nv));
+  FDBB_TRY(take_out(a, 0, U, nv, false));
+  if (a.out[0] == a.in[0]) a.out[0] = nullptr;
+  return launch(t, OpKind::Cons, dim, 0, a, stream);
+}
+
+fdbb_status fdbb_eos(int dim, double gamma, int64_t n, fdbb_dtype t, const void* const* U, void* p, void* c,
+                     fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  FDBB_TRY(take_in(a, 0, U, dim + 2));
+  FDBB_TRY(take_out1(a, 0, p));
+  FDBB_TRY(take_out1(a, 1, c));
+  if (p == nullptr && c == nullptr) return FDBB_OK;
+  return launch(t, OpKind::Eos, dim, 0, a, stream);
+}
+
+fdbb_status fdbb_riemann_inv(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
+                             void* wm, void* wp, void* s, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  FDBB_TRY(take_in(a, 0, U, dim + 2));
+  FDBB_TRY(take_out1(a, 0, wm));
+  FDBB_TRY(take_out1(a, 1, wp));
+  FDBB_TRY(take_out1(a, 2, s));
+  if (wm == nullptr && wp == nullptr && s == nullptr) return FDBB_OK;
+  return launch(t, OpKind::Riemann, dim, dir, a, stream);
+}
+
+fdbb_status fdbb_flux(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
+                      void* const* F, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < -1 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_out(a, 0, F, dir < 0 ? dim * nv : nv, false));
+  return launch(t, dir < 0 ? OpKind::FluxAll : OpKind::Flux, dim, dir, a, stream);
+}
+
+fdbb_status fdbb_flux_jac(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
+                          void* const* A, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_out(a, 0, A, nv * nv, false));
+  return launch(t, OpKind::Jac, dim, dir, a, stream);
+}
+
+fdbb_status fdbb_char_transform(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, int inverse,
+                                const void* const* U, const void* const* W, void* const* Y,
+                                fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_in(a, nv, W, nv));
+  FDBB_TRY(take_out(a, 0, Y, nv, false));
+  return launch(t, inverse ? OpKind::CharInv : OpKind::CharFwd, dim, dir, a, stream);
+}
+
+fdbb_status fdbb_euler_fused(int dim, int dir_jac, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
+                             const void* const* W, void* const* F, void* const* A, void* const* Y,
+                             fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir_jac < 0 || dir_jac >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_out(a, 0, F, dim * nv, true));
+  FDBB_TRY(take_out(a, dim * nv, A, nv * nv, true));
+  FDBB_TRY(take_out(a, dim * nv + nv * nv, Y, nv, true));
+  bool want_y = false;
+  for (int i = 0; i < nv; ++i) want_y = want_y || a.out[dim * nv + nv * nv + i] != nullptr;
+  if (want_y) {
+    FDBB_TRY(take_in(a, nv, W, nv));
+  } else if (W != nullptr) {
+    // W is not needed: leave in[nv] NULL so the kernel does not read it.
+  }
+  return launch(t, OpKind::Fused, dim, dir_jac, a, stream);
+}
+
+fdbb_status fdbb_flux_vjp(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
+                          const void* const* G, void* const* gU, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_in(a, nv, G, nv));
+  FDBB_TRY(take_out(a, 0, gU, nv, false));
+  return launch(t, OpKind::Vjp, dim, dir, a, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,358 @@
+// fdbb_device.cuh -- device-side building blocks: storage traits, 128-bit
+// streaming I/O, and the per-point Euler algebra.
+//
+// Each kernel thread owns VW consecutive points (one 128-bit word per plane:
+// 2 x f64, 4 x f32, 8 x f16/bf16), loads every input plane once, evaluates the
+// requested expressions in registers and stores every output plane once.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdbb {
+
+// ---------------------------------------------------------------------------
+// Storage traits: compute type R and vector width VW of a storage type T.
+// ---------------------------------------------------------------------------
+template <class T> struct Storage;
+template <> struct Storage<double> { using R = double; static constexpr int VW = 2; };
+template <> struct Storage<float> { using R = float; static constexpr int VW = 4; };
+template <> struct Storage<__half> { using R = float; static constexpr int VW = 8; };
+template <> struct Storage<__nv_bfloat16> { using R = float; static constexpr int VW = 8; };
+
+__device__ __forceinline__ double to_r(double x) { return x; }
+__device__ __forceinline__ float to_r(float x) { return x; }
+__device__ __forceinline__ float to_r(__half x) { return __half2float(x); }
+__device__ __forceinline__ float to_r(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <class T> __device__ __forceinline__ T from_r(typename Storage<T>::R x);
+template <> __device__ __forceinline__ double from_r<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_r<float>(float x) { return x; }
+template <> __device__ __forceinline__ __half from_r<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_r<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+
+// 128-bit streaming loads (evict-first: every input is touched once).
+__device__ __forceinline__ void ld_vec(const double* p, double (&x)[2]) {
+  double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  x[0] = v.x;
+  x[1] = v.y;
+}
+__device__ __forceinline__ void ld_vec(const float* p, float (&x)[4]) {
+  float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+  x[0] = v.x;
+  x[1] = v.y;
+  x[2] = v.z;
+  x[3] = v.w;
+}
+__device__ __forceinline__ void ld_vec(const __half* p, float (&x)[8]) {
+  uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __half2 h = *reinterpret_cast<const __half2*>(&w[k]);
+    float2 f = __half22float2(h);
+    x[2 * k] = f.x;
+    x[2 * k + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void ld_vec(const __nv_bfloat16* p, float (&x)[8]) {
+  uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[k]);
+    float2 f = __bfloat1622float2(h);
+    x[2 * k] = f.x;
+    x[2 * k + 1] = f.y;
+  }
+}
+
+// 128-bit streaming stores.
+__device__ __forceinline__ void st_vec(double* p, const double (&x)[2]) {
+  __stcs(reinterpret_cast<double2*>(p), make_double2(x[0], x[1]));
+}
+__device__ __forceinline__ void st_vec(float* p, const float (&x)[4]) {
+  __stcs(reinterpret_cast<float4*>(p), make_float4(x[0], x[1], x[2], x[3]));
+}
+__device__ __forceinline__ void st_vec(__half* p, const float (&x)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __half2 h = __floats2half2_rn(x[2 * k], x[2 * k + 1]);
+    w[k] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+}
+__device__ __forceinline__ void st_vec(__nv_bfloat16* p, const float (&x)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
+    w[k] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+}
+
+// Load VW points starting at i0; cnt < VW only in the ragged last chunk, where
+// the missing lanes get `fill` (a harmless value that is never stored).
+template <class T, int VW, class R>
+__device__ __forceinline__ void load(const T* p, int64_t i0, int cnt, R (&x)[VW], R fill) {
+  if (cnt == VW) {
+    ld_vec(p + i0, x);
+  } else {
+#pragma unroll
+    for (int j = 0; j < VW; ++j) x[j] = (j < cnt) ? to_r(p[i0 + j]) : fill;
+  }
+}
+
+// Store VW points; a NULL plane is skipped.
+template <class T, int VW, class R>
+__device__ __forceinline__ void store(T* p, int64_t i0, int cnt, const R (&x)[VW]) {
+  if (p == nullptr) return;
+  if (cnt == VW) {
+    st_vec(p + i0, x);
+  } else {
+#pragma unroll
+    for (int j = 0; j < VW; ++j)
+      if (j < cnt) p[i0 + j] = from_r<T>(x[j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic helpers, overloaded on the compute type.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_(float x) { return 1.0f / x; }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+
+// Constants derived from gamma on the host in double, rounded once to R.
+template <class R> struct Consts {
+  R g;      // gamma
+  R a1;     // gamma - 1
+  R g3;     // 3 - gamma
+  R ta1;    // 2 / (gamma - 1)
+  R ia1;    // 1 / (gamma - 1)
+  R mg;     // -gamma
+};
+
+// ---------------------------------------------------------------------------
+// Per-point state
+// ---------------------------------------------------------------------------
+template <class R, int D> struct Pt {
+  R rho, m[D], rE;  // conservative state
+  R r;              // 1 / rho
+  R v[D];           // velocity
+  R rq;             // kinetic energy density rho |v|^2 / 2
+  R q;              // |v|^2 / 2
+  R p;              // pressure
+  R H;              // total specific enthalpy (rhoE + p) / rho
+  R c2;             // squared speed of sound gamma p / rho
+};
+
+// Error-free transforms (Knuth TwoSum, FMA-based TwoProduct), written with
+// round-to-nearest intrinsics so that no contraction or reassociation applies.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// Internal-energy density rho e = rhoE - |m|^2 / (2 rho).
+//  double: plain evaluation (relative error ~ u * (rhoE + rho q) / rho e).
+//  float : compensated evaluation; |m|^2 is summed exactly as a float pair
+//          (TwoProduct + TwoSum, Ogita-Rump-Oishi), divided by 2 rho with a
+//          remainder correction, and subtracted from rhoE with TwoSum, so the
+//          result is accurate to a few ulp of rho e itself even when
+//          rho q / rho e ~ 1e3 (Mach 50) or rho ~ 1e-4 (near vacuum).
+template <int D>
+__device__ __forceinline__ void internal_energy(Pt<double, D>& s, double& rhoe) {
+  double mv = s.m[0] * s.v[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) mv = fma(s.m[i], s.v[i], mv);
+  s.rq = 0.5 * mv;
+  rhoe = s.rE - s.rq;
+}
+template <int D>
+__device__ __forceinline__ void internal_energy(Pt<float, D>& s, float& rhoe) {
+  float hi, lo;
+  two_prod(s.m[0], s.m[0], hi, lo);
+#pragma unroll
+  for (int i = 1; i < D; ++i) {
+    float ph, pl, t;
+    two_prod(s.m[i], s.m[i], ph, pl);
+    two_sum(hi, ph, hi, t);
+    lo = __fadd_rn(lo, __fadd_rn(t, pl));
+  }
+  hi = __fmul_rn(0.5f, hi);  // exact scaling by 1/2
+  lo = __fmul_rn(0.5f, lo);
+  const float qh = __fmul_rn(hi, s.r);           // rho q, leading part
+  const float rem = __fmaf_rn(-qh, s.rho, hi);   // hi - qh rho (exact or nearly)
+  const float ql = __fmul_rn(__fadd_rn(rem, lo), s.r);
+  float d, t;
+  two_sum(s.rE, -qh, d, t);
+  rhoe = __fadd_rn(d, __fsub_rn(t, ql));
+  s.rq = qh;
+}
+
+// Conservative -> derived state.  One reciprocal per point.
+template <class R, int D>
+__device__ __forceinline__ void derive(Pt<R, D>& s, const Consts<R>& k) {
+  s.r = rcp_(s.rho);
+#pragma unroll
+  for (int i = 0; i < D; ++i) s.v[i] = s.m[i] * s.r;
+  R rhoe;
+  internal_energy<D>(s, rhoe);
+  s.q = s.rq * s.r;
+  s.p = k.a1 * rhoe;
+  s.H = (s.rE + s.p) * s.r;
+  s.c2 = k.g * s.p * s.r;
+}
+
+// Load the conservative state of VW points.
+template <class T, int VW, int D, class R>
+__device__ __forceinline__ void load_state(const T* const* U, int64_t i0, int cnt, Pt<R, D> (&s)[VW]) {
+  R x[VW];
+  load<T, VW, R>(U[0], i0, cnt, x, R(1));
+#pragma unroll
+  for (int j = 0; j < VW; ++j) s[j].rho = x[j];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    load<T, VW, R>(U[1 + i], i0, cnt, x, R(0));
+#pragma unroll
+    for (int j = 0; j < VW; ++j) s[j].m[i] = x[j];
+  }
+  load<T, VW, R>(U[D + 1], i0, cnt, x, R(1));
+#pragma unroll
+  for (int j = 0; j < VW; ++j) s[j].rE = x[j];
+}
+
+// ---------------------------------------------------------------------------
+// Per-point formulas.  `d` is a compile-time direction.
+// ---------------------------------------------------------------------------
+
+// Flux column d: F[0] = m_d, F[1+i] = m_d v_i + delta_id p, F[nv-1] = v_d (rhoE + p).
+template <int D, int d, class R>
+__device__ __forceinline__ R flux_comp(const Pt<R, D>& s, int k) {
+  if (k == 0) return s.m[d];
+  if (k == D + 1) return s.v[d] * (s.rE + s.p);
+  const int i = k - 1;
+  return (i == d) ? fma_(s.m[d], s.v[d], s.p) : s.m[d] * s.v[i];
+}
+
+// Jacobian entry A_d[row][col] (row-major), u = v_d, phi = (gamma-1) q.
+template <int D, int d, class R>
+__device__ __forceinline__ R jac_entry(const Pt<R, D>& s, const Consts<R>& k, int row, int col) {
+  constexpr int nv = D + 2;
+  const R u = s.v[d];
+  if (row == 0) return (col == 1 + d) ? R(1) : R(0);
+  if (row == nv - 1) {
+    if (col == 0) return u * (k.a1 * s.q - s.H);
+    if (col == nv - 1) return k.g * u;
+    if (col == 1 + d) return fma_(-(k.a1 * u), u, s.H);
+    return -(k.a1 * u) * s.v[col - 1];
+  }
+  const int i = row - 1;
+  if (i != d) {
+    if (col == 0) return -(u * s.v[i]);
+    if (col == 1 + d) return s.v[i];
+    if (col == 1 + i) return u;
+    return R(0);
+  }
+  // row 1 + d
+  if (col == 0) return fma_(-u, u, k.a1 * s.q);
+  if (col == nv - 1) return k.a1;
+  if (col == 1 + d) return k.g3 * u;
+  return -(k.a1 * s.v[col - 1]);
+}
+
+// Tangential direction t_k of d (ascending), compile-time.
+template <int D, int d> __device__ __forceinline__ constexpr int tang(int k) {
+  return (k < d) ? k : k + 1;
+}
+
+// Forward characteristic transform Y = L_d W at one point (see fdbb.h):
+//   t = b1 (q w0 - v.w + w_e), a = (u w0 - w_d) / c, b1 = (gamma-1)/c^2
+//   Y0 = (t + a)/2, Y1 = w0 - t, Y_{1+k} = w_{t_k} - v_{t_k} w0, Y_{nv-1} = (t - a)/2
+template <int D, int d, class R>
+__device__ __forceinline__ void char_fwd(const Pt<R, D>& s, const Consts<R>& k, const R* w, R* y) {
+  constexpr int nv = D + 2;
+  const R ic = rsqrt_(s.c2);
+  const R b1 = k.a1 * ic * ic;
+  R dot = s.v[0] * w[1];
+#pragma unroll
+  for (int i = 1; i < D; ++i) dot = fma_(s.v[i], w[1 + i], dot);
+  const R t = b1 * (fma_(s.q, w[0], w[nv - 1]) - dot);
+  const R a = fma_(s.v[d], w[0], -w[1 + d]) * ic;
+  y[0] = R(0.5) * (t + a);
+  y[1] = w[0] - t;
+#pragma unroll
+  for (int kk = 0; kk < D - 1; ++kk) {
+    const int tk = tang<D, d>(kk);
+    y[2 + kk] = fma_(-s.v[tk], w[0], w[1 + tk]);
+  }
+  y[nv - 1] = R(0.5) * (t - a);
+}
+
+// Inverse characteristic transform Y = R_d W at one point.
+template <int D, int d, class R>
+__device__ __forceinline__ void char_inv(const Pt<R, D>& s, const Consts<R>& k, const R* w, R* y) {
+  constexpr int nv = D + 2;
+  const R c = sqrt_(s.c2);
+  const R a1 = w[0], a2 = w[1], an = w[nv - 1];
+  const R sum = a1 + a2 + an;
+  const R dif = c * (an - a1);
+  y[0] = sum;
+#pragma unroll
+  for (int i = 0; i < D; ++i) y[1 + i] = s.v[i] * sum;
+  y[1 + d] = y[1 + d] + dif;
+  R e = fma_(s.H, a1 + an, s.v[d] * dif);
+  e = fma_(s.q, a2, e);
+#pragma unroll
+  for (int kk = 0; kk < D - 1; ++kk) {
+    const int tk = tang<D, d>(kk);
+    y[1 + tk] = y[1 + tk] + w[2 + kk];
+    e = fma_(s.v[tk], w[2 + kk], e);
+  }
+  y[nv - 1] = e;
+}
+
+// gU = A_d^T G at one point, with z = g_d + u g_e and sigma = sum_{i != d} v_i g_i:
+//   gU[0]     = phi z - u sigma - u (u g_d + H g_e)
+//   gU[1+j]   = u g_j - (gamma-1) v_j z             (j != d)
+//   gU[1+d]   = g_0 + sigma + 2 u g_d + H g_e - (gamma-1) u z
+//   gU[nv-1]  = (gamma-1) g_d + gamma u g_e
+template <int D, int d, class R>
+__device__ __forceinline__ void flux_vjp_pt(const Pt<R, D>& s, const Consts<R>& k, const R* g, R* y) {
+  constexpr int nv = D + 2;
+  const R u = s.v[d];
+  const R gd = g[1 + d], ge = g[nv - 1];
+  const R z = fma_(u, ge, gd);
+  R sigma = R(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+    if (i != d) sigma = fma_(s.v[i], g[1 + i], sigma);
+  const R phi = k.a1 * s.q;
+  y[0] = fma_(phi, z, -fma_(u, sigma, u * fma_(u, gd, s.H * ge)));
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    if (j != d) y[1 + j] = fma_(u, g[1 + j], -(k.a1 * s.v[j] * z));
+  y[1 + d] = g[0] + sigma + fma_(R(2) * u, gd, fma_(s.H, ge, -(k.a1 * u * z)));
+  y[nv - 1] = fma_(k.a1, gd, k.g * u * ge);
+}
+
+}  // namespace fdbb

@@ -1,0 +1,40 @@
+// fdbb_internal.h -- types shared by the C-ABI layer and the kernel
+// translation units (not part of the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdbb {
+
+constexpr int kMaxIn = 10;   // U (nv) + W or G (nv)
+constexpr int kMaxOut = 45;  // fused 3D: 15 flux + 25 Jacobian + 5 characteristic
+
+enum class OpKind { VMag2, Prim, Cons, Eos, Riemann, Flux, FluxAll, Jac, CharFwd, CharInv, Fused, Vjp };
+
+// Kernel parameter block (passed by value as a __grid_constant__).
+struct KArgs {
+  const void* in[kMaxIn];
+  void* out[kMaxOut];
+  int64_t n;
+  double kd[6];  // gamma, gamma-1, 3-gamma, 2/(gamma-1), 1/(gamma-1), -gamma
+  float kf[6];   // the same, rounded once to float
+};
+
+struct LaunchReq {
+  OpKind op;
+  int dim;
+  int dir;
+  cudaStream_t stream;
+};
+
+// Streaming multiprocessors of the current device (cached per device).
+int device_sm_count();
+
+// Defined once per storage type (one translation unit each).
+cudaError_t dispatch_f64(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_f32(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_bf16(const LaunchReq& r, const KArgs& a);
+
+}  // namespace fdbb

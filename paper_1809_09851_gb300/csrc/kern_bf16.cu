@@ -1,0 +1,6 @@
+// kern_bf16.cu -- all building-block kernels for __nv_bfloat16 storage.
+#include "fdbb_kernels.cuh"
+
+namespace fdbb {
+cudaError_t dispatch_bf16(const LaunchReq& r, const KArgs& a) { return dispatch<__nv_bfloat16>(r, a); }
+}  // namespace fdbb

@@ -1,0 +1,6 @@
+// kern_f16.cu -- all building-block kernels for __half storage.
+#include "fdbb_kernels.cuh"
+
+namespace fdbb {
+cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a) { return dispatch<__half>(r, a); }
+}  // namespace fdbb

@@ -1,0 +1,6 @@
+// kern_f64.cu -- all building-block kernels for double storage.
+#include "fdbb_kernels.cuh"
+
+namespace fdbb {
+cudaError_t dispatch_f64(const LaunchReq& r, const KArgs& a) { return dispatch<double>(r, a); }
+}  // namespace fdbb

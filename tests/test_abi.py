@@ -1,0 +1,86 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every entry point declared in include/fdbb.h, and rejects bad
+arguments before any launch (fake device pointers are never dereferenced
+because every call here fails validation or has n == 0)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1809_09851_gb300 import build as lib_build
+from paper_1809_09851_gb300 import capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fdbb.h")
+
+A = 1 << 20          # a 16-byte aligned fake address
+MIS = (1 << 20) + 8  # an 8-byte (not 16-byte) aligned fake address
+
+
+@pytest.fixture(scope="module")
+def L():
+    lib_build.build()
+    return capi.lib()
+
+
+def declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"FDBB_API[^;]*?\b(fdbb_[a-z0-9_]+)\s*\(", text, re.S)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for need in ["fdbb_prim_from_cons", "fdbb_cons_from_prim", "fdbb_eos", "fdbb_riemann_inv",
+                 "fdbb_flux", "fdbb_flux_jac", "fdbb_char_transform", "fdbb_euler_fused",
+                 "fdbb_flux_vjp", "fdbb_v_mag2", "fdbb_status_string"]:
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_build.LIBRARY], capture_output=True, text=True)
+    exported = set(re.findall(r"\sT\s(\w+)", out.stdout))
+    assert set(declared()) <= exported
+    # nothing but the C ABI leaks out of the shared object
+    assert all(s.startswith("fdbb_") or s.startswith("_") for s in exported), sorted(exported)[:10]
+
+
+def test_status_strings(L):
+    assert capi.status_string(0) == "ok"
+    assert "aligned" in capi.status_string(3)
+    assert L.fdbb_version() >= 100
+
+
+def _U(k, addr=A):
+    return capi.planes([addr + 256 * i for i in range(k)])
+
+
+def test_argument_errors_return_before_launch(L):
+    F64 = capi.FDBB_F64
+    # dim out of range
+    assert L.fdbb_flux(4, 0, 1.4, 10, F64, _U(6), _U(6), None) == 1
+    # dir out of range
+    assert L.fdbb_flux(3, 3, 1.4, 10, F64, _U(5), _U(5), None) == 1
+    assert L.fdbb_flux_jac(2, -1, 1.4, 10, F64, _U(4), _U(16), None) == 1
+    # gamma <= 1
+    assert L.fdbb_eos(3, 1.0, 10, F64, _U(5), A, A, None) == 1
+    # n < 0
+    assert L.fdbb_prim_from_cons(3, 1.4, -1, F64, _U(5), _U(5), None) == 1
+    # NULL input array / NULL input plane
+    assert L.fdbb_flux(3, 0, 1.4, 10, F64, None, _U(5), None) == 2
+    assert L.fdbb_flux(3, 0, 1.4, 10, F64, capi.planes([A, 0, A, A, A]), _U(5), None) == 2
+    # misaligned input / output plane
+    assert L.fdbb_flux(3, 0, 1.4, 10, F64, _U(5, MIS), _U(5), None) == 3
+    assert L.fdbb_flux_jac(3, 0, 1.4, 10, F64, _U(5), capi.planes([A] * 24 + [MIS]), None) == 3
+    # unknown storage type
+    assert L.fdbb_flux(3, 0, 1.4, 10, 9, _U(5), _U(5), None) == 4
+    # fused: W required when Y is wanted
+    assert L.fdbb_euler_fused(3, 0, 1.4, 10, F64, _U(5), None, None, None, _U(5), None) == 2
+
+
+def test_empty_input_is_a_no_op(L):
+    # n == 0 validates the arguments and returns without touching the device
+    assert L.fdbb_flux(3, -1, 1.4, 0, capi.FDBB_F32, _U(5), _U(15), None) == 0
+    assert L.fdbb_euler_fused(3, 0, 1.4, 0, capi.FDBB_F64, _U(5), _U(5), _U(15), _U(25), _U(5), None) == 0

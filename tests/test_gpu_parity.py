@@ -1,0 +1,236 @@
+"""GPU parity: every entry point of the C ABI against the FP64 CPU oracle.
+
+FP64 storage: |gpu - oracle| <= 1e-12 * S per output, S the oracle's
+first-order running-error scale (S >= |oracle|, larger where the formula
+cancels; S == 0 only for exact copies, which must then be bit-equal).
+Reduced-precision storage (f32/f16/bf16, float arithmetic): the oracle runs on
+the dequantised inputs and |gpu - oracle| <= u_store |oracle| + 64 * 2^-24 * S,
+u_store the unit roundoff of the output storage type (plus half its
+subnormal spacing, for results below its smallest normal number).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1809_09851_gb300 import blocks, capi, synth
+
+pytestmark = pytest.mark.gpu
+
+G = 1.4
+SIZES = [1, 2, 7, 31, 513, 65539]  # ragged tails, several 256-thread tiles
+U_STORE = {torch.float64: 0.0, torch.float32: 2.0 ** -24, torch.float16: 2.0 ** -11,
+           torch.bfloat16: 2.0 ** -8}
+# half the spacing of the storage type's subnormals: below its smallest normal
+# number, rounding to the storage type is an absolute error of at most this
+TINY_STORE = {torch.float64: 0.0, torch.float32: 2.0 ** -150, torch.float16: 2.0 ** -25,
+              torch.bfloat16: 2.0 ** -134}
+TOL_F64 = 1e-12
+K_F32 = 64 * 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1809_09851_gb300 import build
+    build.build()
+    capi.lib()
+    assert torch.cuda.is_available()
+
+
+DEV = "cuda:0"
+
+
+def fields(n, D, seed=1809):
+    V = synth.euler3d(n, seed=seed, D=D) if D > 1 else synth.euler1d(n, seed=seed)
+    U = oracle.cons_from_prim(D, G, V)
+    W = synth.char_weights(n, D + 2, seed=seed + 1)
+    return V, U, W
+
+
+def quantise(planes, dtype):
+    """Round float64 numpy planes to `dtype`; returns (device tensors, dequantised float64)."""
+    dev = [torch.from_numpy(np.ascontiguousarray(p)).to(DEV).to(dtype) for p in planes]
+    back = [t.double().cpu().numpy() for t in dev]
+    return dev, back
+
+
+def host(planes):
+    return [t.double().cpu().numpy() for t in planes]
+
+
+def check(got, ref, S, dtype, what):
+    u_out = U_STORE[dtype]
+    k = TOL_F64 if dtype == torch.float64 else K_F32
+    assert len(got) == len(ref)
+    for c, (g, o, s) in enumerate(zip(got, ref, S)):
+        bound = u_out * np.abs(o) + TINY_STORE[dtype] + k * s
+        err = np.abs(g - o)
+        ok = err <= bound
+        if dtype == torch.float16:
+            ok |= np.abs(o) > 6.0e4  # beyond the f16 range the stored value is inf
+        if not ok.all():
+            i = int(np.argmin(ok))
+            raise AssertionError(f"{what}: plane {c} point {i}: gpu={g[i]!r} oracle={o[i]!r} "
+                                 f"S={s[i]!r} bound={bound[i]!r}")
+
+
+# ---------------------------------------------------------------------------
+# FP64, every block, every dim / dir, several sizes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_f64_variables_and_eos(n, D):
+    V, U, W = fields(n, D)
+    Ud, _ = quantise(U, torch.float64)
+    Vd, _ = quantise(V, torch.float64)
+    ref, S = oracle.prim_from_cons(D, G, U, scale=True)
+    check(host(blocks.prim_from_cons(Ud, G)), ref, S, torch.float64, "prim_from_cons")
+    ref, S = oracle.cons_from_prim(D, G, V, scale=True)
+    check(host(blocks.cons_from_prim(Vd, G)), ref, S, torch.float64, "cons_from_prim")
+    ref, S = oracle.eos(D, G, U, scale=True)
+    check(host(blocks.eos(Ud, G)), ref, S, torch.float64, "eos")
+    ref, S = oracle.v_mag2(D, U, scale=True)
+    check(host([blocks.v_mag2(Ud)]), ref, S, torch.float64, "v_mag2")
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_f64_directional_blocks(n, D):
+    V, U, W = fields(n, D)
+    Ud, _ = quantise(U, torch.float64)
+    Wd, _ = quantise(W, torch.float64)
+    nv = D + 2
+    Gc = synth.cotangent(n, nv)
+    Gd, _ = quantise(Gc, torch.float64)
+    ref, S = oracle.flux(D, -1, G, U, scale=True)
+    check(host(blocks.flux(Ud, -1, G)), ref, S, torch.float64, "flux all")
+    for d in range(D):
+        ref, S = oracle.flux(D, d, G, U, scale=True)
+        check(host(blocks.flux(Ud, d, G)), ref, S, torch.float64, f"flux {d}")
+        ref, S = oracle.flux_jac(D, d, G, U, scale=True)
+        check(host(blocks.flux_jac(Ud, d, G)), ref, S, torch.float64, f"flux_jac {d}")
+        ref, S = oracle.riemann_inv(D, d, G, U, scale=True)
+        wm, wp, s = blocks.riemann_inv(Ud, d, G, entropy=True)
+        check(host([wm, wp, s]), ref, S, torch.float64, f"riemann {d}")
+        for inv in (False, True):
+            ref, S = oracle.char_transform(D, d, G, U, W, inverse=inv, scale=True)
+            check(host(blocks.char_transform(Ud, Wd, d, G, inverse=inv)), ref, S, torch.float64,
+                  f"char {d} inv={inv}")
+        ref, S = oracle.flux_vjp(D, d, G, U, Gc, scale=True)
+        check(host(blocks.flux_vjp(Ud, Gd, d, G)), ref, S, torch.float64, f"vjp {d}")
+        ref, S = oracle.euler_fused(D, d, G, U, W, scale=True)
+        Fo, Ao, Yo = blocks.euler_fused(Ud, Wd, d, G)
+        check(host([*Fo, *Ao, *Yo]), ref, S, torch.float64, f"fused {d}")
+
+
+# ---------------------------------------------------------------------------
+# reduced-precision storage
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("D", [1, 3])
+def test_reduced_precision_blocks(dtype, D):
+    n = 4099
+    V, U, W = fields(n, D, seed=77)
+    Ud, Uq = quantise(U, dtype)
+    Vd, Vq = quantise(V, dtype)
+    Wd, Wq = quantise(W, dtype)
+    ref, S = oracle.prim_from_cons(D, G, Uq, scale=True)
+    check(host(blocks.prim_from_cons(Ud, G)), ref, S, dtype, "prim")
+    ref, S = oracle.cons_from_prim(D, G, Vq, scale=True)
+    check(host(blocks.cons_from_prim(Vd, G)), ref, S, dtype, "cons")
+    ref, S = oracle.eos(D, G, Uq, scale=True)
+    check(host(blocks.eos(Ud, G)), ref, S, dtype, "eos")
+    for d in range(D):
+        ref, S = oracle.riemann_inv(D, d, G, Uq, scale=True)
+        wm, wp, s = blocks.riemann_inv(Ud, d, G, entropy=True)
+        check(host([wm, wp, s]), ref, S, dtype, "riemann")
+        ref, S = oracle.euler_fused(D, d, G, Uq, Wq, scale=True)
+        Fo, Ao, Yo = blocks.euler_fused(Ud, Wd, d, G)
+        check(host([*Fo, *Ao, *Yo]), ref, S, dtype, f"fused {d}")
+        for inv in (False, True):
+            ref, S = oracle.char_transform(D, d, G, Uq, Wq, inverse=inv, scale=True)
+            check(host(blocks.char_transform(Ud, Wd, d, G, inverse=inv)), ref, S, dtype, "char")
+        ref, S = oracle.flux_vjp(D, d, G, Uq, Wq, scale=True)
+        check(host(blocks.flux_vjp(Ud, Wd, d, G)), ref, S, dtype, "vjp")
+
+
+# ---------------------------------------------------------------------------
+# semantics: in place, skipped outputs, argument errors with real tensors
+# ---------------------------------------------------------------------------
+
+def test_in_place_prim_from_cons():
+    n, D = 1003, 3
+    V, U, W = fields(n, D)
+    Ud, _ = quantise(U, torch.float64)
+    rho_ptr = Ud[0].data_ptr()
+    out = blocks.prim_from_cons(Ud, G, out=Ud)
+    assert out[0].data_ptr() == rho_ptr
+    ref, S = oracle.prim_from_cons(D, G, U, scale=True)
+    check(host(out), ref, S, torch.float64, "in-place prim")
+
+
+def test_skipped_outputs():
+    n, D = 777, 3
+    V, U, W = fields(n, D)
+    Ud, _ = quantise(U, torch.float64)
+    Wd, _ = quantise(W, torch.float64)
+    sentinel = torch.full((n,), 12345.0, dtype=torch.float64, device=DEV)
+    F = [torch.empty(n, dtype=torch.float64, device=DEV) for _ in range(15)]
+    F[3] = None
+    A = [sentinel.clone() if k != 6 else torch.empty(n, dtype=torch.float64, device=DEV) for k in range(25)]
+    Fo, Ao, Yo = blocks.euler_fused(Ud, None, 0, G, out=(F, [a if k == 6 else None for k, a in enumerate(A)], None))
+    ref = oracle.euler_fused(D, 0, G, U, W)
+    for k in range(15):
+        if k != 3:
+            np.testing.assert_allclose(Fo[k].cpu().numpy(), ref[k], rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(Ao[6].cpu().numpy(), ref[15 + 6], rtol=1e-12)
+    p, c = blocks.eos(Ud, G, want_p=False)
+    assert p is None
+    np.testing.assert_allclose(c.cpu().numpy(), oracle.eos(D, G, U)[1], rtol=1e-13)
+
+
+def test_misaligned_plane_is_rejected():
+    base = torch.zeros(1001, dtype=torch.float64, device=DEV)
+    U = [base[1:].clone() for _ in range(5)]
+    U[2] = base[1:]  # 8-byte offset view
+    with pytest.raises(capi.FdbbError) as e:
+        blocks.flux(U, 0, G)
+    assert e.value.status == 3
+
+
+# ---------------------------------------------------------------------------
+# full size, in the benchmark's launch configuration
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_full_size_fused_sampled(dtype):
+    """3D fused pass at N = 2^26 (the benchmark size): sampled points against
+    the oracle, and A_x(U) U = F_x(U) checked at every point."""
+    n, D = 1 << 26, 3
+    V = synth.euler3d(n)
+    U = oracle.cons_from_prim(D, G, V)
+    W = synth.char_weights(n)
+    Ud, Uq = quantise(U, dtype)
+    Wd, Wq = quantise(W, dtype)
+    del V
+    F, A, Y = blocks.euler_fused(Ud, Wd, 0, G)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 4096), np.arange(n - 37, n), np.arange(5)]))
+    it = torch.from_numpy(idx).to(DEV)
+    got = [t[it].double().cpu().numpy() for t in (*F, *A, *Y)]
+    Us = [u[idx] for u in Uq]
+    Ws = [w[idx] for w in Wq]
+    ref, S = oracle.euler_fused(D, 0, G, Us, Ws, scale=True)
+    check(got, ref, S, dtype, "full-size fused")
+    # homogeneity at every point, evaluated on the device in float64
+    Ux = [u.double() for u in Ud]
+    tol = 1e-12 if dtype == torch.float64 else 64 * 2.0 ** -24
+    for r in range(5):
+        Au = sum(A[r * 5 + c].double() * Ux[c] for c in range(5))
+        scale = sum((A[r * 5 + c].double() * Ux[c]).abs() for c in range(5))
+        err = (Au - F[r].double()).abs()
+        assert bool((err <= 8 * tol * scale + 1e-300).all()), r
