@@ -231,6 +231,8 @@ def run_gpu(args):
     # ---- FP32 and BF16 storage (float arithmetic, compensated recovery) -------
     extra = {}
     for tag, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        if args.only not in ("all", tag):
+            continue
         U = [u.to(dt) for u in U64]
         W = [w.to(dt) for w in W64]
         out = (alloc(D * NV, dt), alloc(NV * NV, dt), alloc(NV, dt))
@@ -249,7 +251,7 @@ def run_gpu(args):
         torch.cuda.empty_cache()
 
     # ---- end to end through host buffers ---------------------------------------
-    e2e = run_e2e(args, U64, W64, out64, stream, dev, world)
+    e2e = None if args.no_e2e else run_e2e(args, U64, W64, out64, stream, dev, world)
 
     result = None
     if rank == 0:
@@ -399,6 +401,9 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=1 << 16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16"], default="all",
+                    help="storage types to time besides the f64 headline (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         print("bench: warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -1,0 +1,59 @@
+"""The N > 1 benchmark path on CPU: two gloo ranks, each evaluating its own
+independently seeded field (weak scaling, no data exchange), timing combined
+as the maximum over ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+import oracle
+from paper_1809_09851_gb300 import synth
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w, r, local = bench.dist_env()
+    assert (w, r, local) == (world, rank, rank)
+    seed = bench.shard_seed(1809, r)
+    n = 1000
+    U = oracle.cons_from_prim(3, 1.4, synth.euler3d(n, seed=seed))
+    F = oracle.flux(3, -1, 1.4, U)
+    # each rank's elapsed time differs; the job time is the slowest rank's
+    t = bench.max_over_ranks(0.5 + rank, w)
+    np.save(os.path.join(out_dir, f"rank{rank}.npy"), np.stack([U[0][:8], F[4][:8]]))
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as fh:
+        fh.write(f"{t}\n")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_shard_without_exchange(tmp_path):
+    world = 2
+    mp.start_processes(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       start_method="spawn", join=True)
+    t = [float(open(tmp_path / f"rank{r}.txt").read()) for r in range(world)]
+    assert t == [1.5, 1.5]
+    a, b = (np.load(tmp_path / f"rank{r}.npy") for r in range(world))
+    assert not np.array_equal(a, b)  # independent fields per rank
+    # rank 1's field is exactly what a single process draws with rank 1's seed
+    U1 = oracle.cons_from_prim(3, 1.4, synth.euler3d(1000, seed=bench.shard_seed(1809, 1)))
+    np.testing.assert_array_equal(b[0], U1[0][:8])
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"]) is None
