@@ -74,7 +74,24 @@ typedef enum {
   FDBB_ERR_NOMEM = 7    /* a caller-supplied buffer or budget is too small       */
 } fdbb_status;
 
-typedef enum { FDBB_F64 = 0, FDBB_F32 = 1, FDBB_F16 = 2, FDBB_BF16 = 3 } fdbb_dtype;
+/*
+ * Storage type of every plane of a call (and the arithmetic used):
+ *   FDBB_F64    double planes, IEEE double arithmetic.
+ *   FDBB_F32    float planes, float arithmetic (compensated rho e).
+ *   FDBB_F16    half planes, float arithmetic (compensated rho e).
+ *   FDBB_BF16   bfloat16 planes, float arithmetic (compensated rho e).
+ *   FDBB_F64_DW double planes, double-word ("float-float", ~47-bit
+ *               significand) arithmetic on the float pipe.  Results are within
+ *               1e-12 of the running-error scale of each formula (the same
+ *               bound the FDBB_F64 results meet).  A point where an input or a
+ *               derived quantity (v, |v|^2/2, p, H, c^2) is non-zero with
+ *               magnitude outside [2^-24, 2^24], or not finite, is computed in
+ *               IEEE double instead.  Outputs that are copies of an input are
+ *               bit-exact.  The inverse characteristic transform always uses
+ *               IEEE double.  On GPUs whose FP64 rate is a small fraction of
+ *               the FP32 rate (GB300: 1/64) this is the fast FP64-storage form.
+ */
+typedef enum { FDBB_F64 = 0, FDBB_F32 = 1, FDBB_F16 = 2, FDBB_BF16 = 3, FDBB_F64_DW = 4 } fdbb_dtype;
 
 /* Human-readable name of a status code (static string, never NULL). */
 FDBB_API const char *fdbb_status_string(fdbb_status status);

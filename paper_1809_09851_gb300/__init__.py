@@ -11,6 +11,7 @@ Modules:
   build    -- compile libfdbb.so in-tree (nvcc, sm_103a)
   capi     -- ctypes binding, C names
   blocks   -- torch-tensor wrappers of each entry point
+  autograd -- differentiable flux (backward = the flux VJP kernel)
   synth    -- seeded synthetic input fields (no method arithmetic)
 """
 from . import build, capi  # noqa: F401
@@ -21,7 +22,7 @@ __version__ = "0.1.0"
 def __getattr__(name):
     # Tensor wrappers import torch; load them on first use so that the input
     # generators and the build script work without a GPU stack.
-    if name == "blocks":
+    if name in ("blocks", "autograd"):
         import importlib
-        return importlib.import_module(__name__ + ".blocks")
+        return importlib.import_module(__name__ + "." + name)
     raise AttributeError(name)

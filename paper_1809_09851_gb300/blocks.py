@@ -6,6 +6,11 @@ rhoE), primitive V = (rho, v_1..v_D, p).  All planes of a call share one
 dtype (float64, float32, float16 or bfloat16) and one length.  Outputs are
 allocated with torch unless passed in ``out``; the kernel runs on the current
 torch stream (or ``stream``).  Every computation happens in libfdbb.so.
+
+``dw=True`` (float64 planes only) selects double-word arithmetic
+(FDBB_F64_DW): the same results to within 1e-12 of each formula's
+running-error scale, computed on the float pipe, with IEEE double for points
+outside its range.
 """
 from __future__ import annotations
 
@@ -42,6 +47,14 @@ def _info(planes: Sequence[torch.Tensor]):
     return t0.shape[0], t0.dtype, t0.device
 
 
+def _code(dtype, dw: bool) -> int:
+    if dw:
+        if dtype != torch.float64:
+            raise TypeError("double-word arithmetic applies to float64 planes only")
+        return capi.FDBB_F64_DW
+    return DTYPES[dtype]
+
+
 def _stream(device, stream) -> int:
     s = stream if stream is not None else torch.cuda.current_stream(device)
     return s.cuda_stream
@@ -62,84 +75,84 @@ def _dim(U) -> int:
     return D
 
 
-def v_mag2(U, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+def v_mag2(U, out: Optional[torch.Tensor] = None, stream=None, dw: bool = False) -> torch.Tensor:
     """|v|^2 = sum m_i^2 / rho^2 (paper section 3, Eq. (2)); U may be nv or D+1 planes."""
     D = len(U) - 2 if len(U) >= 3 else len(U) - 1
     D = min(max(D, 1), 3)
     n, dt, dev = _info(U[: D + 1])
     y = out if out is not None else torch.empty(n, dtype=dt, device=dev)
-    capi.call("fdbb_v_mag2", D, n, DTYPES[dt], _ptrs(U[: D + 1]), y.data_ptr(), _stream(dev, stream))
+    capi.call("fdbb_v_mag2", D, n, _code(dt, dw), _ptrs(U[: D + 1]), y.data_ptr(), _stream(dev, stream))
     return y
 
 
-def prim_from_cons(U, gamma: float = GAMMA, out=None, stream=None):
+def prim_from_cons(U, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
     D = _dim(U)
     n, dt, dev = _info(U)
     V = out if out is not None else _alloc(D + 2, n, dt, dev)
-    capi.call("fdbb_prim_from_cons", D, gamma, n, DTYPES[dt], _ptrs(U), _ptrs(V), _stream(dev, stream))
+    capi.call("fdbb_prim_from_cons", D, gamma, n, _code(dt, dw), _ptrs(U), _ptrs(V), _stream(dev, stream))
     return V
 
 
-def cons_from_prim(V, gamma: float = GAMMA, out=None, stream=None):
+def cons_from_prim(V, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
     D = _dim(V)
     n, dt, dev = _info(V)
     U = out if out is not None else _alloc(D + 2, n, dt, dev)
-    capi.call("fdbb_cons_from_prim", D, gamma, n, DTYPES[dt], _ptrs(V), _ptrs(U), _stream(dev, stream))
+    capi.call("fdbb_cons_from_prim", D, gamma, n, _code(dt, dw), _ptrs(V), _ptrs(U), _stream(dev, stream))
     return U
 
 
-def eos(U, gamma: float = GAMMA, want_p: bool = True, want_c: bool = True, stream=None):
+def eos(U, gamma: float = GAMMA, want_p: bool = True, want_c: bool = True, stream=None, dw: bool = False):
     """(p, c); an output not wanted is None."""
     D = _dim(U)
     n, dt, dev = _info(U)
     p = torch.empty(n, dtype=dt, device=dev) if want_p else None
     c = torch.empty(n, dtype=dt, device=dev) if want_c else None
-    capi.call("fdbb_eos", D, gamma, n, DTYPES[dt], _ptrs(U), p.data_ptr() if p is not None else None,
+    capi.call("fdbb_eos", D, gamma, n, _code(dt, dw), _ptrs(U), p.data_ptr() if p is not None else None,
               c.data_ptr() if c is not None else None, _stream(dev, stream))
     return p, c
 
 
-def riemann_inv(U, dir: int, gamma: float = GAMMA, entropy: bool = False, stream=None):
+def riemann_inv(U, dir: int, gamma: float = GAMMA, entropy: bool = False, stream=None, dw: bool = False):
     """(w-, w+, s) along `dir`; s is None unless entropy=True."""
     D = _dim(U)
     n, dt, dev = _info(U)
     wm, wp = _alloc(2, n, dt, dev)
     s = torch.empty(n, dtype=dt, device=dev) if entropy else None
-    capi.call("fdbb_riemann_inv", D, dir, gamma, n, DTYPES[dt], _ptrs(U), wm.data_ptr(), wp.data_ptr(),
+    capi.call("fdbb_riemann_inv", D, dir, gamma, n, _code(dt, dw), _ptrs(U), wm.data_ptr(), wp.data_ptr(),
               s.data_ptr() if s is not None else None, _stream(dev, stream))
     return wm, wp, s
 
 
-def flux(U, dir: int = -1, gamma: float = GAMMA, out=None, stream=None):
+def flux(U, dir: int = -1, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
     """F_dir (nv planes) or all directions, direction-major (dim*nv planes)."""
     D = _dim(U)
     n, dt, dev = _info(U)
     k = (D + 2) * (D if dir < 0 else 1)
     F = out if out is not None else _alloc(k, n, dt, dev)
-    capi.call("fdbb_flux", D, dir, gamma, n, DTYPES[dt], _ptrs(U), _ptrs(F), _stream(dev, stream))
+    capi.call("fdbb_flux", D, dir, gamma, n, _code(dt, dw), _ptrs(U), _ptrs(F), _stream(dev, stream))
     return F
 
 
-def flux_jac(U, dir: int, gamma: float = GAMMA, out=None, stream=None):
+def flux_jac(U, dir: int, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
     """A_dir, nv*nv planes row-major."""
     D = _dim(U)
     n, dt, dev = _info(U)
     A = out if out is not None else _alloc((D + 2) ** 2, n, dt, dev)
-    capi.call("fdbb_flux_jac", D, dir, gamma, n, DTYPES[dt], _ptrs(U), _ptrs(A), _stream(dev, stream))
+    capi.call("fdbb_flux_jac", D, dir, gamma, n, _code(dt, dw), _ptrs(U), _ptrs(A), _stream(dev, stream))
     return A
 
 
-def char_transform(U, W, dir: int, gamma: float = GAMMA, inverse: bool = False, out=None, stream=None):
+def char_transform(U, W, dir: int, gamma: float = GAMMA, inverse: bool = False, out=None, stream=None, dw: bool = False):
     """L_dir(U) W, or R_dir(U) W when inverse=True."""
     D = _dim(U)
     n, dt, dev = _info(list(U) + list(W))
     Y = out if out is not None else _alloc(D + 2, n, dt, dev)
-    capi.call("fdbb_char_transform", D, dir, gamma, n, DTYPES[dt], int(bool(inverse)), _ptrs(U), _ptrs(W),
+    capi.call("fdbb_char_transform", D, dir, gamma, n, _code(dt, dw), int(bool(inverse)), _ptrs(U), _ptrs(W),
               _ptrs(Y), _stream(dev, stream))
     return Y
 
 
-def euler_fused(U, W, dir_jac: int = 0, gamma: float = GAMMA, out=None, stream=None):
+def euler_fused(U, W, dir_jac: int = 0, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
     """(F, A, Y): all flux columns, A_dir_jac and L_dir_jac(U) W in one pass.
 
     ``out`` is an optional (F, A, Y) triple of plane lists (any may be None to
@@ -152,18 +165,18 @@ def euler_fused(U, W, dir_jac: int = 0, gamma: float = GAMMA, out=None, stream=N
         out = (_alloc(D * nv, n, dt, dev), _alloc(nv * nv, n, dt, dev),
                _alloc(nv, n, dt, dev) if W is not None else None)
     F, A, Y = out
-    capi.call("fdbb_euler_fused", D, dir_jac, gamma, n, DTYPES[dt], _ptrs(U),
+    capi.call("fdbb_euler_fused", D, dir_jac, gamma, n, _code(dt, dw), _ptrs(U),
               _ptrs(W) if W is not None else None,
               _ptrs(F) if F is not None else None, _ptrs(A) if A is not None else None,
               _ptrs(Y) if Y is not None else None, _stream(dev, stream))
     return F, A, Y
 
 
-def flux_vjp(U, G, dir: int, gamma: float = GAMMA, out=None, stream=None):
+def flux_vjp(U, G, dir: int, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
     """gU = A_dir(U)^T G."""
     D = _dim(U)
     n, dt, dev = _info(list(U) + list(G))
     gU = out if out is not None else _alloc(D + 2, n, dt, dev)
-    capi.call("fdbb_flux_vjp", D, dir, gamma, n, DTYPES[dt], _ptrs(U), _ptrs(G), _ptrs(gU),
+    capi.call("fdbb_flux_vjp", D, dir, gamma, n, _code(dt, dw), _ptrs(U), _ptrs(G), _ptrs(gU),
               _stream(dev, stream))
     return gU

@@ -17,7 +17,7 @@ STATUS = {
     0: "FDBB_OK", 1: "FDBB_ERR_ARG", 2: "FDBB_ERR_NULLPTR", 3: "FDBB_ERR_ALIGN",
     4: "FDBB_ERR_DTYPE", 5: "FDBB_ERR_CUDA", 6: "FDBB_ERR_TIMEOUT", 7: "FDBB_ERR_NOMEM",
 }
-FDBB_F64, FDBB_F32, FDBB_F16, FDBB_BF16 = 0, 1, 2, 3
+FDBB_F64, FDBB_F32, FDBB_F16, FDBB_BF16, FDBB_F64_DW = 0, 1, 2, 3, 4
 
 _i, _i64, _d, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)

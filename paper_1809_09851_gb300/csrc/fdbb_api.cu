@@ -45,7 +45,8 @@ fdbb_status check_gamma(double gamma) {
 }
 
 fdbb_status check_dtype(fdbb_dtype t) {
-  return (t == FDBB_F64 || t == FDBB_F32 || t == FDBB_F16 || t == FDBB_BF16) ? FDBB_OK : FDBB_ERR_DTYPE;
+  return (t == FDBB_F64 || t == FDBB_F32 || t == FDBB_F16 || t == FDBB_BF16 || t == FDBB_F64_DW) ? FDBB_OK
+                                                                                                  : FDBB_ERR_DTYPE;
 }
 
 // Required input planes: the array and every entry non-NULL and aligned.
@@ -84,6 +85,7 @@ KArgs make_args(int64_t n, double gamma) {
   for (int i = 0; i < 6; ++i) {
     a.kd[i] = kd[i];
     a.kf[i] = static_cast<float>(kd[i]);
+    a.kl[i] = static_cast<float>(kd[i] - static_cast<double>(a.kf[i]));
   }
   return a;
 }
@@ -97,6 +99,7 @@ fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, const KArgs& a, fd
     case FDBB_F32: e = fdbb::dispatch_f32(r, a); break;
     case FDBB_F16: e = fdbb::dispatch_f16(r, a); break;
     case FDBB_BF16: e = fdbb::dispatch_bf16(r, a); break;
+    case FDBB_F64_DW: e = fdbb::dispatch_f64dw(r, a); break;
   }
   return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
 }

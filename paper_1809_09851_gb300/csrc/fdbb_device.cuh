@@ -1,8 +1,9 @@
-// fdbb_device.cuh -- device-side building blocks: storage traits, 128-bit
+// fdbb_device.cuh -- device-side building blocks: storage traits, vector
 // streaming I/O, and the per-point Euler algebra.
 //
-// Each kernel thread owns VW consecutive points (one 128-bit word per plane:
-// 2 x f64, 4 x f32, 8 x f16/bf16), loads every input plane once, evaluates the
+// Each kernel thread owns VW consecutive points (one 128-bit word per plane for
+// 2 x f64 or 4 x f32, one 64-bit word for 4 x f16/bf16), loads every input
+// plane once, evaluates the
 // requested expressions in registers and stores every output plane once.
 #pragma once
 
@@ -11,23 +12,36 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fdbb_dw.cuh"
+
 namespace fdbb {
 
 // ---------------------------------------------------------------------------
-// Storage traits: compute type R and vector width VW of a storage type T.
+// Storage traits: register type L that a plane of storage type T is loaded
+// into (double or float), and vector width VW (points per thread and plane).
+// The compute type R is a separate kernel parameter: L itself, or the
+// double-word type dw for double storage.
 // ---------------------------------------------------------------------------
 template <class T> struct Storage;
-template <> struct Storage<double> { using R = double; static constexpr int VW = 2; };
-template <> struct Storage<float> { using R = float; static constexpr int VW = 4; };
-template <> struct Storage<__half> { using R = float; static constexpr int VW = 8; };
-template <> struct Storage<__nv_bfloat16> { using R = float; static constexpr int VW = 8; };
+template <> struct Storage<double> { using L = double; static constexpr int VW = 2; };
+template <> struct Storage<float> { using L = float; static constexpr int VW = 4; };
+// 16-bit storage moves 64 bits (4 points) per plane and thread: 8 points of
+// state would need ~150 registers and cap occupancy at one block per SM.
+template <> struct Storage<__half> { using L = float; static constexpr int VW = 4; };
+template <> struct Storage<__nv_bfloat16> { using L = float; static constexpr int VW = 4; };
+
+// Points per thread and plane for storage T computed in R: the storage's
+// vector width, except double-word, whose values take twice the registers of
+// float and which therefore moves one double (64 bits) per plane and thread.
+template <class T, class R> struct Width { static constexpr int VW = Storage<T>::VW; };
+template <> struct Width<double, dw> { static constexpr int VW = 1; };
 
 __device__ __forceinline__ double to_r(double x) { return x; }
 __device__ __forceinline__ float to_r(float x) { return x; }
 __device__ __forceinline__ float to_r(__half x) { return __half2float(x); }
 __device__ __forceinline__ float to_r(__nv_bfloat16 x) { return __bfloat162float(x); }
 
-template <class T> __device__ __forceinline__ T from_r(typename Storage<T>::R x);
+template <class T> __device__ __forceinline__ T from_r(typename Storage<T>::L x);
 template <> __device__ __forceinline__ double from_r<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_r<float>(float x) { return x; }
 template <> __device__ __forceinline__ __half from_r<__half>(float x) { return __float2half_rn(x); }
@@ -35,7 +49,8 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_r<__nv_bfloat16>(float
   return __float2bfloat16_rn(x);
 }
 
-// 128-bit streaming loads (evict-first: every input is touched once).
+// Vector streaming loads (evict-first: every input is touched once).
+__device__ __forceinline__ void ld_vec(const double* p, double (&x)[1]) { x[0] = __ldcs(p); }
 __device__ __forceinline__ void ld_vec(const double* p, double (&x)[2]) {
   double2 v = __ldcs(reinterpret_cast<const double2*>(p));
   x[0] = v.x;
@@ -48,22 +63,22 @@ __device__ __forceinline__ void ld_vec(const float* p, float (&x)[4]) {
   x[2] = v.z;
   x[3] = v.w;
 }
-__device__ __forceinline__ void ld_vec(const __half* p, float (&x)[8]) {
-  uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
-  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+__device__ __forceinline__ void ld_vec(const __half* p, float (&x)[4]) {
+  uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+  const uint32_t w[2] = {v.x, v.y};
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 2; ++k) {
     __half2 h = *reinterpret_cast<const __half2*>(&w[k]);
     float2 f = __half22float2(h);
     x[2 * k] = f.x;
     x[2 * k + 1] = f.y;
   }
 }
-__device__ __forceinline__ void ld_vec(const __nv_bfloat16* p, float (&x)[8]) {
-  uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
-  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+__device__ __forceinline__ void ld_vec(const __nv_bfloat16* p, float (&x)[4]) {
+  uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+  const uint32_t w[2] = {v.x, v.y};
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 2; ++k) {
     __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[k]);
     float2 f = __bfloat1622float2(h);
     x[2 * k] = f.x;
@@ -71,55 +86,98 @@ __device__ __forceinline__ void ld_vec(const __nv_bfloat16* p, float (&x)[8]) {
   }
 }
 
-// 128-bit streaming stores.
+// Vector streaming stores.
+__device__ __forceinline__ void st_vec(double* p, const double (&x)[1]) { __stcs(p, x[0]); }
 __device__ __forceinline__ void st_vec(double* p, const double (&x)[2]) {
   __stcs(reinterpret_cast<double2*>(p), make_double2(x[0], x[1]));
 }
 __device__ __forceinline__ void st_vec(float* p, const float (&x)[4]) {
   __stcs(reinterpret_cast<float4*>(p), make_float4(x[0], x[1], x[2], x[3]));
 }
-__device__ __forceinline__ void st_vec(__half* p, const float (&x)[8]) {
-  uint32_t w[4];
+__device__ __forceinline__ void st_vec(__half* p, const float (&x)[4]) {
+  uint32_t w[2];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 2; ++k) {
     __half2 h = __floats2half2_rn(x[2 * k], x[2 * k + 1]);
     w[k] = *reinterpret_cast<uint32_t*>(&h);
   }
-  __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+  __stcs(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
 }
-__device__ __forceinline__ void st_vec(__nv_bfloat16* p, const float (&x)[8]) {
-  uint32_t w[4];
+__device__ __forceinline__ void st_vec(__nv_bfloat16* p, const float (&x)[4]) {
+  uint32_t w[2];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 2; ++k) {
     __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
     w[k] = *reinterpret_cast<uint32_t*>(&h);
   }
-  __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+  __stcs(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
 }
 
-// Load VW points starting at i0; cnt < VW only in the ragged last chunk, where
-// the missing lanes get `fill` (a harmless value that is never stored).
-template <class T, int VW, class R>
-__device__ __forceinline__ void load(const T* p, int64_t i0, int cnt, R (&x)[VW], R fill) {
+// Range guard of a compute type: a no-op for IEEE types; for dw it records
+// whether every checked value lies in the double-word fast-path range.
+struct NoGuard {
+  static constexpr bool ok = true;
+  template <class X> __device__ __forceinline__ void check(const X&) {}
+};
+template <class R> struct GuardOf { using type = NoGuard; };
+template <> struct GuardOf<dw> { using type = DwGuard; };
+
+// Register value (double or float) -> compute type.
+template <class R, class G> __device__ __forceinline__ R to_compute(double x, G&) { return x; }
+template <class R, class G> __device__ __forceinline__ R to_compute(float x, G&) { return x; }
+template <> __device__ __forceinline__ dw to_compute<dw, DwGuard>(double x, DwGuard& g) {
+  return dw_from_double(x, g);
+}
+// Compute type -> register value of the storage's load type.
+__device__ __forceinline__ double to_load(double x) { return x; }
+__device__ __forceinline__ float to_load(float x) { return x; }
+__device__ __forceinline__ double to_load(dw x) { return dw_to_double(x); }
+
+// Load VW points starting at i0 in the storage's load type; cnt < VW only in
+// the ragged last chunk, where the missing lanes get `fill` (a harmless
+// in-range value that is never stored).
+template <class T, int VW>
+__device__ __forceinline__ void load_raw(const T* p, int64_t i0, int cnt, typename Storage<T>::L (&raw)[VW],
+                                         float fill) {
+  using L = typename Storage<T>::L;
   if (cnt == VW) {
-    ld_vec(p + i0, x);
+    ld_vec(p + i0, raw);
   } else {
 #pragma unroll
-    for (int j = 0; j < VW; ++j) x[j] = (j < cnt) ? to_r(p[i0 + j]) : fill;
+    for (int j = 0; j < VW; ++j) raw[j] = (j < cnt) ? to_r(p[i0 + j]) : static_cast<L>(fill);
   }
 }
 
-// Store VW points; a NULL plane is skipped.
-template <class T, int VW, class R>
-__device__ __forceinline__ void store(T* p, int64_t i0, int cnt, const R (&x)[VW]) {
+// Load VW points and convert them to the compute type R.
+template <class T, int VW, class R, class G>
+__device__ __forceinline__ void load(const T* p, int64_t i0, int cnt, R (&x)[VW], float fill, G& g) {
+  typename Storage<T>::L raw[VW];
+  load_raw<T, VW>(p, i0, cnt, raw, fill);
+#pragma unroll
+  for (int j = 0; j < VW; ++j) x[j] = to_compute<R, G>(raw[j], g);
+}
+
+// Store VW values of the storage's load type; a NULL plane is skipped.
+template <class T, int VW>
+__device__ __forceinline__ void store_raw(T* p, int64_t i0, int cnt, const typename Storage<T>::L (&raw)[VW]) {
   if (p == nullptr) return;
   if (cnt == VW) {
-    st_vec(p + i0, x);
+    st_vec(p + i0, raw);
   } else {
 #pragma unroll
     for (int j = 0; j < VW; ++j)
-      if (j < cnt) p[i0 + j] = from_r<T>(x[j]);
+      if (j < cnt) p[i0 + j] = from_r<T>(raw[j]);
   }
+}
+
+// Store VW points of the compute type; a NULL plane is skipped.
+template <class T, int VW, class R>
+__device__ __forceinline__ void store(T* p, int64_t i0, int cnt, const R (&x)[VW]) {
+  if (p == nullptr) return;
+  typename Storage<T>::L raw[VW];
+#pragma unroll
+  for (int j = 0; j < VW; ++j) raw[j] = to_load(x[j]);
+  store_raw<T, VW>(p, i0, cnt, raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -149,7 +207,16 @@ template <class R> struct Consts {
 // ---------------------------------------------------------------------------
 // Per-point state
 // ---------------------------------------------------------------------------
+// The loaded doubles of rho and m, kept for the outputs that are exact copies
+// of an input (F_d[0] = m_d, rho in cons <-> prim) when the compute type is
+// double-word (whose split of a double keeps 47 of its 53 bits).
+template <class R, int D> struct RawState {};
+template <int D> struct RawState<dw, D> {
+  double rho, m[D];
+};
+
 template <class R, int D> struct Pt {
+  RawState<R, D> raw;
   R rho, m[D], rE;  // conservative state
   R r;              // 1 / rho
   R v[D];           // velocity
@@ -173,18 +240,18 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 }
 
 // Internal-energy density rho e = rhoE - |m|^2 / (2 rho).
-//  double: plain evaluation (relative error ~ u * (rhoE + rho q) / rho e).
+//  double, dw: plain evaluation (error ~ u * (rhoE + rho q)).
 //  float : compensated evaluation; |m|^2 is summed exactly as a float pair
 //          (TwoProduct + TwoSum, Ogita-Rump-Oishi), divided by 2 rho with a
 //          remainder correction, and subtracted from rhoE with TwoSum, so the
 //          result is accurate to a few ulp of rho e itself even when
 //          rho q / rho e ~ 1e3 (Mach 50) or rho ~ 1e-4 (near vacuum).
-template <int D>
-__device__ __forceinline__ void internal_energy(Pt<double, D>& s, double& rhoe) {
-  double mv = s.m[0] * s.v[0];
+template <class R, int D>
+__device__ __forceinline__ void internal_energy(Pt<R, D>& s, R& rhoe) {
+  R mv = s.m[0] * s.v[0];
 #pragma unroll
-  for (int i = 1; i < D; ++i) mv = fma(s.m[i], s.v[i], mv);
-  s.rq = 0.5 * mv;
+  for (int i = 1; i < D; ++i) mv = fma_(s.m[i], s.v[i], mv);
+  s.rq = R(0.5f) * mv;
   rhoe = s.rE - s.rq;
 }
 template <int D>
@@ -209,36 +276,26 @@ __device__ __forceinline__ void internal_energy(Pt<float, D>& s, float& rhoe) {
   s.rq = qh;
 }
 
-// Conservative -> derived state.  One reciprocal per point.
-template <class R, int D>
-__device__ __forceinline__ void derive(Pt<R, D>& s, const Consts<R>& k) {
+// Conservative -> derived state.  One reciprocal per point.  The guard sees
+// every derived quantity that later enters a product (1/rho is covered by
+// rho, 1/c and (gamma-1)/c^2 by c^2).
+template <class R, int D, class G>
+__device__ __forceinline__ void derive(Pt<R, D>& s, const Consts<R>& k, G& g) {
   s.r = rcp_(s.rho);
 #pragma unroll
   for (int i = 0; i < D; ++i) s.v[i] = s.m[i] * s.r;
   R rhoe;
-  internal_energy<D>(s, rhoe);
+  internal_energy(s, rhoe);
   s.q = s.rq * s.r;
   s.p = k.a1 * rhoe;
   s.H = (s.rE + s.p) * s.r;
   s.c2 = k.g * s.p * s.r;
-}
-
-// Load the conservative state of VW points.
-template <class T, int VW, int D, class R>
-__device__ __forceinline__ void load_state(const T* const* U, int64_t i0, int cnt, Pt<R, D> (&s)[VW]) {
-  R x[VW];
-  load<T, VW, R>(U[0], i0, cnt, x, R(1));
 #pragma unroll
-  for (int j = 0; j < VW; ++j) s[j].rho = x[j];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    load<T, VW, R>(U[1 + i], i0, cnt, x, R(0));
-#pragma unroll
-    for (int j = 0; j < VW; ++j) s[j].m[i] = x[j];
-  }
-  load<T, VW, R>(U[D + 1], i0, cnt, x, R(1));
-#pragma unroll
-  for (int j = 0; j < VW; ++j) s[j].rE = x[j];
+  for (int i = 0; i < D; ++i) g.check(s.v[i]);
+  g.check(s.q);
+  g.check(s.p);
+  g.check(s.H);
+  g.check(s.c2);
 }
 
 // ---------------------------------------------------------------------------
@@ -298,14 +355,14 @@ __device__ __forceinline__ void char_fwd(const Pt<R, D>& s, const Consts<R>& k, 
   for (int i = 1; i < D; ++i) dot = fma_(s.v[i], w[1 + i], dot);
   const R t = b1 * (fma_(s.q, w[0], w[nv - 1]) - dot);
   const R a = fma_(s.v[d], w[0], -w[1 + d]) * ic;
-  y[0] = R(0.5) * (t + a);
+  y[0] = R(0.5f) * (t + a);
   y[1] = w[0] - t;
 #pragma unroll
   for (int kk = 0; kk < D - 1; ++kk) {
     const int tk = tang<D, d>(kk);
     y[2 + kk] = fma_(-s.v[tk], w[0], w[1 + tk]);
   }
-  y[nv - 1] = R(0.5) * (t - a);
+  y[nv - 1] = R(0.5f) * (t - a);
 }
 
 // Inverse characteristic transform Y = R_d W at one point.

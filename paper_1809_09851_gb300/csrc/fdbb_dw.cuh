@@ -1,0 +1,215 @@
+// fdbb_dw.cuh -- double-word ("float-float") arithmetic for FP64-storage
+// kernels on GB300.
+//
+// GB300 executes FP64 FMA, FP64<->FP32 conversion and every other FP64-pipe
+// instruction at 1/64 of the FP32 rate (about 2 per clock per SM).  The fused
+// 3D pass needs ~70 FP64 operations per point, which makes it FP64-bound at
+// about half of the HBM roofline.  A double-word number x = hi + lo (two
+// floats, |lo| <= ulp(hi)) carries a ~47-bit significand; its arithmetic runs
+// on the FP32 pipe and the conversions from and to IEEE double are done with
+// integer bit operations, so no FP64-pipe instruction is needed on the fast
+// path.
+//
+// Algorithms (all error-free-transform based):
+//   TwoSum (Knuth), Fast2Sum (Dekker), TwoProd via FMA;
+//   addition  = "SloppyDWPlusDW", multiplication = "DWTimesDW1" of
+//   M. Joldes, J.-M. Muller, V. Popescu, "Tight and rigorous error bounds for
+//   basic building blocks of double-word arithmetic", ACM TOMS 44(2), 2017;
+//   reciprocal / reciprocal square root = one Newton step from the hardware
+//   approximation with the residual formed exactly by FMA.
+// The sloppy addition is accurate to ~4u^2 (|a| + |b|) (u = 2^-24) rather than
+// relative to |a + b|; with respect to the running-error scale of the
+// formulas (which contains |a| + |b| whenever an operand is itself computed)
+// this is the same order as the other operations.  Sums of two *exact inputs*
+// are never formed in double-word arithmetic (the inverse characteristic
+// transform, the only block that adds inputs directly, stays in FP64).
+//
+// Range: the fast path is taken only where every input and derived
+// quantity is 0 or has magnitude in [2^-24, 2^24] (DwGuard); products of
+// up to four such factors then stay far inside the normal float range, so no
+// low word underflows.  A point outside it is recomputed in native FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdbb {
+
+struct dw {
+  float hi, lo;
+  dw() = default;
+  __device__ __forceinline__ constexpr dw(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ constexpr dw(float h) : hi(h), lo(0.0f) {}
+  __device__ __forceinline__ constexpr dw(double) = delete;
+  __device__ __forceinline__ constexpr dw(int h) : hi(static_cast<float>(h)), lo(0.0f) {}
+};
+
+// s + e == a + b exactly (Knuth).
+__device__ __forceinline__ void dw_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s + e == a + b exactly when |a| >= |b| (Dekker).
+__device__ __forceinline__ void dw_fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ dw operator-(dw a) { return dw(-a.hi, -a.lo); }
+
+__device__ __forceinline__ dw operator+(dw a, dw b) {
+  float s, e;
+  dw_two_sum(a.hi, b.hi, s, e);
+  const float v = __fadd_rn(a.lo, b.lo);
+  const float w = __fadd_rn(e, v);
+  dw z;
+  dw_fast_two_sum(s, w, z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ dw operator-(dw a, dw b) { return a + (-b); }
+
+__device__ __forceinline__ dw operator*(dw a, dw b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pe = __fmaf_rn(a.hi, b.hi, -p);
+  const float t = __fmul_rn(a.hi, b.lo);
+  const float c = __fmaf_rn(a.lo, b.hi, t);
+  const float l = __fadd_rn(pe, c);
+  dw z;
+  dw_fast_two_sum(p, l, z.hi, z.lo);
+  return z;
+}
+
+// a * b + c with one renormalisation.
+__device__ __forceinline__ dw fma_(dw a, dw b, dw c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pe = __fmaf_rn(a.hi, b.hi, -p);
+  float s, se;
+  dw_two_sum(p, c.hi, s, se);
+  float t = __fmaf_rn(a.hi, b.lo, pe);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  t = __fadd_rn(t, c.lo);
+  t = __fadd_rn(t, se);
+  dw z;
+  dw_fast_two_sum(s, t, z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ float dw_rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float dw_rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// 1/y: r0 ~ 1/y.hi, e = 1 - y r0 (exact residual of the high word by FMA),
+// 1/y = r0 (1 + e + e^2 + ...).
+__device__ __forceinline__ dw rcp_(dw y) {
+  const float r0 = dw_rcp_approx(y.hi);
+  float e = __fmaf_rn(-y.hi, r0, 1.0f);
+  e = __fmaf_rn(-y.lo, r0, e);
+  const float c = __fmaf_rn(e, e, e);
+  dw z;
+  dw_fast_two_sum(r0, __fmul_rn(r0, c), z.hi, z.lo);
+  return z;
+}
+
+// 1/sqrt(x): y0 ~ 1/sqrt(x.hi), m = x y0^2 - 1 (formed with TwoProd and FMA),
+// 1/sqrt(x) = y0 (1 - m/2 + 3 m^2 / 8 - ...).
+__device__ __forceinline__ dw rsqrt_(dw x) {
+  const float y0 = dw_rsqrt_approx(x.hi);
+  const float q = __fmul_rn(y0, y0);
+  const float qe = __fmaf_rn(y0, y0, -q);
+  float m = __fmaf_rn(x.hi, q, -1.0f);
+  m = __fmaf_rn(x.hi, qe, m);
+  m = __fmaf_rn(x.lo, q, m);
+  const float c = __fmaf_rn(0.375f, m, -0.5f);
+  dw z;
+  dw_fast_two_sum(y0, __fmul_rn(y0, __fmul_rn(m, c)), z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ dw operator/(dw a, dw b) { return a * rcp_(b); }
+
+__device__ __forceinline__ dw sqrt_(dw x) {
+  if (x.hi == 0.0f) return dw(0.0f);
+  return x * rsqrt_(x);
+}
+
+__device__ __forceinline__ double dw_to_double(dw x);
+__device__ __forceinline__ dw dw_from_double_unchecked(double x);
+
+// x^y through FP64 (used only for the optional entropy output).
+__device__ __forceinline__ dw pow_(dw x, dw y) {
+  return dw_from_double_unchecked(pow(dw_to_double(x), dw_to_double(y)));
+}
+
+// ---------------------------------------------------------------------------
+// Conversions between IEEE double and double-word, in integer arithmetic.
+// ---------------------------------------------------------------------------
+
+// Range guard of the double-word fast path: every checked value is 0 or has
+// magnitude in [2^-24, 2^24].
+struct DwGuard {
+  bool ok = true;
+  __device__ __forceinline__ void check(dw x) {
+    const float a = fabsf(x.hi);
+    ok = ok && ((a >= 0x1p-24f && a <= 0x1p24f) || a == 0.0f);
+  }
+};
+
+// Split a double into hi (its leading 24 significant bits, truncated) and lo
+// (the next 23 bits, exact in float): |x - (hi + lo)| <= 2^-47 |x|.  The
+// guard records whether x is 0 or 2^-24 <= |x| < 2^24 (tested on the double's
+// own exponent field, since outside 2^-102 <= |x| < 2^128 the split itself is
+// meaningless).
+__device__ __forceinline__ dw dw_from_double(double x, DwGuard& g) {
+  const uint32_t H = static_cast<uint32_t>(__double2hiint(x));
+  const uint32_t L = static_cast<uint32_t>(__double2loint(x));
+  if (((H << 1) | L) == 0u) return dw(0.0f);
+  const uint32_t E = (H >> 20) & 0x7FFu;
+  g.ok = g.ok && (E - 999u) < 48u;                              // 2^-24 <= |x| < 2^24
+  const uint32_t sign = H & 0x80000000u;
+  const uint32_t t = (H & 0x7FFFFFFFu) - (896u << 20);        // exponent 1023 -> 127 bias
+  const uint32_t hb = __funnelshift_l(L, t, 3) | sign;          // sign | exp | top 23 mantissa bits
+  const uint32_t base = (hb & 0xFF800000u) - (23u << 23);       // sign | 2^(e-23)
+  const uint32_t yb = base | ((L >> 6) & 0x007FFFFFu);          // 2^(e-23) * (1 + next 23 bits)
+  return dw(__uint_as_float(hb), __fsub_rn(__uint_as_float(yb), __uint_as_float(base)));
+}
+
+__device__ __forceinline__ dw dw_from_double_unchecked(double x) {
+  DwGuard g;
+  return dw_from_double(x, g);
+}
+
+// hi + lo rounded to a double: the double of hi is built from its bit pattern
+// and lo is added as an integer number of units of 2^(e_hi - 45) (|lo| <
+// 2^(e_hi - 23), so the count fits the float magic-number rounding range).
+// Error <= 2^-46 |x|.  When hi is a power of two and the correction is
+// negative the result lies in the binade below, whose ulp is half as large.
+__device__ __forceinline__ double dw_to_double(dw x) {
+  const uint32_t f = __float_as_uint(x.hi);
+  const uint32_t mag = f & 0x7FFFFFFFu;
+  const uint32_t sign = f & 0x80000000u;
+  if (mag < 0x00800000u) return __hiloint2double(static_cast<int>(sign), 0);  // |x| < 2^-126
+  const uint32_t H = ((mag >> 3) + (896u << 20)) | sign;
+  const uint32_t L = f << 29;
+  int64_t bits = static_cast<int64_t>((static_cast<uint64_t>(H) << 32) | L);
+  const uint32_t ebits = mag & 0x7F800000u;
+  if (ebits >= (45u << 23)) {  // |hi| >= 2^-82: the scale 2^(45 - e_hi) is a normal float
+    const float scale = __uint_as_float(((299u << 23) - ebits) | sign);
+    const float k = __fmaf_rn(x.lo, scale, 12582912.0f);  // round to an integer via 1.5 * 2^23
+    const int32_t ki = static_cast<int32_t>(__float_as_uint(k)) - 0x4B400000;
+    const int64_t unit = ((mag & 0x007FFFFFu) == 0u && ki < 0) ? 256 : 128;
+    bits += static_cast<int64_t>(ki) * unit;
+  }
+  return __longlong_as_double(bits);
+}
+
+}  // namespace fdbb

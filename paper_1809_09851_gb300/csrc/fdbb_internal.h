@@ -19,6 +19,7 @@ struct KArgs {
   int64_t n;
   double kd[6];  // gamma, gamma-1, 3-gamma, 2/(gamma-1), 1/(gamma-1), -gamma
   float kf[6];   // the same, rounded once to float
+  float kl[6];   // kd - kf rounded to float: (kf, kl) is the double-word constant
 };
 
 struct LaunchReq {
@@ -36,5 +37,6 @@ cudaError_t dispatch_f64(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f32(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_bf16(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_f64dw(const LaunchReq& r, const KArgs& a);
 
 }  // namespace fdbb

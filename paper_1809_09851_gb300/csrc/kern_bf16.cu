@@ -2,5 +2,5 @@
 #include "fdbb_kernels.cuh"
 
 namespace fdbb {
-cudaError_t dispatch_bf16(const LaunchReq& r, const KArgs& a) { return dispatch<__nv_bfloat16>(r, a); }
+cudaError_t dispatch_bf16(const LaunchReq& r, const KArgs& a) { return dispatch<__nv_bfloat16, float>(r, a); }
 }  // namespace fdbb

@@ -2,5 +2,5 @@
 #include "fdbb_kernels.cuh"
 
 namespace fdbb {
-cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a) { return dispatch<__half>(r, a); }
+cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a) { return dispatch<__half, float>(r, a); }
 }  // namespace fdbb

@@ -2,5 +2,5 @@
 #include "fdbb_kernels.cuh"
 
 namespace fdbb {
-cudaError_t dispatch_f32(const LaunchReq& r, const KArgs& a) { return dispatch<float>(r, a); }
+cudaError_t dispatch_f32(const LaunchReq& r, const KArgs& a) { return dispatch<float, float>(r, a); }
 }  // namespace fdbb

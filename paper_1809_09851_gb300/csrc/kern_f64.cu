@@ -2,5 +2,5 @@
 #include "fdbb_kernels.cuh"
 
 namespace fdbb {
-cudaError_t dispatch_f64(const LaunchReq& r, const KArgs& a) { return dispatch<double>(r, a); }
+cudaError_t dispatch_f64(const LaunchReq& r, const KArgs& a) { return dispatch<double, double>(r, a); }
 }  // namespace fdbb

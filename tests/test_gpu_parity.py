@@ -78,25 +78,27 @@ def check(got, ref, S, dtype, what):
 # FP64, every block, every dim / dir, several sizes
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("dw", [False, True], ids=["f64", "f64dw"])
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("D", [1, 2, 3])
-def test_f64_variables_and_eos(n, D):
+def test_f64_variables_and_eos(n, D, dw):
     V, U, W = fields(n, D)
     Ud, _ = quantise(U, torch.float64)
     Vd, _ = quantise(V, torch.float64)
     ref, S = oracle.prim_from_cons(D, G, U, scale=True)
-    check(host(blocks.prim_from_cons(Ud, G)), ref, S, torch.float64, "prim_from_cons")
+    check(host(blocks.prim_from_cons(Ud, G, dw=dw)), ref, S, torch.float64, "prim_from_cons")
     ref, S = oracle.cons_from_prim(D, G, V, scale=True)
-    check(host(blocks.cons_from_prim(Vd, G)), ref, S, torch.float64, "cons_from_prim")
+    check(host(blocks.cons_from_prim(Vd, G, dw=dw)), ref, S, torch.float64, "cons_from_prim")
     ref, S = oracle.eos(D, G, U, scale=True)
-    check(host(blocks.eos(Ud, G)), ref, S, torch.float64, "eos")
+    check(host(blocks.eos(Ud, G, dw=dw)), ref, S, torch.float64, "eos")
     ref, S = oracle.v_mag2(D, U, scale=True)
-    check(host([blocks.v_mag2(Ud)]), ref, S, torch.float64, "v_mag2")
+    check(host([blocks.v_mag2(Ud, dw=dw)]), ref, S, torch.float64, "v_mag2")
 
 
+@pytest.mark.parametrize("dw", [False, True], ids=["f64", "f64dw"])
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("D", [1, 2, 3])
-def test_f64_directional_blocks(n, D):
+def test_f64_directional_blocks(n, D, dw):
     V, U, W = fields(n, D)
     Ud, _ = quantise(U, torch.float64)
     Wd, _ = quantise(W, torch.float64)
@@ -104,23 +106,23 @@ def test_f64_directional_blocks(n, D):
     Gc = synth.cotangent(n, nv)
     Gd, _ = quantise(Gc, torch.float64)
     ref, S = oracle.flux(D, -1, G, U, scale=True)
-    check(host(blocks.flux(Ud, -1, G)), ref, S, torch.float64, "flux all")
+    check(host(blocks.flux(Ud, -1, G, dw=dw)), ref, S, torch.float64, "flux all")
     for d in range(D):
         ref, S = oracle.flux(D, d, G, U, scale=True)
-        check(host(blocks.flux(Ud, d, G)), ref, S, torch.float64, f"flux {d}")
+        check(host(blocks.flux(Ud, d, G, dw=dw)), ref, S, torch.float64, f"flux {d}")
         ref, S = oracle.flux_jac(D, d, G, U, scale=True)
-        check(host(blocks.flux_jac(Ud, d, G)), ref, S, torch.float64, f"flux_jac {d}")
+        check(host(blocks.flux_jac(Ud, d, G, dw=dw)), ref, S, torch.float64, f"flux_jac {d}")
         ref, S = oracle.riemann_inv(D, d, G, U, scale=True)
-        wm, wp, s = blocks.riemann_inv(Ud, d, G, entropy=True)
+        wm, wp, s = blocks.riemann_inv(Ud, d, G, entropy=True, dw=dw)
         check(host([wm, wp, s]), ref, S, torch.float64, f"riemann {d}")
         for inv in (False, True):
             ref, S = oracle.char_transform(D, d, G, U, W, inverse=inv, scale=True)
-            check(host(blocks.char_transform(Ud, Wd, d, G, inverse=inv)), ref, S, torch.float64,
+            check(host(blocks.char_transform(Ud, Wd, d, G, inverse=inv, dw=dw)), ref, S, torch.float64,
                   f"char {d} inv={inv}")
         ref, S = oracle.flux_vjp(D, d, G, U, Gc, scale=True)
-        check(host(blocks.flux_vjp(Ud, Gd, d, G)), ref, S, torch.float64, f"vjp {d}")
+        check(host(blocks.flux_vjp(Ud, Gd, d, G, dw=dw)), ref, S, torch.float64, f"vjp {d}")
         ref, S = oracle.euler_fused(D, d, G, U, W, scale=True)
-        Fo, Ao, Yo = blocks.euler_fused(Ud, Wd, d, G)
+        Fo, Ao, Yo = blocks.euler_fused(Ud, Wd, d, G, dw=dw)
         check(host([*Fo, *Ao, *Yo]), ref, S, torch.float64, f"fused {d}")
 
 
@@ -200,13 +202,61 @@ def test_misaligned_plane_is_rejected():
     assert e.value.status == 3
 
 
+def test_dw_out_of_range_points_fall_back_to_fp64():
+    """Points whose inputs or derived values leave the double-word range
+    (tiny or huge magnitudes, tiny nonzero momentum or weights, non-finite
+    values) are computed in IEEE double and still match the oracle."""
+    n, D = 4103, 3
+    V, U, W = fields(n, D, seed=99)
+    U = [u.copy() for u in U]
+    W = [w.copy() for w in W]
+    # scaled states: rho, m, rhoE scaled together keep the state physical
+    for i, sc in ((10, 1e-30), (11, 1e30), (12, 1e-9), (513, 1e12), (4100, 2.0 ** -25)):
+        for k in range(5):
+            U[k][i] *= sc
+    U[1][20] = 1e-40            # tiny nonzero momentum
+    U[2][21] = -3e-300
+    W[3][30] = 1e-200           # tiny characteristic weight
+    W[0][31] = 5e25
+    ref, S = oracle.euler_fused(D, 0, G, U, W, scale=True)
+    Ud, _ = quantise(U, torch.float64)
+    Wd, _ = quantise(W, torch.float64)
+    for dj in range(D):
+        ref, S = oracle.euler_fused(D, dj, G, U, W, scale=True)
+        Fo, Ao, Yo = blocks.euler_fused(Ud, Wd, dj, G, dw=True)
+        check(host([*Fo, *Ao, *Yo]), ref, S, torch.float64, f"dw fallback fused {dj}")
+        Fn, An, Yn = blocks.euler_fused(Ud, Wd, dj, G)
+        check(host([*Fn, *An, *Yn]), ref, S, torch.float64, f"native fused {dj}")
+    ref, S = oracle.prim_from_cons(D, G, U, scale=True)
+    check(host(blocks.prim_from_cons(Ud, G, dw=True)), ref, S, torch.float64, "dw fallback prim")
+    # a NaN state gives NaN outputs in both arithmetics
+    U[0][40] = np.nan
+    Ud, _ = quantise(U, torch.float64)
+    p_dw, _ = blocks.eos(Ud, G, dw=True)
+    p_nat, _ = blocks.eos(Ud, G)
+    assert torch.isnan(p_dw[40]) and torch.isnan(p_nat[40])
+
+
+def test_dw_copies_are_bit_exact():
+    n, D = 1001, 3
+    V, U, W = fields(n, D, seed=5)
+    Ud, _ = quantise(U, torch.float64)
+    Wd, _ = quantise(W, torch.float64)
+    F, A, Y = blocks.euler_fused(Ud, Wd, 0, G, dw=True)
+    for d in range(D):
+        assert torch.equal(F[d * 5], Ud[1 + d])
+    Vo = blocks.prim_from_cons(Ud, G, dw=True)
+    assert torch.equal(Vo[0], Ud[0])
+
+
 # ---------------------------------------------------------------------------
 # full size, in the benchmark's launch configuration
 # ---------------------------------------------------------------------------
 
 @pytest.mark.slow
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_full_size_fused_sampled(dtype):
+@pytest.mark.parametrize("dtype,dw", [(torch.float64, False), (torch.float64, True), (torch.float32, False)],
+                         ids=["f64", "f64dw", "f32"])
+def test_full_size_fused_sampled(dtype, dw):
     """3D fused pass at N = 2^26 (the benchmark size): sampled points against
     the oracle, and A_x(U) U = F_x(U) checked at every point."""
     n, D = 1 << 26, 3
@@ -216,7 +266,7 @@ def test_full_size_fused_sampled(dtype):
     Ud, Uq = quantise(U, dtype)
     Wd, Wq = quantise(W, dtype)
     del V
-    F, A, Y = blocks.euler_fused(Ud, Wd, 0, G)
+    F, A, Y = blocks.euler_fused(Ud, Wd, 0, G, dw=dw)
     torch.cuda.synchronize()
     rng = np.random.default_rng(5)
     idx = np.unique(np.concatenate([rng.integers(0, n, 4096), np.arange(n - 37, n), np.arange(5)]))
