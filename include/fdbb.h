@@ -197,6 +197,64 @@ FDBB_API fdbb_status fdbb_flux_vjp(int dim, int dir, double gamma, int64_t n, fd
                           const void *const *U, const void *const *G, void *const *gU,
                           fdbb_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batched finite-volume steps (the serving workload).
+ *
+ * An explicit first-order finite-volume scheme with the Rusanov (local
+ * Lax-Friedrichs) numerical flux built on the paper's inviscid flux
+ * (section 2.2, "Inviscid Fluxes"), on periodic n^3 grids over [0,1]^3,
+ * dx = 1/n, cell (i,j,k) at plane index (k*n + j)*n + i:
+ *   Fh_d = (F_d(U_L) + F_d(U_R))/2 - s (U_R - U_L)/2,
+ *          s = max(|v_d,L| + c_L, |v_d,R| + c_R);
+ *   U_new = U - dt/dx * sum_d (Fh_{d,+1/2} - Fh_{d,-1/2});
+ *   dt    = CFL * dx / max_cells sum_d (|v_d| + c), from the state at the
+ *           start of the step.
+ * The paper has no finite-volume scheme; this one is the standard
+ * first-order scheme (Toro, ch. 10) driven by the paper's flux.
+ *
+ * Many grids of different sizes are advanced in one launch.  Each grid owns
+ * a range of a virtual cell index space that starts at a multiple of
+ * FDBB_FV_TILE and is FDBB_FV_TILE-padded; descriptors are passed in a HOST
+ * array (copied into the launch), sorted by cell_begin, at most
+ * FDBB_FV_MAX_GRIDS per call.  The per-grid maximum wave speed lives in a
+ * caller-owned DEVICE scratch array `smax` of the storage type, three slots
+ * per grid (smax[3*slot + 0..2]):
+ *   fdbb_fv_max_speed   reduces max sum_d(|v_d| + c) of U into slot `phase`
+ *                       (which the caller must have set to 0);
+ *   fdbb_fv_rusanov_step reads slot `phase`, writes U_new, reduces U_new's
+ *                       wave speed into slot (phase+1)%3 and clears slot
+ *                       (phase+2)%3.
+ * So a grid started with fdbb_fv_max_speed at phase 0 (slots zeroed) can be
+ * stepped any number of times by incrementing phase modulo 3 and swapping U
+ * and Unew between calls.  The maximum is order independent: a grid's
+ * results do not depend on the other grids in the launch.
+ * Storage: FDBB_F32 (float arithmetic with compensated internal energy) or
+ * FDBB_F64 (double).  Arguments are checked on the host (ranges sorted,
+ * aligned and inside vcells; planes non-NULL and aligned; Unew distinct from
+ * U); device pointers themselves cannot be checked and must be valid.
+ * Calls are asynchronous on `stream`; nothing is allocated.
+ * ------------------------------------------------------------------------ */
+#define FDBB_FV_TILE 256
+#define FDBB_FV_MAX_GRIDS 256
+
+typedef struct fdbb_fv_grid {
+  void *U[5];         /* state at the start of the step (rho, m_x, m_y, m_z, rhoE), n^3 each */
+  void *Unew[5];      /* state after the step (written by fdbb_fv_rusanov_step only)        */
+  double *dt_log;     /* optional device array: dt of this step stored at dt_log[step]      */
+  int64_t cell_begin; /* first virtual cell index, a multiple of FDBB_FV_TILE                */
+  int32_t n;          /* cells per side, 1 <= n <= 4096                                     */
+  int32_t slot;       /* wave-speed slots smax[3*slot .. 3*slot+2]                          */
+  int32_t phase;      /* step index modulo 3                                                */
+  int32_t step;       /* step index (position in dt_log)                                    */
+} fdbb_fv_grid;
+
+FDBB_API fdbb_status fdbb_fv_max_speed(int ngrids, const fdbb_fv_grid *grids, int64_t vcells,
+                                       double gamma, fdbb_dtype t, void *smax, fdbb_stream_t stream);
+
+FDBB_API fdbb_status fdbb_fv_rusanov_step(int ngrids, const fdbb_fv_grid *grids, int64_t vcells,
+                                          double gamma, double cfl, fdbb_dtype t, void *smax,
+                                          fdbb_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,6 +36,23 @@ SIGNATURES = {
     "fdbb_flux_vjp": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _vp],
 }
 
+
+
+class FvGrid(ctypes.Structure):
+    """struct fdbb_fv_grid (include/fdbb.h)."""
+    _fields_ = [("U", ctypes.c_void_p * 5), ("Unew", ctypes.c_void_p * 5), ("dt_log", ctypes.c_void_p),
+                ("cell_begin", ctypes.c_int64), ("n", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("phase", ctypes.c_int32), ("step", ctypes.c_int32)]
+
+
+FV_TILE = 256
+FV_MAX_GRIDS = 256
+_FVP = ctypes.POINTER(FvGrid)
+SIGNATURES.update({
+    "fdbb_fv_max_speed": [_i, _FVP, _i64, _d, _i, _vp, _vp],
+    "fdbb_fv_rusanov_step": [_i, _FVP, _i64, _d, _d, _i, _vp, _vp],
+})
+
 _lib = None
 
 

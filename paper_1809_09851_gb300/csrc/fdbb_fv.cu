@@ -1,0 +1,291 @@
+// fdbb_fv.cu -- batched explicit finite-volume steps (first-order Rusanov /
+// local Lax-Friedrichs) on many periodic n^3 grids in one persistent launch.
+//
+// Each grid occupies a range of a "virtual" cell index space, padded to a
+// multiple of FDBB_FV_TILE cells, so that a block-sized tile of virtual cells
+// always belongs to one grid.  The grid table (up to FDBB_FV_MAX_GRIDS
+// descriptors) travels in the kernel's parameter block.  A thread owns one
+// cell: it reads the cell and its six periodic neighbours, forms the six face
+// fluxes from the paper's inviscid flux (section 2.2) and writes the updated
+// state.  The time step of every grid comes from a per-grid maximum wave
+// speed kept in a caller-provided scratch array of three slots per grid:
+//   step s reads slot s%3 (max of the state at its start), reduces the new
+//   state's wave speed into slot (s+1)%3 with atomicMax, and clears slot
+//   (s+2)%3, which step s-1 read and step s+1 will fill.
+// The maximum is order independent, so a grid's results do not depend on
+// which other grids share the launch.
+#include <cmath>
+#include <cstdint>
+
+#include "fdbb.h"
+#include "fdbb_device.cuh"
+#include "fdbb_internal.h"
+
+namespace fdbb {
+namespace {
+
+constexpr int kFvThreads = FDBB_FV_TILE;
+
+struct FvArgs {
+  int ngrids;
+  int64_t vcells;    // virtual cells (sum of padded grid sizes)
+  double gamma, cfl;
+  void* smax;        // 3 slots per grid, storage type T
+  fdbb_fv_grid g[FDBB_FV_MAX_GRIDS];
+};
+
+// Grid owning virtual cell vc: the last descriptor with cell_begin <= vc
+// (descriptors are sorted by cell_begin).
+__device__ __forceinline__ int find_grid(const FvArgs& a, int64_t vc) {
+  int lo = 0, hi = a.ngrids - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.g[mid].cell_begin <= vc) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class T> __device__ __forceinline__ T ldg(const void* p, int64_t i) {
+  return __ldg(static_cast<const T*>(p) + i);
+}
+
+// Positive floating-point values order like their bit patterns.
+__device__ __forceinline__ void atomic_max_pos(float* p, float v) {
+  atomicMax(reinterpret_cast<int*>(p), __float_as_int(v));
+}
+__device__ __forceinline__ void atomic_max_pos(double* p, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <class T> __device__ __forceinline__ Consts<T> fv_consts(double g) {
+  const double a1 = g - 1.0;
+  return {T(g), T(a1), T(3.0 - g), T(2.0 / a1), T(1.0 / a1), T(-g)};
+}
+
+// Derived state of the cell at linear index c of the planes P.
+template <class T>
+__device__ __forceinline__ void cell_state(void* const* P, int64_t c, const Consts<T>& k, Pt<T, 3>& s) {
+  NoGuard g;
+  s.rho = ldg<T>(P[0], c);
+  s.m[0] = ldg<T>(P[1], c);
+  s.m[1] = ldg<T>(P[2], c);
+  s.m[2] = ldg<T>(P[3], c);
+  s.rE = ldg<T>(P[4], c);
+  derive(s, k, g);
+}
+
+template <class T> __device__ __forceinline__ T wave_speed_sum(const Pt<T, 3>& s) {
+  const T c = sqrt_(s.c2);
+  return (fabs(s.v[0]) + c) + (fabs(s.v[1]) + c) + (fabs(s.v[2]) + c);
+}
+
+// Rusanov face flux in direction d between left state L and right state R,
+// accumulated as  acc += sign * Fh.
+template <class T, int d>
+__device__ __forceinline__ void face_flux(const Pt<T, 3>& L, const Pt<T, 3>& R, T (&Fh)[5]) {
+  const T cL = sqrt_(L.c2), cR = sqrt_(R.c2);
+  const T sL = fabs(L.v[d]) + cL, sR = fabs(R.v[d]) + cR;
+  const T sm = sL > sR ? sL : sR;
+  const T uL[5] = {L.rho, L.m[0], L.m[1], L.m[2], L.rE};
+  const T uR[5] = {R.rho, R.m[0], R.m[1], R.m[2], R.rE};
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    Fh[q] = T(0.5f) * (flux_comp<3, d>(L, q) + flux_comp<3, d>(R, q)) - T(0.5f) * sm * (uR[q] - uL[q]);
+}
+
+template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_max_speed(const __grid_constant__ FvArgs a) {
+  __shared__ int s_grid;
+  const Consts<T> k = fv_consts<T>(a.gamma);
+  for (int64_t base = (int64_t)blockIdx.x * kFvThreads; base < a.vcells; base += (int64_t)gridDim.x * kFvThreads) {
+    if (threadIdx.x == 0) s_grid = find_grid(a, base);
+    __syncthreads();
+    const fdbb_fv_grid& g = a.g[s_grid];
+    __syncthreads();
+    const int64_t n = g.n, ncell = n * n * n;
+    const int64_t c = base + threadIdx.x - g.cell_begin;
+    T v = T(0);
+    if (c >= 0 && c < ncell) {
+      Pt<T, 3> s;
+      cell_state<T>(g.U, c, k, s);
+      v = wave_speed_sum(s);
+    }
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0 && v > T(0)) atomic_max_pos(static_cast<T*>(a.smax) + 3 * g.slot + g.phase, v);
+  }
+}
+
+template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_constant__ FvArgs a) {
+  __shared__ int s_grid;
+  const Consts<T> k = fv_consts<T>(a.gamma);
+  for (int64_t base = (int64_t)blockIdx.x * kFvThreads; base < a.vcells; base += (int64_t)gridDim.x * kFvThreads) {
+    if (threadIdx.x == 0) s_grid = find_grid(a, base);
+    __syncthreads();
+    const fdbb_fv_grid& g = a.g[s_grid];
+    __syncthreads();
+    T* smax = static_cast<T*>(a.smax) + 3 * g.slot;
+    const int n = g.n;
+    const int64_t ncell = (int64_t)n * n * n;
+    const int64_t c = base + threadIdx.x - g.cell_begin;
+    const int ph = g.phase, ph1 = ph == 2 ? 0 : ph + 1, ph2 = ph1 == 2 ? 0 : ph1 + 1;
+    const T dx = T(1) / T(n);
+    const T dt = T(a.cfl) * dx / smax[ph];
+    if (c == 0) {
+      smax[ph2] = T(0);  // read by the previous step, filled by the next one
+      if (g.dt_log) g.dt_log[g.step] = static_cast<double>(dt);
+    }
+    T v = T(0);
+    if (c < ncell) {
+      const int i = (int)(c % n), j = (int)((c / n) % n), kk = (int)(c / ((int64_t)n * n));
+      const int im = i == 0 ? n - 1 : i - 1, ip = i == n - 1 ? 0 : i + 1;
+      const int jm = j == 0 ? n - 1 : j - 1, jp = j == n - 1 ? 0 : j + 1;
+      const int km = kk == 0 ? n - 1 : kk - 1, kp = kk == n - 1 ? 0 : kk + 1;
+      auto idx = [n](int x, int y, int z) { return ((int64_t)z * n + y) * n + x; };
+      Pt<T, 3> C, M, P;
+      cell_state<T>(g.U, c, k, C);
+      T div[5] = {T(0), T(0), T(0), T(0), T(0)};
+      T Fm[5], Fp[5];
+      // x faces
+      cell_state<T>(g.U, idx(im, j, kk), k, M);
+      cell_state<T>(g.U, idx(ip, j, kk), k, P);
+      face_flux<T, 0>(M, C, Fm);
+      face_flux<T, 0>(C, P, Fp);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) div[q] = div[q] + (Fp[q] - Fm[q]);
+      // y faces
+      cell_state<T>(g.U, idx(i, jm, kk), k, M);
+      cell_state<T>(g.U, idx(i, jp, kk), k, P);
+      face_flux<T, 1>(M, C, Fm);
+      face_flux<T, 1>(C, P, Fp);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) div[q] = div[q] + (Fp[q] - Fm[q]);
+      // z faces
+      cell_state<T>(g.U, idx(i, j, km), k, M);
+      cell_state<T>(g.U, idx(i, j, kp), k, P);
+      face_flux<T, 2>(M, C, Fm);
+      face_flux<T, 2>(C, P, Fp);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) div[q] = div[q] + (Fp[q] - Fm[q]);
+      const T lam = dt / dx;
+      const T u0[5] = {C.rho, C.m[0], C.m[1], C.m[2], C.rE};
+      Pt<T, 3> N;
+      T un[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        un[q] = u0[q] - lam * div[q];
+        static_cast<T*>(g.Unew[q])[c] = un[q];
+      }
+      N.rho = un[0];
+      N.m[0] = un[1];
+      N.m[1] = un[2];
+      N.m[2] = un[3];
+      N.rE = un[4];
+      NoGuard ng;
+      derive(N, k, ng);
+      v = wave_speed_sum(N);
+    }
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0 && v > T(0)) atomic_max_pos(smax + ph1, v);
+  }
+}
+
+template <class T> int fv_blocks_per_sm(bool step) {
+  static const int bs = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fv_rusanov_step<T>, kFvThreads, 0) != cudaSuccess) b = 1;
+    return b > 0 ? b : 1;
+  }();
+  static const int bm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fv_max_speed<T>, kFvThreads, 0) != cudaSuccess) b = 1;
+    return b > 0 ? b : 1;
+  }();
+  return step ? bs : bm;
+}
+
+template <class T> cudaError_t fv_launch(const FvArgs& a, bool step, cudaStream_t s) {
+  const int64_t tiles = a.vcells / kFvThreads;
+  const int64_t cap = (int64_t)device_sm_count() * fv_blocks_per_sm<T>(step);
+  const int grid = (int)(tiles < cap ? tiles : cap);
+  if (step)
+    k_fv_rusanov_step<T><<<grid, kFvThreads, 0, s>>>(a);
+  else
+    k_fv_max_speed<T><<<grid, kFvThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// Host-side checks of a grid table: sorted, tile-aligned, non-overlapping
+// ranges inside [0, vcells), non-NULL aligned planes, U and Unew distinct.
+fdbb_status fv_check(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, fdbb_dtype t, const void* smax,
+                     bool step, int64_t* slots_out) {
+  if (ngrids < 0 || ngrids > FDBB_FV_MAX_GRIDS || vcells < 0 || vcells % FDBB_FV_TILE) return FDBB_ERR_ARG;
+  if (t != FDBB_F32 && t != FDBB_F64) return FDBB_ERR_DTYPE;
+  if (ngrids > 0 && (grids == nullptr || smax == nullptr)) return FDBB_ERR_NULLPTR;
+  if (smax && !aligned(smax, t == FDBB_F64 ? 8 : 4)) return FDBB_ERR_ALIGN;
+  const size_t es = t == FDBB_F64 ? 8 : 4;
+  int64_t end = 0, slots = 0;
+  for (int i = 0; i < ngrids; ++i) {
+    const fdbb_fv_grid& g = grids[i];
+    if (g.n < 1 || g.n > 4096 || g.slot < 0 || g.phase < 0 || g.phase > 2 || g.step < 0) return FDBB_ERR_ARG;
+    const int64_t cells = (int64_t)g.n * g.n * g.n;
+    const int64_t padded = (cells + FDBB_FV_TILE - 1) / FDBB_FV_TILE * FDBB_FV_TILE;
+    if (g.cell_begin < end || g.cell_begin % FDBB_FV_TILE || g.cell_begin + padded > vcells) return FDBB_ERR_ARG;
+    end = g.cell_begin + padded;
+    for (int q = 0; q < 5; ++q) {
+      if (g.U[q] == nullptr || (step && g.Unew[q] == nullptr)) return FDBB_ERR_NULLPTR;
+      if (!aligned(g.U[q], es) || (step && !aligned(g.Unew[q], es))) return FDBB_ERR_ALIGN;
+      if (step)
+        for (int r = 0; r < 5; ++r)
+          if (g.Unew[q] == g.U[r]) return FDBB_ERR_ARG;
+    }
+    if (g.dt_log && !aligned(g.dt_log, 8)) return FDBB_ERR_ALIGN;
+    if (g.slot + 1 > slots) slots = g.slot + 1;
+  }
+  if (slots_out) *slots_out = slots;
+  return FDBB_OK;
+}
+
+fdbb_status fv_run(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double gamma, double cfl, fdbb_dtype t,
+                   void* smax, bool step, fdbb_stream_t stream) {
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return FDBB_ERR_ARG;
+  if (step && !(cfl > 0.0 && std::isfinite(cfl))) return FDBB_ERR_ARG;
+  const fdbb_status st = fv_check(ngrids, grids, vcells, t, smax, step, nullptr);
+  if (st != FDBB_OK) return st;
+  if (ngrids == 0 || vcells == 0) return FDBB_OK;
+  FvArgs a;
+  a.ngrids = ngrids;
+  a.vcells = vcells;
+  a.gamma = gamma;
+  a.cfl = cfl;
+  a.smax = smax;
+  for (int i = 0; i < ngrids; ++i) a.g[i] = grids[i];
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const cudaError_t e = t == FDBB_F64 ? fv_launch<double>(a, step, s) : fv_launch<float>(a, step, s);
+  return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace fdbb
+
+extern "C" {
+
+fdbb_status fdbb_fv_max_speed(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double gamma, fdbb_dtype t,
+                              void* smax, fdbb_stream_t stream) {
+  return fdbb::fv_run(ngrids, grids, vcells, gamma, 1.0, t, smax, false, stream);
+}
+
+fdbb_status fdbb_fv_rusanov_step(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double gamma, double cfl,
+                                 fdbb_dtype t, void* smax, fdbb_stream_t stream) {
+  return fdbb::fv_run(ngrids, grids, vcells, gamma, cfl, t, smax, true, stream);
+}
+
+}  // extern "C"

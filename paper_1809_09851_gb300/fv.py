@@ -1,0 +1,154 @@
+"""Batched Rusanov finite-volume steps on periodic n^3 grids (binding).
+
+Thin marshalling over ``fdbb_fv_max_speed`` / ``fdbb_fv_rusanov_step``
+(include/fdbb.h): a list of :class:`FvGrid` states is laid out in the virtual
+cell index space (each grid padded to a multiple of the 256-cell tile),
+packed into descriptor tables of at most 256 grids and advanced by one
+launch per table.  The per-grid wave-speed scratch ``smax`` (three slots per
+grid, storage dtype) is owned by the caller.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import blocks, capi
+
+TILE = capi.FV_TILE
+MAX_GRIDS = capi.FV_MAX_GRIDS
+_CODES = {torch.float32: capi.FDBB_F32, torch.float64: capi.FDBB_F64}
+
+
+def padded_cells(n: int) -> int:
+    return (n ** 3 + TILE - 1) // TILE * TILE
+
+
+class FvGrid:
+    """State of one periodic n^3 grid: U (current), Unew (next), its
+    wave-speed slot, the step index and the step phase (step mod 3)."""
+
+    def __init__(self, U: List[torch.Tensor], Unew: List[torch.Tensor], n: int, slot: int,
+                 dt_log: Optional[torch.Tensor] = None):
+        self.U, self.Unew, self.n, self.slot = list(U), list(Unew), n, slot
+        self.phase = 0
+        self.step = 0
+        self.dt_log = dt_log
+
+    @property
+    def dtype(self):
+        return self.U[0].dtype
+
+    def advance(self):
+        self.U, self.Unew = self.Unew, self.U
+        self.phase = (self.phase + 1) % 3
+        self.step += 1
+
+
+def _table(grids: Sequence[FvGrid], with_new: bool):
+    arr = (capi.FvGrid * max(1, len(grids)))()
+    off = 0
+    for i, g in enumerate(grids):
+        e = arr[i]
+        for q in range(5):
+            e.U[q] = g.U[q].data_ptr()
+            e.Unew[q] = g.Unew[q].data_ptr() if with_new else None
+        e.dt_log = g.dt_log.data_ptr() if g.dt_log is not None else None
+        e.cell_begin = off
+        e.n, e.slot, e.phase, e.step = g.n, g.slot, g.phase, g.step
+        off += padded_cells(g.n)
+    return arr, off
+
+
+def _chunks(grids):
+    for i in range(0, len(grids), MAX_GRIDS):
+        yield grids[i:i + MAX_GRIDS]
+
+
+def _stream(stream, device) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return s.cuda_stream
+
+
+def max_speed(grids: Sequence[FvGrid], smax: torch.Tensor, gamma: float = 1.4, stream=None):
+    """Reduce max sum_d(|v_d| + c) of each grid's U into smax[3*slot + phase]
+    (the slot must be zero)."""
+    if not grids:
+        return
+    code = _CODES[grids[0].dtype]
+    for ch in _chunks(list(grids)):
+        tab, vcells = _table(ch, with_new=False)
+        capi.call("fdbb_fv_max_speed", len(ch), tab, vcells, gamma, code, smax.data_ptr(),
+                  _stream(stream, smax.device))
+
+
+def rusanov_step(grids: Sequence[FvGrid], smax: torch.Tensor, gamma: float = 1.4, cfl: float = 0.4,
+                 stream=None):
+    """Advance every grid by one step (one launch per 256 grids)."""
+    if not grids:
+        return
+    code = _CODES[grids[0].dtype]
+    for ch in _chunks(list(grids)):
+        tab, vcells = _table(ch, with_new=True)
+        capi.call("fdbb_fv_rusanov_step", len(ch), tab, vcells, gamma, cfl, code, smax.data_ptr(),
+                  _stream(stream, smax.device))
+    for g in grids:
+        g.advance()
+
+
+def primitive_on_device(n: int, seed: int, dtype, device, amplitude: float = 0.1):
+    """The smooth seeded initial data of a serving request, evaluated on the
+    device (rho, v = 0, p), from the sinusoid parameters of synth.smooth_params."""
+    from . import synth
+    x = (torch.arange(n, device=device, dtype=torch.float64) + 0.5) / n
+    X, Y, Z = x[None, None, :], x[None, :, None], x[:, None, None]
+    planes = []
+    for k, ph, a in synth.smooth_params(seed):
+        g = torch.zeros((n, n, n), dtype=torch.float64, device=device)
+        for m in range(3):
+            g = g + float(a[m]) * torch.sin(
+                2 * math.pi * (int(k[m, 0]) * X + int(k[m, 1]) * Y + int(k[m, 2]) * Z) + float(ph[m]))
+        g = g / g.abs().max()
+        planes.append((1.0 + amplitude * g).reshape(-1).to(dtype))
+    zero = torch.zeros(n ** 3, dtype=dtype, device=device)
+    return [planes[0], zero, zero.clone(), zero.clone(), planes[1]]
+
+
+def new_grid(V: Sequence[torch.Tensor], n: int, slot: int, smax: torch.Tensor, gamma: float = 1.4,
+             dt_log_steps: int = 0, stream=None) -> FvGrid:
+    """Allocate U/Unew, convert the primitive planes V to conservative U with
+    fdbb_cons_from_prim, clear the grid's three wave-speed slots and reduce the
+    initial wave speed into slot 0."""
+    dtype, device = V[0].dtype, V[0].device
+    cells = n ** 3
+    U = [torch.empty(cells, dtype=dtype, device=device) for _ in range(5)]
+    Unew = [torch.empty(cells, dtype=dtype, device=device) for _ in range(5)]
+    with torch.cuda.stream(stream) if stream is not None else _null():
+        blocks.cons_from_prim(list(V), gamma, out=U, stream=stream)
+        smax[3 * slot:3 * slot + 3].zero_()
+    dt_log = torch.zeros(dt_log_steps, dtype=torch.float64, device=device) if dt_log_steps else None
+    g = FvGrid(U, Unew, n, slot, dt_log)
+    max_speed([g], smax, gamma, stream)
+    return g
+
+
+class _null:
+    def __enter__(self):
+        return None
+
+    def __exit__(self, *a):
+        return False
+
+
+def grid_from_conservative(U: Sequence[torch.Tensor], n: int, slot: int, smax: torch.Tensor,
+                           gamma: float = 1.4, dt_log_steps: int = 0, stream=None) -> FvGrid:
+    """Like new_grid, from conservative planes (copied)."""
+    dtype, device = U[0].dtype, U[0].device
+    Uc = [u.clone() for u in U]
+    Unew = [torch.empty_like(u) for u in U]
+    smax[3 * slot:3 * slot + 3].zero_()
+    dt_log = torch.zeros(dt_log_steps, dtype=torch.float64, device=device) if dt_log_steps else None
+    g = FvGrid(Uc, Unew, n, slot, dt_log)
+    max_speed([g], smax, gamma, stream)
+    return g

@@ -134,6 +134,19 @@ def request_stream(count: int, rate: float = 2000.0, n_lo: int = 16, n_hi: int =
             for i in range(count)]
 
 
+def smooth_params(seed: int):
+    """Wave vectors k (3x3 ints in 1..3), phases and amplitudes of the three
+    sinusoids of the rho (plane 0) and p (plane 1) perturbations."""
+    out = []
+    for plane in (0, 1):
+        r = _rng(seed, 70 + plane)
+        k = r.integers(1, 4, size=(3, 3))
+        ph = r.uniform(0.0, 2.0 * math.pi, size=3)
+        a = r.uniform(0.5, 1.0, size=3)
+        out.append((k, ph, a))
+    return out
+
+
 def smooth_perturbation(n: int, seed: int, amplitude: float = 0.1):
     """rho and p planes for one periodic n^3 grid: 1 + amplitude * g(x) with g a
     sum of 3 seeded low-wavenumber sinusoids scaled to max |g| = 1; v = 0.
@@ -145,11 +158,7 @@ def smooth_perturbation(n: int, seed: int, amplitude: float = 0.1):
     Y = x[None, :, None]
     Z = x[:, None, None]
     out = []
-    for plane in (0, 1):
-        r = _rng(seed, 70 + plane)
-        k = r.integers(1, 4, size=(3, 3))
-        ph = r.uniform(0.0, 2.0 * math.pi, size=3)
-        a = r.uniform(0.5, 1.0, size=3)
+    for k, ph, a in smooth_params(seed):
         g = np.zeros((n, n, n))
         for m in range(3):
             g = g + a[m] * np.sin(2 * math.pi * (k[m, 0] * X + k[m, 1] * Y + k[m, 2] * Z) + ph[m])

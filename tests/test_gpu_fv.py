@@ -1,0 +1,132 @@
+"""Batched Rusanov finite-volume steps and the serving loop on the GPU.
+
+FP64 grids match the FP64 oracle (same scheme, different operation order)
+to 1e-11 of the field's magnitude after several steps, with the same time
+steps; FP32 grids match it to 2e-5.  A grid's results are bitwise the same
+whether it runs alone or batched with other grids, and a served request's
+answer is bitwise the same alone and in the mix.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1809_09851_gb300 import fv, serve, synth
+
+pytestmark = pytest.mark.gpu
+G_ = 1.4
+DEV = "cuda:0"
+
+
+def _initial(n, seed, swirl=0.3):
+    V = synth.smooth_perturbation(n, seed)
+    x = (np.arange(n) + 0.5) / n
+    V[1] = V[1] + swirl * np.broadcast_to(np.sin(2 * np.pi * x)[None, :, None], (n, n, n)).reshape(-1)
+    V[3] = V[3] - 0.5 * swirl * np.broadcast_to(np.cos(2 * np.pi * x)[None, None, :], (n, n, n)).reshape(-1)
+    return oracle.cons_from_prim(3, G_, V)
+
+
+def _dev(U, dtype):
+    return [torch.from_numpy(u).to(DEV).to(dtype) for u in U]
+
+
+@pytest.mark.parametrize("n,steps", [(8, 5), (13, 4)])
+def test_fv_fp64_matches_oracle(n, steps):
+    U = _initial(n, 3)
+    smax = torch.zeros(3 * 4, dtype=torch.float64, device=DEV)
+    g = fv.grid_from_conservative(_dev(U, torch.float64), n, 1, smax, G_, dt_log_steps=steps)
+    for _ in range(steps):
+        fv.rusanov_step([g], smax, G_, 0.4)
+    torch.cuda.synchronize()
+    ref, dts = oracle.rusanov_run(n, G_, 0.4, steps, U)
+    np.testing.assert_allclose(g.dt_log.cpu().numpy(), dts, rtol=1e-13)
+    for k in range(5):
+        got = g.U[k].cpu().numpy()
+        assert np.abs(got - ref[k]).max() <= 1e-11 * max(1.0, np.abs(ref[k]).max()), k
+
+
+def test_fv_fp32_matches_oracle():
+    n, steps = 12, 10
+    U = _initial(n, 4)
+    Uq = [u.astype(np.float32).astype(np.float64) for u in U]
+    smax = torch.zeros(3, dtype=torch.float32, device=DEV)
+    g = fv.grid_from_conservative(_dev(Uq, torch.float32), n, 0, smax, G_, dt_log_steps=steps)
+    for _ in range(steps):
+        fv.rusanov_step([g], smax, G_, 0.4)
+    ref, dts = oracle.rusanov_run(n, G_, 0.4, steps, Uq)
+    np.testing.assert_allclose(g.dt_log.cpu().numpy(), dts, rtol=1e-5)
+    for k in range(5):
+        got = g.U[k].double().cpu().numpy()
+        assert np.abs(got - ref[k]).max() <= 2e-5 * max(1.0, np.abs(ref[k]).max()), k
+    # conservation of mass, momentum and energy (to float roundoff)
+    for k in range(5):
+        tot0, tot = Uq[k].sum(), g.U[k].double().sum().item()
+        assert abs(tot - tot0) <= 1e-5 * max(1.0, np.abs(Uq[k]).sum())
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_fv_batched_equals_alone(dtype):
+    sizes = [3, 5, 8, 13, 16, 7]
+    steps = 6
+    Us = [_initial(n, 10 + i) for i, n in enumerate(sizes)]
+    smax_a = torch.zeros(3 * len(sizes), dtype=dtype, device=DEV)
+    alone = []
+    for i, (n, U) in enumerate(zip(sizes, Us)):
+        g = fv.grid_from_conservative(_dev(U, dtype), n, i, smax_a, G_)
+        for _ in range(steps):
+            fv.rusanov_step([g], smax_a, G_, 0.4)
+        alone.append(g)
+    smax_b = torch.zeros(3 * len(sizes), dtype=dtype, device=DEV)
+    together = [fv.grid_from_conservative(_dev(U, dtype), n, len(sizes) - 1 - i, smax_b, G_)
+                for i, (n, U) in enumerate(zip(sizes, Us))]
+    # staggered: the first half starts two steps earlier
+    for _ in range(2):
+        fv.rusanov_step(together[:3], smax_b, G_, 0.4)
+    for s in range(steps - 2):
+        fv.rusanov_step(together, smax_b, G_, 0.4)
+    for _ in range(2):
+        fv.rusanov_step(together[3:], smax_b, G_, 0.4)
+    for a, b in zip(alone, together):
+        assert a.step == b.step == steps
+        for k in range(5):
+            assert torch.equal(a.U[k], b.U[k])
+
+
+def test_fv_many_grids_over_one_table():
+    """More grids than one descriptor table holds (two launches per step)."""
+    sizes = [2 + (i % 5) for i in range(300)]
+    smax = torch.zeros(3 * 300, dtype=torch.float32, device=DEV)
+    grids = [fv.grid_from_conservative(_dev(_initial(n, 100 + i), torch.float32), n, i, smax, G_)
+             for i, n in enumerate(sizes)]
+    for _ in range(3):
+        fv.rusanov_step(grids, smax, G_, 0.4)
+    g = grids[257]
+    ref, _ = oracle.rusanov_run(g.n, G_, 0.4, 3,
+                                [u.astype(np.float32).astype(np.float64) for u in _initial(g.n, 100 + 257)])
+    for k in range(5):
+        assert np.abs(g.U[k].double().cpu().numpy() - ref[k]).max() <= 2e-5 * max(1.0, np.abs(ref[k]).max())
+
+
+def test_serving_alone_equals_mixed():
+    reqs = synth.request_stream(12, rate=2e5, n_lo=6, n_hi=24, steps_lo=5, steps_hi=15, seed=77)
+    srv = serve.FVServer(DEV, torch.float32, keep_results=True)
+    rep = srv.run(reqs, realtime=True)
+    assert sorted(rep.latencies) == [r.rid for r in reqs]
+    assert rep.max_active > 1  # requests really overlapped
+    for r in reqs[:5]:
+        one = serve.FVServer(DEV, torch.float32, keep_results=True).run([r], realtime=False)
+        for k in range(5):
+            assert torch.equal(one.results[r.rid][k], rep.results[r.rid][k]), (r.rid, k)
+    s = rep.summary()
+    assert s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_serving_admission_by_budget():
+    reqs = synth.request_stream(6, rate=1e6, n_lo=10, n_hi=10, steps_lo=3, steps_hi=3, seed=5)
+    big = synth.Request(rid=99, arrival=0.0, n=64, steps=2, seed=1)
+    one_grid = 2 * 5 * 10 ** 3 * 4
+    srv = serve.FVServer(DEV, torch.float32, hbm_budget=one_grid + 100)
+    rep = srv.run(reqs + [big], realtime=False)
+    assert rep.max_active == 1
+    assert rep.rejected == [99]
+    assert len(rep.latencies) == 6

@@ -68,19 +68,28 @@ def test_precision_form(dtype):
     ref, S = oracle.euler_fused(3, 0, G_, Uq, Wq, scale=True)
     u, tiny = U_STORE[dtype], TINY[dtype]
     report = []
+    # points whose *stored* state is at or below vacuum: rounding rhoE and m
+    # to bf16 at Mach 50 can make rhoE - |m|^2/(2 rho) zero or negative.  The
+    # exact pressure is then <= 0 (the oracle's p is within its own rounding
+    # bound of zero or negative), c = 0 or imaginary and the characteristic
+    # transform, which divides by c, is undefined: these points are counted,
+    # not compared.
+    (p_o, _), (Sp, _) = oracle.eos(3, G_, Uq, scale=True)
+    unphysical = p_o <= 8 * 2.0 ** -53 * Sp
     for c, (g, o, s) in enumerate(zip(got, ref, S)):
-        finite = np.isfinite(g)
-        if dtype != torch.float16:
-            assert finite.all(), c
-        else:
-            assert np.all(np.abs(o[~finite]) > 6.0e4)  # only f16 overflow
+        finite = np.isfinite(g) | unphysical
+        bad = ~finite & np.isfinite(o)
+        if dtype == torch.float16:
+            bad &= ~(np.abs(o) > 6.0e4)  # f16 overflow to inf
+        assert not bad.any(), (c, int(np.argmax(bad)))
+        cmp = np.isfinite(g) & np.isfinite(o) & ~unphysical
         ok = np.abs(g - o) <= u * np.abs(o) + tiny + 64 * U32 * s
-        assert ok[finite].all(), (c, int(np.argmin(ok | ~finite)))
+        assert ok[cmp].all(), (c, int(np.argmin(ok | ~cmp)))
     # the pressure, in particular at the high-Mach and near-vacuum points
     p_gpu, c_gpu = blocks.eos(Ud, G_)
     p_gpu = p_gpu.double().cpu().numpy()
     p_ref = oracle.eos(3, G_, Uq)[0]
-    fin = np.isfinite(p_gpu)
+    fin = np.isfinite(p_gpu) & ~unphysical
     err = np.abs(p_gpu - p_ref)
     assert np.all(err[fin] <= (u + 16 * U32) * np.abs(p_ref[fin]) + tiny)
     # (ii) end to end against the original FP64 fields: report only
@@ -89,7 +98,8 @@ def test_precision_form(dtype):
         rel = np.concatenate([_rel(np.abs(got[i] - ref64[i]), ref64[i])[np.isfinite(got[i])] for i in idx])
         report.append(f"{name}: max {rel.max():.2e} rms {np.sqrt(np.mean(rel ** 2)):.2e}")
     nonfinite = sum(int((~np.isfinite(g)).sum()) for g in got)
-    print(f"\n[{dtype}] end-to-end vs FP64 oracle: " + "; ".join(report) + f"; non-finite outputs {nonfinite}")
+    print(f"\n[{dtype}] end-to-end vs FP64 oracle: " + "; ".join(report)
+          + f"; non-finite outputs {nonfinite}; stored states at or below vacuum: {int(unphysical.sum())}")
 
 
 def test_compensated_recovery_beats_plain_float_at_high_mach():
