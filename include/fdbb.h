@@ -255,6 +255,36 @@ FDBB_API fdbb_status fdbb_fv_rusanov_step(int ngrids, const fdbb_fv_grid *grids,
                                           double gamma, double cfl, fdbb_dtype t, void *smax,
                                           fdbb_stream_t stream);
 
+/*
+ * fdbb_fv_rusanov_step_noalloc -- the same step for callers that cannot
+ * allocate device memory.  (The paper has no counterpart; this is an
+ * interface convenience of this library.)
+ *
+ * Some callers cannot call cudaMalloc: host frameworks that own every byte of
+ * device memory and hand plug-ins only the buffers they manage, or time-
+ * critical loops where an allocation (which may synchronise the device) is not
+ * allowed.  They still pass the grid state (U, Unew, dt_log) as with
+ * fdbb_fv_rusanov_step, but no wave-speed scratch: this entry point keeps it
+ * in a fixed array of the library's own device memory, 3 * FDBB_FV_MAX_GRIDS
+ * doubles (6 KiB), which every GPU that loads the library holds until the
+ * process exits.  Nothing is allocated or freed by the call.
+ *
+ * Each call is one complete step: it clears the array, reduces the maximum
+ * wave speed of every grid's U into it and advances the grids, so the
+ * descriptors' `slot` and `phase` fields are ignored (dt is still that of the
+ * state at the start of the step, and dt_log[step] is written as usual).  The
+ * results equal those of fdbb_fv_max_speed + fdbb_fv_rusanov_step.
+ * At most FDBB_FV_MAX_GRIDS grids per call; more returns FDBB_ERR_ARG.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents, so calls that overlap on the GPU (on
+ * different streams, or from different threads) race: serialise them.
+ */
+FDBB_API fdbb_status fdbb_fv_rusanov_step_noalloc(int ngrids, const fdbb_fv_grid *grids,
+                                                  int64_t vcells, double gamma, double cfl,
+                                                  fdbb_dtype t, fdbb_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

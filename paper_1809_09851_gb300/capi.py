@@ -51,6 +51,7 @@ _FVP = ctypes.POINTER(FvGrid)
 SIGNATURES.update({
     "fdbb_fv_max_speed": [_i, _FVP, _i64, _d, _i, _vp, _vp],
     "fdbb_fv_rusanov_step": [_i, _FVP, _i64, _d, _d, _i, _vp, _vp],
+    "fdbb_fv_rusanov_step_noalloc": [_i, _FVP, _i64, _d, _d, _i, _vp],
 })
 
 _lib = None

@@ -16,6 +16,7 @@
 // which other grids share the launch.
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "fdbb.h"
 #include "fdbb_device.cuh"
@@ -273,10 +274,82 @@ fdbb_status fv_run(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double
   return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
 }
 
+// Scratch of fdbb_fv_rusanov_step_noalloc: three wave-speed slots for each of
+// at most FDBB_FV_MAX_GRIDS grids (6 KiB).  It lives in every device that loads
+// the library, for as long as the library stays loaded, and is shared by every
+// call of that entry point on that device.
+static __device__ __align__(256) double g_fv_noalloc_smax[3 * FDBB_FV_MAX_GRIDS];
+
+// Device address of g_fv_noalloc_smax on the current device.  In host code the
+// symbol's name is a host-side stand-in, not a device address, so the address
+// is looked up with cudaGetSymbolAddress, with the device current, the first
+// time the entry point runs on that device, and cached.
+fdbb_status noalloc_scratch(void** out) {
+  static std::mutex mu;
+  static void* cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FDBB_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && cache[dev] != nullptr) {
+    *out = cache[dev];
+    return FDBB_OK;
+  }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_fv_noalloc_smax) != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return FDBB_ERR_CUDA;
+  }
+  if (dev >= 0 && dev < 64) cache[dev] = p;
+  *out = p;
+  return FDBB_OK;
+}
+
+fdbb_status fv_step_noalloc(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double gamma, double cfl,
+                            fdbb_dtype t, fdbb_stream_t stream) {
+  if (ngrids > FDBB_FV_MAX_GRIDS) return FDBB_ERR_ARG;  // beyond the static scratch
+  if (ngrids < 0 || !(gamma > 1.0) || !std::isfinite(gamma) || !(cfl > 0.0 && std::isfinite(cfl)))
+    return FDBB_ERR_ARG;
+  if (ngrids > 0 && grids == nullptr) return FDBB_ERR_NULLPTR;
+  void* scratch = nullptr;
+  const fdbb_status sst = noalloc_scratch(&scratch);
+  if (sst != FDBB_OK) return sst;
+  FvArgs a;
+  a.ngrids = ngrids;
+  a.vcells = vcells;
+  a.gamma = gamma;
+  a.cfl = cfl;
+  a.smax = scratch;
+  for (int i = 0; i < ngrids; ++i) {
+    a.g[i] = grids[i];
+    a.g[i].slot = i;   // slot and phase of the caller's table are not used:
+    a.g[i].phase = 0;  // every call recomputes the wave speed of U
+  }
+  const fdbb_status st = fv_check(ngrids, a.g, vcells, t, scratch, true, nullptr);
+  if (st != FDBB_OK) return st;
+  if (ngrids == 0 || vcells == 0) return FDBB_OK;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the slots keep the previous call's contents: clear them first
+  if (cudaMemsetAsync(scratch, 0, sizeof(double) * 3 * (size_t)ngrids, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FDBB_ERR_CUDA;
+  }
+  cudaError_t e = t == FDBB_F64 ? fv_launch<double>(a, false, s) : fv_launch<float>(a, false, s);
+  if (e == cudaSuccess) e = t == FDBB_F64 ? fv_launch<double>(a, true, s) : fv_launch<float>(a, true, s);
+  return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
+}
+
 }  // namespace
 }  // namespace fdbb
 
 extern "C" {
+
+fdbb_status fdbb_fv_rusanov_step_noalloc(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double gamma,
+                                         double cfl, fdbb_dtype t, fdbb_stream_t stream) {
+  return fdbb::fv_step_noalloc(ngrids, grids, vcells, gamma, cfl, t, stream);
+}
 
 fdbb_status fdbb_fv_max_speed(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double gamma, fdbb_dtype t,
                               void* smax, fdbb_stream_t stream) {
