@@ -202,6 +202,9 @@ def run_gpu(args):
     seed = shard_seed(1809, rank)
     stream = torch.cuda.Stream(dev)
     hbm_peak, peak_kind = measured_peaks()
+    if args.only == "fv":  # the finite-volume step kernel alone (profiling runs)
+        print(json.dumps({"fv_batch": run_fv_batch(args, dev, hbm_peak)}), flush=True)
+        return None
 
     U64, W64 = make_fields(n, seed, dev)
     alloc = lambda k, dt: [torch.empty(n, dtype=dt, device=dev) for _ in range(k)]
@@ -267,6 +270,12 @@ def run_gpu(args):
 
     # ---- end to end through host buffers ---------------------------------------
     e2e = None if args.no_e2e else run_e2e(args, U64, W64, out64, stream, dev, world)
+    del out64
+    torch.cuda.empty_cache()
+    serving = run_serving(args, dev) if (args.serve_requests > 0 and world == 1) else None
+    fv_batch = run_fv_batch(args, dev, hbm_peak) if (args.serve_requests > 0 and world == 1) else None
+    if serving is not None:
+        serving["fv_step_kernel"] = fv_batch
 
     result = None
     if rank == 0:
@@ -288,6 +297,7 @@ def run_gpu(args):
             "f64_dw": f64dw,
             "mixed": extra,
             "e2e": e2e,
+            "serving": serving,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -300,10 +310,75 @@ def run_gpu(args):
     return result
 
 
+def run_serving(args, dev):
+    """Serving workload: a bounded window of the Poisson request stream
+    (2,000 req/s, n^3 periodic grids with n log-uniform in [16, 192], 10-200
+    Rusanov steps, FP32 state) through the continuous-batching loop, at the
+    full and at half the arrival rate; and one-grid-at-a-time FP64 on a prefix
+    of the same requests."""
+    import torch
+    from paper_1809_09851_gb300 import serve, synth
+    out = {}
+    reqs = synth.request_stream(args.serve_requests, rate=2000.0)
+    offered = sum(r.n ** 3 * r.steps for r in reqs)
+    for tag, scale in (("rate_2000", 1.0), ("rate_1000", 2.0)):
+        rs = [synth.Request(r.rid, r.arrival * scale, r.n, r.steps, r.seed) for r in reqs]
+        srv = serve.FVServer(dev, torch.float32)
+        serve.FVServer(dev, torch.float32).run(rs[:4], realtime=False)  # warm-up (kernels, allocator)
+        rep = srv.run(rs, realtime=True)
+        sm = rep.summary()
+        window = rs[-1].arrival
+        out[tag] = {"requests": sm["requests"], "p50_s": round(sm["p50_s"], 4), "p99_s": round(sm["p99_s"], 4),
+                    "cells_per_s": round(sm["cells_per_s"], 1), "wall_s": round(sm["wall_s"], 3),
+                    "offered_cells_per_s": round(offered / window, 1) if window > 0 else None,
+                    "max_active": sm["max_active"], "launches": sm["launches"]}
+    base = reqs[:args.serve_fp64_requests]
+    srv = serve.FVServer(dev, torch.float64, max_active=1)
+    rep = srv.run(base, realtime=False)
+    sm = rep.summary()
+    out["fp64_one_at_a_time"] = {"requests": sm["requests"], "p50_s": round(sm["p50_s"], 4),
+                                 "p99_s": round(sm["p99_s"], 4), "cells_per_s": round(sm["cells_per_s"], 1)}
+    rep32 = serve.FVServer(dev, torch.float32).run(base, realtime=False)
+    out["fp32_batched_same_requests"] = {"cells_per_s": round(rep32.summary()["cells_per_s"], 1)}
+    out["workload"] = (f"first {len(reqs)} requests of the Poisson stream (2000/s), n^3 grids n in [16,192] "
+                       f"log-uniform, 10-200 steps, CFL 0.4, FP32 state; FP64 baseline on the first {len(base)}")
+    return out
+
+
+def run_fv_batch(args, dev, hbm_peak):
+    """Batched Rusanov step kernel alone: 8 periodic 128^3 FP32 grids (16.8 M
+    cells) advanced together, 40 B algorithmic traffic per cell-step (5 planes
+    read, 5 written)."""
+    import torch
+    from paper_1809_09851_gb300 import fv
+    n, ngrid = args.fv_n, args.fv_grids
+    smax = torch.zeros(3 * ngrid, dtype=torch.float32, device=dev)
+    grids = [fv.new_grid(fv.primitive_on_device(n, 100 + i, torch.float32, dev), n, i, smax)
+             for i in range(ngrid)]
+    for _ in range(max(3, args.warmup)):
+        fv.rusanov_step(grids, smax)
+    steps = max(3, args.fv_steps)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record()
+    for i in range(steps):
+        fv.rusanov_step(grids, smax)
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(steps)]
+    cells = ngrid * n ** 3
+    avg = sum(per) / len(per)
+    gbs = 40.0 * cells / avg / 1e9
+    return {"workload": f"{ngrid} grids of {n}^3, FP32", "cell_steps_per_s": round(cells / avg, 1),
+            "ms_per_step": round(avg * 1e3, 4), "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3),
+            "bytes_per_cell_step": 40}
+
+
 def run_e2e(args, U, W, out, stream, dev, world):
     """Same metric through the public API with pinned host buffers: every step
     copies U and W host->device, runs the fused pass and copies all 45 output
-    planes device->host."""
+    planes device->host (blocks.euler_fused_host: chunks of 2^22 points whose
+    copies and kernels overlap on three streams)."""
     import torch
     from paper_1809_09851_gb300 import blocks
     n = U[0].shape[0]
@@ -311,32 +386,27 @@ def run_e2e(args, U, W, out, stream, dev, world):
     hU = [u.cpu().pin_memory() for u in U]
     hW = [w.cpu().pin_memory() for w in W]
     F, A, Y = out
-    outs = [*F, *A, *Y]
-    hO = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in outs]
+    hF = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in F]
+    hA = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in A]
+    hY = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in Y]
     h2d = sum(t.numel() * t.element_size() for t in hU + hW)
-    d2h = sum(t.numel() * t.element_size() for t in hO)
-
-    def step():
-        for d, h in zip(U + W, hU + hW):
-            d.copy_(h, non_blocking=True)
-        blocks.euler_fused(U, W, 0, GAMMA, out=(F, A, Y))
-        for h, d in zip(hO, outs):
-            h.copy_(d, non_blocking=True)
-
+    d2h = sum(t.numel() * t.element_size() for t in hF + hA + hY)
     with torch.cuda.stream(stream):
-        step()
+        work = blocks.euler_fused_host(hU, hW, (hF, hA, hY), 0, GAMMA, chunk=args.e2e_chunk, device=dev)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            step()
+            work = blocks.euler_fused_host(hU, hW, (hF, hA, hY), 0, GAMMA, chunk=args.e2e_chunk, device=dev,
+                                           work=work)
         e1.record(stream)
         torch.cuda.synchronize()
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
-    del hU, hW, hO
+    del hU, hW, hF, hA, hY, work
     return {"value": round(world * n * steps / t / 1e9, 4), "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": round(t * 1e3 / steps, 3)}
+            "ms_per_step": round(t * 1e3 / steps, 3), "chunk_points": args.e2e_chunk,
+            "gpu_launches_per_step": -(-n // args.e2e_chunk)}
 
 
 # ---------------------------------------------------------------------------
@@ -413,12 +483,19 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["fdbb", "reference"], default="fdbb")
     ap.add_argument("--n", type=int, default=N_POINTS, help="points per GPU (default 2^26)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-chunk", type=int, default=1 << 22)
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=1 << 16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--only", choices=["all", "f64", "f64dw", "f32", "bf16"], default="all",
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests in the serving window (0 skips the serving leg)")
+    ap.add_argument("--serve-fp64-requests", type=int, default=20)
+    ap.add_argument("--fv-n", type=int, default=128)
+    ap.add_argument("--fv-grids", type=int, default=8)
+    ap.add_argument("--fv-steps", type=int, default=20)
+    ap.add_argument("--only", choices=["all", "f64", "f64dw", "f32", "bf16", "fv"], default="all",
                     help="storage types to time besides the f64 headline (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -100,6 +100,16 @@ FDBB_API const char *fdbb_status_string(fdbb_status status);
 FDBB_API int fdbb_version(void);
 
 /*
+ * Kernels that stage their inputs through shared memory wait on the copies
+ * with a bounded number of polls; a wait that runs out makes the kernel stop
+ * (after waiting, bounded again, for its copies in flight) and count the
+ * event.  fdbb_device_status synchronises with the device, returns
+ * FDBB_ERR_TIMEOUT if any such wait ran out since the previous call (and
+ * clears the count), else FDBB_OK.
+ */
+FDBB_API fdbb_status fdbb_device_status(void);
+
+/*
  * |v|^2 = (m_1^2 + .. + m_D^2) / rho^2, the kinetic-energy sub-expression
  * used as micro-benchmark in the paper (section 3, Eq. (2)).
  * U: the first D+1 planes of a conservative field (rho, m_1..m_D); y: 1 plane.

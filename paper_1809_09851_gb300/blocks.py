@@ -180,3 +180,74 @@ def flux_vjp(U, G, dir: int, gamma: float = GAMMA, out=None, stream=None, dw: bo
     capi.call("fdbb_flux_vjp", D, dir, gamma, n, _code(dt, dw), _ptrs(U), _ptrs(G), _ptrs(gU),
               _stream(dev, stream))
     return gU
+
+
+def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: int = 1 << 22,
+                     device=None, dw: bool = False, work=None):
+    """fdbb_euler_fused over fields in pinned HOST memory.
+
+    U (nv planes) and W (nv planes) are pinned CPU tensors and ``out`` the
+    (F, A, Y) plane lists, also pinned CPU tensors.  The points are processed
+    in chunks of ``chunk`` through device staging buffers on three streams, so
+    that the host-to-device copy of chunk i+1, the kernel on chunk i and the
+    device-to-host copy of chunk i-1 overlap.  ``work`` may hold the staging
+    buffers of a previous call (returned) to avoid reallocating them.
+    Returns ``work``; the results are complete when the current stream has
+    caught up (the call makes the current stream wait for its streams).
+    """
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    D = _dim(U)
+    nv = D + 2
+    n = U[0].shape[0]
+    dt = U[0].dtype
+    F, A, Y = out
+    host_out = [*F, *A, *Y]
+    n_out = len(host_out)
+    nbuf = 2
+    if work is None or work["chunk"] != chunk or work["dtype"] != dt:
+        work = {
+            "chunk": chunk, "dtype": dt,
+            "in": [[torch.empty(chunk, dtype=dt, device=dev) for _ in range(2 * nv)] for _ in range(nbuf)],
+            "out": [[torch.empty(chunk, dtype=dt, device=dev) for _ in range(n_out)] for _ in range(nbuf)],
+            "s_h2d": torch.cuda.Stream(dev), "s_cmp": torch.cuda.Stream(dev), "s_d2h": torch.cuda.Stream(dev),
+        }
+    s_h2d, s_cmp, s_d2h = work["s_h2d"], work["s_cmp"], work["s_d2h"]
+    cur = torch.cuda.current_stream(dev)
+    for s in (s_h2d, s_cmp, s_d2h):
+        s.wait_stream(cur)
+    ev_in = [torch.cuda.Event() for _ in range(nbuf)]    # inputs of buffer b staged
+    ev_done = [torch.cuda.Event() for _ in range(nbuf)]  # kernel on buffer b finished
+    ev_out = [torch.cuda.Event() for _ in range(nbuf)]   # outputs of buffer b copied out
+    used = [False] * nbuf
+    nchunks = (n + chunk - 1) // chunk
+    for c in range(nchunks):
+        b = c % nbuf
+        lo, hi = c * chunk, min(n, (c + 1) * chunk)
+        m = hi - lo
+        din = work["in"][b]
+        dout = work["out"][b]
+        with torch.cuda.stream(s_h2d):
+            if used[b]:
+                s_h2d.wait_event(ev_done[b])  # the kernel no longer reads din
+            for d, h in zip(din, list(U) + list(W)):
+                d[:m].copy_(h[lo:hi], non_blocking=True)
+            ev_in[b].record(s_h2d)
+        with torch.cuda.stream(s_cmp):
+            s_cmp.wait_event(ev_in[b])
+            if used[b]:
+                s_cmp.wait_event(ev_out[b])  # dout has been copied out
+            ins = [t[:m] for t in din]
+            outs = [t[:m] for t in dout]
+            euler_fused(ins[:nv], ins[nv:], dir_jac, gamma,
+                        out=(outs[:D * nv], outs[D * nv:D * nv + nv * nv], outs[D * nv + nv * nv:]),
+                        stream=s_cmp, dw=dw)
+            ev_done[b].record(s_cmp)
+        with torch.cuda.stream(s_d2h):
+            s_d2h.wait_event(ev_done[b])
+            for h, d in zip(host_out, dout):
+                h[lo:hi].copy_(d[:m], non_blocking=True)
+            ev_out[b].record(s_d2h)
+        used[b] = True
+    for s in (s_h2d, s_cmp, s_d2h):
+        cur.wait_stream(s)
+    return work

@@ -80,6 +80,8 @@ def lib():
         L.fdbb_status_string.restype = ctypes.c_char_p
         L.fdbb_version.argtypes = []
         L.fdbb_version.restype = _i
+        L.fdbb_device_status.argtypes = []
+        L.fdbb_device_status.restype = _i
         _lib = L
     return _lib
 
@@ -103,4 +105,4 @@ def status_string(status: int) -> str:
 
 
 def exported_symbols():
-    return ["fdbb_status_string", "fdbb_version", *SIGNATURES.keys()]
+    return ["fdbb_status_string", "fdbb_version", "fdbb_device_status", *SIGNATURES.keys()]

@@ -90,8 +90,10 @@ KArgs make_args(int64_t n, double gamma) {
   return a;
 }
 
-fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, const KArgs& a, fdbb_stream_t stream) {
+fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, KArgs& a, fdbb_stream_t stream) {
   if (a.n == 0) return FDBB_OK;
+  a.nin = 0;
+  while (a.nin < fdbb::kMaxIn && a.in[a.nin] != nullptr) ++a.nin;
   const LaunchReq r{op, dim, dir, reinterpret_cast<cudaStream_t>(stream)};
   cudaError_t e = cudaErrorInvalidValue;
   switch (t) {
@@ -129,6 +131,12 @@ const char* fdbb_status_string(fdbb_status s) {
 }
 
 int fdbb_version(void) { return 100; }
+
+fdbb_status fdbb_device_status(void) {
+  const unsigned int n = fdbb::wait_timeouts_f64() + fdbb::wait_timeouts_f32() + fdbb::wait_timeouts_f16() +
+                         fdbb::wait_timeouts_bf16() + fdbb::wait_timeouts_f64dw();
+  return n ? FDBB_ERR_TIMEOUT : FDBB_OK;
+}
 
 fdbb_status fdbb_v_mag2(int dim, int64_t n, fdbb_dtype t, const void* const* U, void* y, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));

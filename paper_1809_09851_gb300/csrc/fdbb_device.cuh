@@ -113,6 +113,40 @@ __device__ __forceinline__ void st_vec(__nv_bfloat16* p, const float (&x)[4]) {
   __stcs(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
 }
 
+// Vector reads of a tile staged in shared memory (plain loads; the data was
+// written there by the tensor-memory-access engine).
+__device__ __forceinline__ void ld_sh(const double* p, double (&x)[1]) { x[0] = p[0]; }
+__device__ __forceinline__ void ld_sh(const double* p, double (&x)[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  x[0] = v.x;
+  x[1] = v.y;
+}
+__device__ __forceinline__ void ld_sh(const float* p, float (&x)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x;
+  x[1] = v.y;
+  x[2] = v.z;
+  x[3] = v.w;
+}
+__device__ __forceinline__ void ld_sh(const __half* p, float (&x)[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+  x[0] = a.x;
+  x[1] = a.y;
+  x[2] = b.x;
+  x[3] = b.y;
+}
+__device__ __forceinline__ void ld_sh(const __nv_bfloat16* p, float (&x)[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+  x[0] = a.x;
+  x[1] = a.y;
+  x[2] = b.x;
+  x[3] = b.y;
+}
+
 // Range guard of a compute type: a no-op for IEEE types; for dw it records
 // whether every checked value lies in the double-word fast-path range.
 struct NoGuard {

@@ -17,6 +17,7 @@ struct KArgs {
   const void* in[kMaxIn];
   void* out[kMaxOut];
   int64_t n;
+  int nin;       // input planes in use (the leading non-NULL entries of in[])
   double kd[6];  // gamma, gamma-1, 3-gamma, 2/(gamma-1), 1/(gamma-1), -gamma
   float kf[6];   // the same, rounded once to float
   float kl[6];   // kd - kf rounded to float: (kf, kl) is the double-word constant
@@ -38,5 +39,13 @@ cudaError_t dispatch_f32(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_bf16(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f64dw(const LaunchReq& r, const KArgs& a);
+
+// Bounded device waits that ran out since the last call, per translation unit
+// (read and cleared; synchronous).
+unsigned int wait_timeouts_f64();
+unsigned int wait_timeouts_f32();
+unsigned int wait_timeouts_f16();
+unsigned int wait_timeouts_bf16();
+unsigned int wait_timeouts_f64dw();
 
 }  // namespace fdbb

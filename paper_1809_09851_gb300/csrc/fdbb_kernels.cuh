@@ -1,13 +1,25 @@
-// fdbb_kernels.cuh -- one fused grid-stride kernel per building block.
+// fdbb_kernels.cuh -- one fused kernel per building block.
 //
-// Every kernel is k_pointwise<Op, T, R>: a persistent grid (a multiple of the
-// SM count) strides over chunks of VW points; Op::apply loads the chunk's input
-// planes (storage type T), converts them to the compute type R, evaluates its
-// expressions in registers and stores its output planes.  No temporaries touch
-// memory.
+// Each block evaluates one expression tree point by point: Op::apply takes the
+// input planes of VW consecutive points (storage type T) from a *source*,
+// converts them to the compute type R, evaluates the expressions in registers
+// and stores every output plane once.  No temporaries touch memory.
+//
+// Two kernels drive the ops:
+//   k_pointwise -- a persistent grid strides over chunks of VW points and
+//                  reads them straight from global memory (GlobalSrc);
+//   k_staged    -- a persistent grid walks 256*VW-point tiles; one thread per
+//                  block streams the input planes of the block's next tiles
+//                  into a two-stage shared-memory ring with bulk asynchronous
+//                  copies (cp.async.bulk, completion on an mbarrier) while the
+//                  block computes the current tile from the other stage
+//                  (SmemSrc), so HBM latency overlaps the arithmetic.  The
+//                  ragged tail (< one tile) is read straight from global
+//                  memory.
 //
 // apply() returns false -- before storing anything -- when the double-word
-// range guard fails; the kernel then recomputes that chunk in native FP64.
+// range guard fails; the chunk is then recomputed in native FP64 from the same
+// source.
 #pragma once
 
 #include <type_traits>
@@ -18,6 +30,8 @@
 namespace fdbb {
 
 constexpr int kThreads = 256;
+constexpr int kStages = 2;
+constexpr int kWaitLimit = 1 << 22;  // bounded mbarrier polls per wait
 
 template <class T> __device__ __forceinline__ const T* inp(const KArgs& a, int k) {
   return static_cast<const T*>(a.in[k]);
@@ -38,11 +52,35 @@ template <> __device__ __forceinline__ Consts<dw> consts<dw>(const KArgs& a) {
           dw(a.kf[3], a.kl[3]), dw(a.kf[4], a.kl[4]), dw(a.kf[5], a.kl[5])};
 }
 
+// ---------------------------------------------------------------------------
+// Input sources: plane k of the current VW points, in the storage's load type.
+// ---------------------------------------------------------------------------
+
+// Straight from global memory (cnt < VW only in the ragged last chunk).
+template <class T, int VW> struct GlobalSrc {
+  const KArgs& a;
+  int64_t i0;
+  int cnt;
+  __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float fill) const {
+    load_raw<T, VW>(inp<T>(a, k), i0, cnt, r, fill);
+  }
+};
+
+// From the block's shared-memory stage: this thread's VW points of plane k sit
+// at base + k * TILE (the stage stays valid until the block has finished the
+// tile, so a double-word chunk can be re-read for its FP64 fallback).
+template <class T, int VW, int TILE> struct SmemSrc {
+  const T* base;
+  __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float) const {
+    ld_sh(base + (size_t)k * TILE, r);
+  }
+};
+
 // Conservative state of VW points from input planes base..base+D+1.
-template <class T, int VW, int D, class R, class G>
-__device__ __forceinline__ void load_U(const KArgs& a, int base, int64_t i0, int cnt, Pt<R, D> (&s)[VW], G& g) {
+template <class T, int VW, int D, class R, class G, class Src>
+__device__ __forceinline__ void load_U(const Src& src, int base, Pt<R, D> (&s)[VW], G& g) {
   typename Storage<T>::L raw[VW];
-  load_raw<T, VW>(inp<T>(a, base), i0, cnt, raw, 1.0f);
+  src.raw(base, raw, 1.0f);
 #pragma unroll
   for (int j = 0; j < VW; ++j) {
     s[j].rho = to_compute<R, G>(raw[j], g);
@@ -50,26 +88,35 @@ __device__ __forceinline__ void load_U(const KArgs& a, int base, int64_t i0, int
   }
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    load_raw<T, VW>(inp<T>(a, base + 1 + i), i0, cnt, raw, 0.0f);
+    src.raw(base + 1 + i, raw, 0.0f);
 #pragma unroll
     for (int j = 0; j < VW; ++j) {
       s[j].m[i] = to_compute<R, G>(raw[j], g);
       if constexpr (std::is_same<R, dw>::value) s[j].raw.m[i] = raw[j];
     }
   }
-  load_raw<T, VW>(inp<T>(a, base + D + 1), i0, cnt, raw, 1.0f);
+  src.raw(base + D + 1, raw, 1.0f);
 #pragma unroll
   for (int j = 0; j < VW; ++j) s[j].rE = to_compute<R, G>(raw[j], g);
 }
 
+// One plane, converted to the compute type.
+template <class T, int VW, class R, class G, class Src>
+__device__ __forceinline__ void load_plane(const Src& src, int k, R (&x)[VW], float fill, G& g) {
+  typename Storage<T>::L raw[VW];
+  src.raw(k, raw, fill);
+#pragma unroll
+  for (int j = 0; j < VW; ++j) x[j] = to_compute<R, G>(raw[j], g);
+}
+
 // nv planes of a second input field (W or G) from planes base..base+nv-1,
 // as w[point][component].
-template <class T, int VW, int NV, class R, class G>
-__device__ __forceinline__ void load_field(const KArgs& a, int base, int64_t i0, int cnt, R (&w)[VW][NV], G& g) {
+template <class T, int VW, int NV, class R, class G, class Src>
+__device__ __forceinline__ void load_field(const Src& src, int base, R (&w)[VW][NV], G& g) {
   R x[VW];
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
-    load<T, VW, R>(inp<T>(a, base + c), i0, cnt, x, 0.0f, g);
+    load_plane<T, VW, R>(src, base + c, x, 0.0f, g);
 #pragma unroll
     for (int j = 0; j < VW; ++j) w[j][c] = x[j];
   }
@@ -139,22 +186,24 @@ __device__ __forceinline__ void emit_jac(const KArgs& a, int base, int64_t i0, i
 }
 
 // ---------------------------------------------------------------------------
-// Ops
+// Ops.  kIn = number of input planes; apply<T, VW, R>(a, k, src, i0, cnt).
 // ---------------------------------------------------------------------------
 
 // |v|^2 = (sum m_i^2) / (rho rho)  (paper section 3, Eq. (2)).
 template <int D> struct OpVMag2 {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>&, int64_t i0, int cnt) {
+  static constexpr int kIn = D + 1;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>&, const Src& src, int64_t i0,
+                                               int cnt) {
     typename GuardOf<R>::type g;
     R rho[VW], m[VW], num[VW];
-    load<T, VW, R>(inp<T>(a, 0), i0, cnt, rho, 1.0f, g);
-    load<T, VW, R>(inp<T>(a, 1), i0, cnt, m, 0.0f, g);
+    load_plane<T, VW, R>(src, 0, rho, 1.0f, g);
+    load_plane<T, VW, R>(src, 1, m, 0.0f, g);
 #pragma unroll
     for (int j = 0; j < VW; ++j) num[j] = m[j] * m[j];
 #pragma unroll
     for (int i = 1; i < D; ++i) {
-      load<T, VW, R>(inp<T>(a, 1 + i), i0, cnt, m, 0.0f, g);
+      load_plane<T, VW, R>(src, 1 + i, m, 0.0f, g);
 #pragma unroll
       for (int j = 0; j < VW; ++j) num[j] = fma_(m[j], m[j], num[j]);
     }
@@ -168,11 +217,13 @@ template <int D> struct OpVMag2 {
 
 // V = (rho, v, p) from U.
 template <int D> struct OpPrim {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
-    load_U<T, VW, D>(a, 0, i0, cnt, s, g);
+    load_U<T, VW, D>(src, 0, s, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
     R x[VW];
@@ -201,17 +252,19 @@ template <int D> struct OpPrim {
 
 // U = (rho, rho v, p/(gamma-1) + rho |v|^2 / 2) from V.
 template <int D> struct OpCons {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     typename GuardOf<R>::type g;
     R rho[VW], v[D][VW], p[VW], x[VW];
     typename Storage<T>::L rho_raw[VW];
-    load_raw<T, VW>(inp<T>(a, 0), i0, cnt, rho_raw, 1.0f);
+    src.raw(0, rho_raw, 1.0f);
 #pragma unroll
     for (int j = 0; j < VW; ++j) rho[j] = to_compute<R>(rho_raw[j], g);
 #pragma unroll
-    for (int i = 0; i < D; ++i) load<T, VW, R>(inp<T>(a, 1 + i), i0, cnt, v[i], 0.0f, g);
-    load<T, VW, R>(inp<T>(a, D + 1), i0, cnt, p, 1.0f, g);
+    for (int i = 0; i < D; ++i) load_plane<T, VW, R>(src, 1 + i, v[i], 0.0f, g);
+    load_plane<T, VW, R>(src, D + 1, p, 1.0f, g);
     if (!g.ok) return false;
     store_raw<T, VW>(outp<T>(a, 0), i0, cnt, rho_raw);  // rho: a copy of the input
     R v2[VW];
@@ -233,11 +286,13 @@ template <int D> struct OpCons {
 
 // p and c.
 template <int D> struct OpEos {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
-    load_U<T, VW, D>(a, 0, i0, cnt, s, g);
+    load_U<T, VW, D>(src, 0, s, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
     R x[VW];
@@ -257,11 +312,13 @@ template <int D> struct OpEos {
 
 // w- = u - 2c/(gamma-1), w+ = u + 2c/(gamma-1), s = p rho^-gamma.
 template <int D, int d> struct OpRiemann {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
-    load_U<T, VW, D>(a, 0, i0, cnt, s, g);
+    load_U<T, VW, D>(src, 0, s, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
     R wm[VW], wp[VW];
@@ -284,11 +341,13 @@ template <int D, int d> struct OpRiemann {
 
 // Flux column d, or all columns when d == -1.
 template <int D, int d> struct OpFlux {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
-    load_U<T, VW, D>(a, 0, i0, cnt, s, g);
+    load_U<T, VW, D>(src, 0, s, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
     if constexpr (d >= 0) {
@@ -303,11 +362,13 @@ template <int D, int d> struct OpFlux {
 };
 
 template <int D, int d> struct OpJac {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
-    load_U<T, VW, D>(a, 0, i0, cnt, s, g);
+    load_U<T, VW, D>(src, 0, s, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
     emit_jac<T, VW, D, d>(a, 0, i0, cnt, s, k);
@@ -316,14 +377,16 @@ template <int D, int d> struct OpJac {
 };
 
 template <int D, int d, bool INV> struct OpChar {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = 2 * (D + 2);
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
-    load_U<T, VW, D>(a, 0, i0, cnt, s, g);
+    load_U<T, VW, D>(src, 0, s, g);
     R w[VW][nv], y[VW][nv];
-    load_field<T, VW, nv>(a, nv, i0, cnt, w, g);
+    load_field<T, VW, nv>(src, nv, w, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
 #pragma unroll
@@ -341,15 +404,17 @@ template <int D, int d, bool INV> struct OpChar {
 // All flux columns (planes 0..D*nv-1), A_dj (D*nv .. D*nv+nv^2-1) and
 // L_dj W (last nv planes) in one pass; inputs U (planes 0..nv-1), W (nv..2nv-1).
 template <int D, int dj> struct OpFused {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = 2 * (D + 2);
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
-    load_U<T, VW, D>(a, 0, i0, cnt, s, g);
+    load_U<T, VW, D>(src, 0, s, g);
     R w[VW][nv];
     const bool want_y = a.in[nv] != nullptr;
-    if (want_y) load_field<T, VW, nv>(a, nv, i0, cnt, w, g);
+    if (want_y) load_field<T, VW, nv>(src, nv, w, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
     emit_flux<T, VW, D, 0>(a, 0, i0, cnt, s);
@@ -367,14 +432,16 @@ template <int D, int dj> struct OpFused {
 };
 
 template <int D, int d> struct OpVjp {
-  template <class T, int VW, class R>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, int64_t i0, int cnt) {
+  static constexpr int kIn = 2 * (D + 2);
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
-    load_U<T, VW, D>(a, 0, i0, cnt, s, g);
+    load_U<T, VW, D>(src, 0, s, g);
     R gg[VW][nv], y[VW][nv];
-    load_field<T, VW, nv>(a, nv, i0, cnt, gg, g);
+    load_field<T, VW, nv>(src, nv, gg, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
 #pragma unroll
@@ -385,30 +452,166 @@ template <int D, int d> struct OpVjp {
 };
 
 // ---------------------------------------------------------------------------
-// The kernel and its launcher
+// Bulk asynchronous copies and mbarriers (sm_90+ PTX, used on sm_103a)
 // ---------------------------------------------------------------------------
-template <class Op, class T, class R>
-__global__ void __launch_bounds__(kThreads) k_pointwise(const __grid_constant__ KArgs a) {
+
+// Bounded mbarrier waits that ran out in this translation unit's kernels.
+static __device__ unsigned int g_wait_timeouts;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Order this thread's earlier shared-memory accesses before later accesses of
+// the asynchronous (bulk copy) proxy.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// bytes from global src to shared dst; both 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Wait for the phase with the given parity to complete; false after
+// kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_addr(bar);
+  for (int i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+template <class Op, class T, class R, class Src>
+__device__ __forceinline__ void apply_chunk(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0, int cnt) {
   constexpr int VW = Width<T, R>::VW;
-  const Consts<R> k = consts<R>(a);
-  const int64_t nchunk = (a.n + VW - 1) / VW;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunk; ch += stride) {
-    const int64_t i0 = ch * VW;
-    const int cnt = (a.n - i0 < VW) ? (int)(a.n - i0) : VW;
-    if constexpr (std::is_same<R, dw>::value) {
-      // double-word fast path; chunks outside its range run in native FP64
-      if (!Op::template apply<T, VW, dw>(a, k, i0, cnt))
-        Op::template apply<T, VW, double>(a, consts<double>(a), i0, cnt);
-    } else {
-      Op::template apply<T, VW, R>(a, k, i0, cnt);
-    }
+  if constexpr (std::is_same<R, dw>::value) {
+    // double-word fast path; chunks outside its range run in native FP64
+    if (!Op::template apply<T, VW, dw>(a, k, src, i0, cnt))
+      Op::template apply<T, VW, double>(a, consts<double>(a), src, i0, cnt);
+  } else {
+    Op::template apply<T, VW, R>(a, k, src, i0, cnt);
   }
 }
 
-// Persistent grid: enough blocks to fill every SM at the kernel's occupancy,
-// but no more blocks than there are chunks to process.
-template <class Op, class T, class R> cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
+// Chunks [ch0, nchunk) of VW points read straight from global memory.
+template <class Op, class T, class R>
+__device__ __forceinline__ void global_chunks(const KArgs& a, const Consts<R>& k, int64_t ch0) {
+  constexpr int VW = Width<T, R>::VW;
+  const int64_t nchunk = (a.n + VW - 1) / VW;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t ch = ch0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunk; ch += stride) {
+    const int64_t i0 = ch * VW;
+    const int cnt = (a.n - i0 < VW) ? (int)(a.n - i0) : VW;
+    const GlobalSrc<T, VW> src{a, i0, cnt};
+    apply_chunk<Op, T, R>(a, k, src, i0, cnt);
+  }
+}
+
+template <class Op, class T, class R>
+__global__ void __launch_bounds__(kThreads) k_pointwise(const __grid_constant__ KArgs a) {
+  global_chunks<Op, T, R>(a, consts<R>(a), 0);
+}
+
+template <class Op, class T, class R>
+__global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KArgs a) {
+  constexpr int VW = Width<T, R>::VW;
+  constexpr int TILE = kThreads * VW;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  T* buf = reinterpret_cast<T*>(smem_raw);  // [kStages][nin][TILE]
+  const int nin = a.nin;
+  const int tid = threadIdx.x;
+  const int64_t ntiles = a.n / TILE;
+  const uint32_t plane_bytes = TILE * sizeof(T);
+  const Consts<R> k = consts<R>(a);
+  // The j-th tile of this block is tile blockIdx.x + j * gridDim.x, streamed
+  // into stage j % kStages; its copy completes phase j / kStages of that
+  // stage's mbarrier.
+  int issued = 0;  // tiles whose copies thread 0 has issued
+  auto issue = [&](int j) {
+    const int s = j % kStages;
+    const int64_t tile = blockIdx.x + (int64_t)j * gridDim.x;
+    mbar_expect_tx(&bars[s], nin * plane_bytes);
+    for (int q = 0; q < nin; ++q)
+      bulk_g2s(buf + ((size_t)s * nin + q) * TILE, inp<T>(a, q) + tile * TILE, plane_bytes, &bars[s]);
+    ++issued;
+  };
+  auto has_tile = [&](int j) { return blockIdx.x + (int64_t)j * gridDim.x < ntiles; };
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int j = 0; j < kStages && has_tile(j); ++j) issue(j);
+
+  int j = 0;
+  for (; has_tile(j); ++j) {
+    const int s = j % kStages;
+    const bool ok = mbar_wait(&bars[s], (uint32_t)(j / kStages) & 1u);
+    if (__syncthreads_or(!ok)) break;
+    const SmemSrc<T, VW, TILE> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW};
+    const int64_t i0 = (blockIdx.x + (int64_t)j * gridDim.x) * TILE + (int64_t)tid * VW;
+    apply_chunk<Op, T, R>(a, k, src, i0, VW);
+    __syncthreads();  // the whole block is done with stage s: refill it
+    if (tid == 0 && has_tile(j + kStages)) {
+      fence_proxy_async();
+      issue(j + kStages);
+    }
+  }
+  if (has_tile(j)) {
+    // A wait ran out: record it, wait (bounded again) for this block's copies
+    // still in flight so that none lands after the block exits, and return.
+    if (tid == 0) {
+      atomicAdd(&g_wait_timeouts, 1u);
+      for (int q = j; q < issued; ++q) mbar_wait(&bars[q % kStages], (uint32_t)(q / kStages) & 1u);
+    }
+    return;
+  }
+  // the ragged tail (fewer than TILE points) straight from global memory
+  global_chunks<Op, T, R>(a, k, ntiles * kThreads);
+}
+
+// Host: read and clear the timeout count of this translation unit.
+inline unsigned int take_wait_timeouts_tu() {
+  unsigned int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (v) cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(zero));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+// Persistent grid of the direct kernel: enough blocks to fill every SM at its
+// occupancy, no more than there are chunks.
+template <class Op, class T, class R> cudaError_t launch_direct(const KArgs& a, cudaStream_t stream) {
   static const int blocks_per_sm = [] {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pointwise<Op, T, R>, kThreads, 0) != cudaSuccess) b = 1;
@@ -421,6 +624,37 @@ template <class Op, class T, class R> cudaError_t launch_op(const KArgs& a, cuda
   const int grid = (int)(need < cap ? need : cap);
   k_pointwise<Op, T, R><<<grid, kThreads, 0, stream>>>(a);
   return cudaGetLastError();
+}
+
+// Staged kernel: kStages * nin planes of one tile in dynamic shared memory.
+template <class Op, class T, class R> cudaError_t launch_staged(const KArgs& a, cudaStream_t stream) {
+  constexpr int VW = Width<T, R>::VW;
+  constexpr int TILE = kThreads * VW;
+  constexpr size_t kMaxSmem = (size_t)kStages * Op::kIn * TILE * sizeof(T);
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_staged<Op, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  if (attr != cudaSuccess) return attr;
+  const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T);
+  static int bps_cache[Op::kIn + 1] = {};  // blocks per SM for each nin
+  int& bps = bps_cache[a.nin];
+  if (bps == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_staged<Op, T, R>, kThreads, smem) != cudaSuccess) b = 1;
+    bps = b > 0 ? b : 1;
+  }
+  const int64_t ntiles = a.n / TILE;
+  const int64_t cap = (int64_t)device_sm_count() * bps;
+  const int grid = (int)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
+  k_staged<Op, T, R><<<grid, kThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// The staged kernel pays off once every SM has a few tiles to stream.
+template <class Op, class T, class R> cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
+  constexpr int TILE = kThreads * Width<T, R>::VW;
+  if (a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn)
+    return launch_staged<Op, T, R>(a, stream);
+  return launch_direct<Op, T, R>(a, stream);
 }
 
 // Dispatch on (op, dim, dir) for storage type T and compute type R.

@@ -3,4 +3,5 @@
 
 namespace fdbb {
 cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a) { return dispatch<__half, float>(r, a); }
+unsigned int wait_timeouts_f16() { return take_wait_timeouts_tu(); }
 }  // namespace fdbb

@@ -4,4 +4,5 @@
 
 namespace fdbb {
 cudaError_t dispatch_f64dw(const LaunchReq& r, const KArgs& a) { return dispatch<double, dw>(r, a); }
+unsigned int wait_timeouts_f64dw() { return take_wait_timeouts_tu(); }
 }  // namespace fdbb
