@@ -27,13 +27,43 @@ namespace {
 
 constexpr int kFvThreads = FDBB_FV_TILE;
 
+// Tiles of the step kernel: a 32 x 8 (x, y) column segment of up to 32 planes.
+constexpr int kBX = 32, kBY = 8, kZSeg = 32;
+constexpr int kSX = kBX + 2, kSY = kBY + 2, kSlots = kSX * kSY;  // plane tile with a one-cell halo
+constexpr int kSlotVals = 23;  // U[5], F_x[5], F_y[5], F_z[5], |v_x|+c, |v_y|+c, |v_z|+c
+
 struct FvArgs {
   int ngrids;
   int64_t vcells;    // virtual cells (sum of padded grid sizes)
   double gamma, cfl;
   void* smax;        // 3 slots per grid, storage type T
+  int64_t tiles;     // step kernel: total tiles
   fdbb_fv_grid g[FDBB_FV_MAX_GRIDS];
+  int64_t tile_begin[FDBB_FV_MAX_GRIDS];  // step kernel: first tile of each grid
 };
+
+__host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Host: tile table of the step kernel.
+void fv_tiles(FvArgs& a) {
+  int64_t t = 0;
+  for (int i = 0; i < a.ngrids; ++i) {
+    const int n = a.g[i].n;
+    a.tile_begin[i] = t;
+    t += (int64_t)ceil_div(n, kBX) * ceil_div(n, kBY) * ceil_div(n, kZSeg);
+  }
+  a.tiles = t;
+}
+
+// Grid owning step tile vt (tile_begin is sorted).
+__device__ __forceinline__ int find_tile_grid(const FvArgs& a, int64_t vt) {
+  int lo = 0, hi = a.ngrids - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.tile_begin[mid] <= vt) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 // Grid owning virtual cell vc: the last descriptor with cell_begin <= vc
 // (descriptors are sorted by cell_begin).
@@ -123,84 +153,152 @@ template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_max_speed(
   }
 }
 
+// Shared-memory plane of a step tile: kSlotVals values for each of the kSlots
+// cells of a (32+2) x (8+2) plane tile, structure of arrays.
+template <class T> struct PlaneTile {
+  T v[kSlotVals][kSlots];
+};
+
+// State, the three flux columns and the three wave speeds |v_d| + c of the
+// cell (x, y, z) of grid g, into slot `slot` of plane tile P.
+template <class T>
+__device__ __forceinline__ void fill_slot(const fdbb_fv_grid& g, int x, int y, int z, const Consts<T>& k,
+                                          PlaneTile<T>& P, int slot) {
+  const int n = g.n;
+  Pt<T, 3> s;
+  cell_state<T>(g.U, ((int64_t)z * n + y) * n + x, k, s);
+  const T c = sqrt_(s.c2);
+  const T u[5] = {s.rho, s.m[0], s.m[1], s.m[2], s.rE};
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    P.v[q][slot] = u[q];
+    P.v[5 + q][slot] = flux_comp<3, 0>(s, q);
+    P.v[10 + q][slot] = flux_comp<3, 1>(s, q);
+    P.v[15 + q][slot] = flux_comp<3, 2>(s, q);
+  }
+  P.v[20][slot] = fabs(s.v[0]) + c;
+  P.v[21][slot] = fabs(s.v[1]) + c;
+  P.v[22][slot] = fabs(s.v[2]) + c;
+}
+
+// Rusanov flux through the face between slot l (left) and slot r (right) in
+// direction d, from plane tiles PL and PR.
+template <class T, int d>
+__device__ __forceinline__ void face(const PlaneTile<T>& PL, int l, const PlaneTile<T>& PR, int r, T (&Fh)[5]) {
+  const T sl = PL.v[20 + d][l], sr = PR.v[20 + d][r];
+  const T sm = sl > sr ? sl : sr;
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    Fh[q] = T(0.5f) * (PL.v[5 + 5 * d + q][l] + PR.v[5 + 5 * d + q][r]) - T(0.5f) * sm * (PR.v[q][r] - PL.v[q][l]);
+}
+
+// One step of every grid.  A block takes tiles of 32 x 8 cells in (x, y) and
+// up to 32 planes in z: plane by plane it fills the next plane's tile (cells
+// with a one-cell periodic halo in x and y: state, fluxes, wave speeds, each
+// computed once) into a double-buffered shared-memory plane, then updates its
+// own cells from the four x/y faces of the current plane and the z faces,
+// carrying the lower z face of the next plane in registers.
 template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_constant__ FvArgs a) {
-  __shared__ int s_grid;
+  extern __shared__ __align__(16) unsigned char fv_smem[];
+  PlaneTile<T>* tiles = reinterpret_cast<PlaneTile<T>*>(fv_smem);  // [2]
   const Consts<T> k = fv_consts<T>(a.gamma);
-  for (int64_t base = (int64_t)blockIdx.x * kFvThreads; base < a.vcells; base += (int64_t)gridDim.x * kFvThreads) {
-    if (threadIdx.x == 0) s_grid = find_grid(a, base);
-    __syncthreads();
-    const fdbb_fv_grid& g = a.g[s_grid];
-    __syncthreads();
-    T* smax = static_cast<T*>(a.smax) + 3 * g.slot;
+  const int tid = threadIdx.x, lx = tid % kBX, ly = tid / kBX;
+  const int own = (ly + 1) * kSX + (lx + 1);
+  for (int64_t vt = blockIdx.x; vt < a.tiles; vt += gridDim.x) {
+    const int gi = find_tile_grid(a, vt);
+    const fdbb_fv_grid& g = a.g[gi];
     const int n = g.n;
-    const int64_t ncell = (int64_t)n * n * n;
-    const int64_t c = base + threadIdx.x - g.cell_begin;
+    const int ntx = ceil_div(n, kBX), nty = ceil_div(n, kBY);
+    int64_t loc = vt - a.tile_begin[gi];
+    const int tx = (int)(loc % ntx);
+    loc /= ntx;
+    const int ty = (int)(loc % nty);
+    const int tz = (int)(loc / nty);
+    const int x0 = tx * kBX, y0 = ty * kBY, z0 = tz * kZSeg;
+    const int z1 = z0 + kZSeg < n ? z0 + kZSeg : n;
+    T* smax = static_cast<T*>(a.smax) + 3 * g.slot;
     const int ph = g.phase, ph1 = ph == 2 ? 0 : ph + 1, ph2 = ph1 == 2 ? 0 : ph1 + 1;
     const T dx = T(1) / T(n);
     const T dt = T(a.cfl) * dx / smax[ph];
-    if (c == 0) {
+    const T lam = dt / dx;
+    if (tx == 0 && ty == 0 && tz == 0 && tid == 0) {  // the grid's first tile
       smax[ph2] = T(0);  // read by the previous step, filled by the next one
       if (g.dt_log) g.dt_log[g.step] = static_cast<double>(dt);
     }
-    T v = T(0);
-    if (c < ncell) {
-      const int i = (int)(c % n), j = (int)((c / n) % n), kk = (int)(c / ((int64_t)n * n));
-      const int im = i == 0 ? n - 1 : i - 1, ip = i == n - 1 ? 0 : i + 1;
-      const int jm = j == 0 ? n - 1 : j - 1, jp = j == n - 1 ? 0 : j + 1;
-      const int km = kk == 0 ? n - 1 : kk - 1, kp = kk == n - 1 ? 0 : kk + 1;
-      auto idx = [n](int x, int y, int z) { return ((int64_t)z * n + y) * n + x; };
-      Pt<T, 3> C, M, P;
-      cell_state<T>(g.U, c, k, C);
-      T div[5] = {T(0), T(0), T(0), T(0), T(0)};
-      T Fm[5], Fp[5];
-      // x faces
-      cell_state<T>(g.U, idx(im, j, kk), k, M);
-      cell_state<T>(g.U, idx(ip, j, kk), k, P);
-      face_flux<T, 0>(M, C, Fm);
-      face_flux<T, 0>(C, P, Fp);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) div[q] = div[q] + (Fp[q] - Fm[q]);
-      // y faces
-      cell_state<T>(g.U, idx(i, jm, kk), k, M);
-      cell_state<T>(g.U, idx(i, jp, kk), k, P);
-      face_flux<T, 1>(M, C, Fm);
-      face_flux<T, 1>(C, P, Fp);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) div[q] = div[q] + (Fp[q] - Fm[q]);
-      // z faces
-      cell_state<T>(g.U, idx(i, j, km), k, M);
-      cell_state<T>(g.U, idx(i, j, kp), k, P);
-      face_flux<T, 2>(M, C, Fm);
-      face_flux<T, 2>(C, P, Fp);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) div[q] = div[q] + (Fp[q] - Fm[q]);
-      const T lam = dt / dx;
-      const T u0[5] = {C.rho, C.m[0], C.m[1], C.m[2], C.rE};
-      Pt<T, 3> N;
-      T un[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        un[q] = u0[q] - lam * div[q];
-        static_cast<T*>(g.Unew[q])[c] = un[q];
+    const int x = x0 + lx, y = y0 + ly;
+    const bool active = x < n && y < n;
+    auto fill = [&](PlaneTile<T>& P, int z) {
+      for (int sl = tid; sl < kSlots; sl += kFvThreads) {
+        const int sx = sl % kSX, sy = sl / kSX;
+        fill_slot<T>(g, (x0 + sx - 1 + n) % n, (y0 + sy - 1 + n) % n, z, k, P, sl);
       }
-      N.rho = un[0];
-      N.m[0] = un[1];
-      N.m[1] = un[2];
-      N.m[2] = un[3];
-      N.rE = un[4];
-      NoGuard ng;
-      derive(N, k, ng);
-      v = wave_speed_sum(N);
+    };
+    // lower z face of the first plane: the own cell of plane z0 - 1 (periodic)
+    fill(tiles[0], z0);
+    T zlo[5];
+    __syncthreads();
+    if (active) {
+      PlaneTile<T>& P1 = tiles[1];  // its own slot only, as scratch for the face
+      fill_slot<T>(g, x, y, z0 == 0 ? n - 1 : z0 - 1, k, P1, own);
+      face<T, 2>(P1, own, tiles[0], own, zlo);
     }
-    v = warp_max(v);
-    if ((threadIdx.x & 31) == 0 && v > T(0)) atomic_max_pos(smax + ph1, v);
+    __syncthreads();
+    T vmax = T(0);
+    for (int z = z0; z < z1; ++z) {
+      const PlaneTile<T>& C = tiles[(z - z0) & 1];
+      PlaneTile<T>& N = tiles[((z - z0) & 1) ^ 1];
+      fill(N, z + 1 == n ? 0 : z + 1);
+      __syncthreads();
+      if (active) {
+        T lo[5], hi[5], div[5];
+        face<T, 0>(C, own - 1, C, own, lo);
+        face<T, 0>(C, own, C, own + 1, hi);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) div[q] = T(0) + (hi[q] - lo[q]);
+        face<T, 1>(C, own - kSX, C, own, lo);
+        face<T, 1>(C, own, C, own + kSX, hi);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) div[q] = div[q] + (hi[q] - lo[q]);
+        face<T, 2>(C, own, N, own, hi);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          div[q] = div[q] + (hi[q] - zlo[q]);
+          zlo[q] = hi[q];
+        }
+        const int64_t c = ((int64_t)z * n + y) * n + x;
+        Pt<T, 3> Nw;
+        T un[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          un[q] = C.v[q][own] - lam * div[q];
+          static_cast<T*>(g.Unew[q])[c] = un[q];
+        }
+        Nw.rho = un[0];
+        Nw.m[0] = un[1];
+        Nw.m[1] = un[2];
+        Nw.m[2] = un[3];
+        Nw.rE = un[4];
+        NoGuard ng;
+        derive(Nw, k, ng);
+        const T w = wave_speed_sum(Nw);
+        vmax = w > vmax ? w : vmax;
+      }
+      __syncthreads();  // the next iteration refills the current plane
+    }
+    vmax = warp_max(vmax);
+    if ((tid & 31) == 0 && vmax > T(0)) atomic_max_pos(smax + ph1, vmax);
   }
 }
+
+constexpr size_t fv_step_smem(size_t es) { return 2 * (size_t)kSlotVals * kSlots * es; }
 
 template <class T> int fv_blocks_per_sm(bool step) {
   static const int bs = [] {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fv_rusanov_step<T>, kFvThreads, 0) != cudaSuccess) b = 1;
+    cudaFuncSetAttribute(k_fv_rusanov_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fv_step_smem(sizeof(T)));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fv_rusanov_step<T>, kFvThreads, fv_step_smem(sizeof(T))) !=
+        cudaSuccess)
+      b = 1;
     return b > 0 ? b : 1;
   }();
   static const int bm = [] {
@@ -212,11 +310,12 @@ template <class T> int fv_blocks_per_sm(bool step) {
 }
 
 template <class T> cudaError_t fv_launch(const FvArgs& a, bool step, cudaStream_t s) {
-  const int64_t tiles = a.vcells / kFvThreads;
+  const int64_t work = step ? a.tiles : a.vcells / kFvThreads;
   const int64_t cap = (int64_t)device_sm_count() * fv_blocks_per_sm<T>(step);
-  const int grid = (int)(tiles < cap ? tiles : cap);
+  const int grid = (int)(work < cap ? work : cap);
+  if (grid <= 0) return cudaSuccess;
   if (step)
-    k_fv_rusanov_step<T><<<grid, kFvThreads, 0, s>>>(a);
+    k_fv_rusanov_step<T><<<grid, kFvThreads, fv_step_smem(sizeof(T)), s>>>(a);
   else
     k_fv_max_speed<T><<<grid, kFvThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -269,6 +368,7 @@ fdbb_status fv_run(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double
   a.cfl = cfl;
   a.smax = smax;
   for (int i = 0; i < ngrids; ++i) a.g[i] = grids[i];
+  fv_tiles(a);
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const cudaError_t e = t == FDBB_F64 ? fv_launch<double>(a, step, s) : fv_launch<float>(a, step, s);
   return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
@@ -330,6 +430,7 @@ fdbb_status fv_step_noalloc(int ngrids, const fdbb_fv_grid* grids, int64_t vcell
   const fdbb_status st = fv_check(ngrids, a.g, vcells, t, scratch, true, nullptr);
   if (st != FDBB_OK) return st;
   if (ngrids == 0 || vcells == 0) return FDBB_OK;
+  fv_tiles(a);
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // the slots keep the previous call's contents: clear them first
   if (cudaMemsetAsync(scratch, 0, sizeof(double) * 3 * (size_t)ngrids, s) != cudaSuccess) {
