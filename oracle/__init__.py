@@ -44,6 +44,8 @@ def _load():
             "oracle_flux_vjp": [ci, ci, dbl, i64, vp, vp, vp, vp],
             "oracle_euler_fused": [ci, ci, dbl, i64, vp, vp, vp, vp],
             "oracle_eig": [ci, ci, dbl, i64, vp, vp, vp, vp],
+            "oracle_roe_flux": [ci, ci, dbl, i64, vp, vp, vp, vp],
+            "oracle_roe_char_transform": [ci, ci, dbl, ci, i64, vp, vp, vp, vp, vp],
             "oracle_rusanov_step": [ci, dbl, dbl, vp, vp],
             "oracle_rusanov_run": [ci, dbl, dbl, ci, vp, vp, vp],
         }
@@ -156,6 +158,22 @@ def euler_fused(D, dj, gamma, U, W, scale=False):
     return _call(_load().oracle_euler_fused, k, n, (D, dj, gamma, n, pu, pw), scale)
 
 
+def roe_flux(D, d, gamma, UL, UR, scale=False):
+    """Roe flux between UL and UR in direction d (nv planes)."""
+    pl, Lk, n = _planes(UL)
+    pr, Rk, _ = _planes(UR, n)
+    return _call(_load().oracle_roe_flux, nv(D), n, (D, d, gamma, n, pl, pr), scale)
+
+
+def roe_char_transform(D, d, gamma, UL, UR, W, inverse=False, scale=False):
+    """L^ W (or R^ W) at the Roe-averaged state of (UL, UR)."""
+    pl, Lk, n = _planes(UL)
+    pr, Rk, _ = _planes(UR, n)
+    pw, Wk, _ = _planes(W, n)
+    return _call(_load().oracle_roe_char_transform, nv(D), n,
+                 (D, d, gamma, int(bool(inverse)), n, pl, pr, pw), scale)
+
+
 def eig(D, d, gamma, U):
     """(R, L, lam): R columns are right eigenvectors, L = R^-1, as plane lists."""
     pu, Uk, n = _planes(U)
@@ -200,5 +218,5 @@ def rusanov_run(n, gamma, cfl, steps, U):
 __all__ = [
     "v_mag2", "prim_from_cons", "cons_from_prim", "eos", "riemann_inv", "flux",
     "flux_jac", "char_transform", "flux_vjp", "euler_fused", "eig", "rusanov_dt",
-    "rusanov_step", "rusanov_run", "library_path", "nv",
+    "rusanov_step", "rusanov_run", "roe_flux", "roe_char_transform", "library_path", "nv",
 ]

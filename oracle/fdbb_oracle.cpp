@@ -76,6 +76,8 @@ inline Err sqrt_(Err a) {
   return {v, v + prop};
 }
 inline double sqrt_(double a) { return std::sqrt(a); }
+inline double abs_(double a) { return std::fabs(a); }
+inline Err abs_(Err a) { return {std::fabs(a.v), a.s}; }
 
 // x^y for x > 0 (entropy p / rho^gamma); libm pow is within about 1 ulp.
 inline double pow_(double x, double y) { return std::pow(x, y); }
@@ -294,6 +296,45 @@ template <class T> void matvec_t(int nv, const T* M, const T* x, T* y) {
   }
 }
 
+// Roe-averaged state between left and right states (P. L. Roe, J. Comput.
+// Phys. 43, 1981; Toro ch. 11): with w = sqrt(rho),
+//   v^ = (w_L v_L + w_R v_R) / (w_L + w_R),  H^ = (w_L H_L + w_R H_R) / (w_L + w_R),
+//   q^ = |v^|^2 / 2,  c^ = sqrt((gamma - 1)(H^ - q^)).
+// Only the fields the eigenvectors use (v, q, H, c, gamma, a1) are set.
+template <class T> State<T> roe_state(const State<T>& L, const State<T>& R) {
+  State<T> s = L;
+  const T wL = sqrt_(L.rho), wR = sqrt_(R.rho);
+  const T den = wL + wR;
+  for (int i = 0; i < L.D; ++i) s.v[i] = (wL * L.v[i] + wR * R.v[i]) / den;
+  s.H = (wL * L.H + wR * R.H) / den;
+  T v2 = s.v[0] * s.v[0];
+  for (int i = 1; i < L.D; ++i) v2 = v2 + s.v[i] * s.v[i];
+  s.q = lit<T>(0.5) * v2;
+  s.c = sqrt_(s.a1 * (s.H - s.q));
+  return s;
+}
+
+// Roe flux in direction d: Fh = (F_d(U_L) + F_d(U_R))/2 - 1/2 sum_k |lambda^_k|
+// alpha_k r^_k with alpha = L^ (U_R - U_L), all at the Roe state.
+template <class T> void roe_flux_d(const State<T>& L, const State<T>& R, int d, T* Fh) {
+  const int D = L.D, nv = D + 2;
+  T fL[5], fR[5], Rm[25], Lm[25], lam[5], dU[5], alpha[5];
+  flux_d(L, d, fL);
+  flux_d(R, d, fR);
+  const State<T> s = roe_state(L, R);
+  right_eig_d(s, d, Rm, lam);
+  left_eig_d(s, d, Lm);
+  dU[0] = R.rho - L.rho;
+  for (int i = 0; i < D; ++i) dU[1 + i] = R.m[i] - L.m[i];
+  dU[nv - 1] = R.rhoE - L.rhoE;
+  matvec(nv, Lm, dU, alpha);
+  for (int q = 0; q < nv; ++q) {
+    T diss = abs_(lam[0]) * alpha[0] * Rm[q * nv + 0];
+    for (int k = 1; k < nv; ++k) diss = diss + abs_(lam[k]) * alpha[k] * Rm[q * nv + k];
+    Fh[q] = lit<T>(0.5) * (fL[q] + fR[q]) - lit<T>(0.5) * diss;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Plane output helpers
 // ---------------------------------------------------------------------------
@@ -476,6 +517,41 @@ void run_fused(int D, int dj, double g, int64_t n, const double* const* U, const
   }
 }
 
+template <class T>
+void run_roe_flux(int D, int d, double g, int64_t n, const double* const* UL, const double* const* UR,
+                  double* const* F, double* const* sc) {
+  // Roe flux between the states UL and UR of each point (direction d).
+  const int nv = D + 2;
+  T f[5];
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> L = state_from_cons<T>(D, g, UL, i);
+    State<T> R = state_from_cons<T>(D, g, UR, i);
+    roe_flux_d(L, R, d, f);
+    for (int k = 0; k < nv; ++k) put(F, sc, k, i, f[k]);
+  }
+}
+
+template <class T>
+void run_roe_char(int D, int d, double g, int inverse, int64_t n, const double* const* UL,
+                  const double* const* UR, const double* const* W, double* const* Y, double* const* sc) {
+  // Characteristic transform at the Roe-averaged state of (UL, UR):
+  // forward Y = L^ W, inverse Y = R^ W.
+  const int nv = D + 2;
+  T M[25], w[5], y[5];
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> L = state_from_cons<T>(D, g, UL, i);
+    State<T> R = state_from_cons<T>(D, g, UR, i);
+    const State<T> s = roe_state(L, R);
+    if (inverse)
+      right_eig_d(s, d, M, (T*)nullptr);
+    else
+      left_eig_d(s, d, M);
+    for (int k = 0; k < nv; ++k) w[k] = lit<T>(W[k][i]);
+    matvec(nv, M, w, y);
+    for (int k = 0; k < nv; ++k) put(Y, sc, k, i, y[k]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Explicit first-order finite-volume step with the Rusanov (local
 // Lax-Friedrichs) numerical flux on a periodic n^3 grid over [0,1]^3.
@@ -628,6 +704,23 @@ int oracle_euler_fused(int D, int dj, double g, int64_t n, const double* const* 
   if (bad_dim(D) || dj < 0 || dj >= D || n < 0 || !(g > 1.0)) return 1;
   run_fused<double>(D, dj, g, n, U, W, out, nullptr);
   if (scale) run_fused<Err>(D, dj, g, n, U, W, nullptr, scale);
+  return 0;
+}
+
+int oracle_roe_flux(int D, int d, double g, int64_t n, const double* const* UL, const double* const* UR,
+                    double* const* F, double* const* scale) {
+  if (bad_dim(D) || d < 0 || d >= D || n < 0 || !(g > 1.0)) return 1;
+  run_roe_flux<double>(D, d, g, n, UL, UR, F, nullptr);
+  if (scale) run_roe_flux<Err>(D, d, g, n, UL, UR, nullptr, scale);
+  return 0;
+}
+
+int oracle_roe_char_transform(int D, int d, double g, int inverse, int64_t n, const double* const* UL,
+                              const double* const* UR, const double* const* W, double* const* Y,
+                              double* const* scale) {
+  if (bad_dim(D) || d < 0 || d >= D || n < 0 || !(g > 1.0)) return 1;
+  run_roe_char<double>(D, d, g, inverse, n, UL, UR, W, Y, nullptr);
+  if (scale) run_roe_char<Err>(D, d, g, inverse, n, UL, UR, W, nullptr, scale);
   return 0;
 }
 

@@ -488,3 +488,84 @@ def test_rusanov_is_monotone_and_dissipative():
         r2 = U2[0]
         assert r2.max() <= 2.0 + 1e-12 and r2.min() >= 1.0 - 1e-12
         assert r2.var() < var0
+
+
+# ---------------------------------------------------------------------------
+# Roe flux and Roe-averaged characteristic transform
+# ---------------------------------------------------------------------------
+
+def _pair(n, D, seed):
+    UL, _ = _rand_U(n, D, seed=seed)
+    UR, _ = _rand_U(n, D, seed=seed + 1)
+    return UL, UR
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_roe_flux_consistency(D):
+    """Fh(U, U) = F(U): no dissipation between equal states."""
+    U, _ = _rand_U(500, D, seed=51)
+    for d in range(D):
+        np.testing.assert_array_equal(_stack(oracle.roe_flux(D, d, GAMMA, U, U)),
+                                      _stack(oracle.flux(D, d, GAMMA, U)))
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_roe_property(D):
+    """Roe's matrix A^ = R^ Lambda^ L^ at the averaged state satisfies
+    A^ (U_R - U_L) = F(U_R) - F(U_L) for the ideal gas; with the Roe flux this
+    reads Fh = F(U_L) + sum_{lambda<0} ... , equivalently
+    F(U_R) - F(U_L) = 2 (Fh - F(U_L)) + sum |lambda| alpha r - ... ; tested as
+    (F_L + F_R)/2 - Fh = 1/2 sum |lambda^| alpha r with A^ dU = F_R - F_L."""
+    UL, UR = _pair(800, D, 61)
+    nv = D + 2
+    dU = _stack(UR) - _stack(UL)
+    for d in range(D):
+        FL = _stack(oracle.flux(D, d, GAMMA, UL))
+        FR = _stack(oracle.flux(D, d, GAMMA, UR))
+        # Roe-averaged eigen-decomposition through the characteristic transform
+        # at the Roe state: alpha = L^ dU, A^ dU = R^ (lambda^ * alpha)
+        alpha = _stack(oracle.roe_char_transform(D, d, GAMMA, UL, UR, [dU[:, k] for k in range(nv)]))
+        # eigenvalues of A^: u^ - c^, u^, u^ + c^ from the Roe state via R^ applied to unit vectors
+        Rm = np.stack([_stack(oracle.roe_char_transform(D, d, GAMMA, UL, UR,
+                                                          [np.full(dU.shape[0], float(k == j)) for k in range(nv)],
+                                                          inverse=True)) for j in range(nv)], axis=-1)
+        # u^ and c^: R^ columns r_1 = (1, v - c e_d, .) and r_nv = (1, v + c e_d, .)
+        u_hat = 0.5 * (Rm[:, 1 + d, 0] + Rm[:, 1 + d, nv - 1])
+        c_hat = 0.5 * (Rm[:, 1 + d, nv - 1] - Rm[:, 1 + d, 0])
+        lam = np.stack([u_hat - c_hat] + [u_hat] * (nv - 2) + [u_hat + c_hat], axis=-1)
+        AdU = np.einsum("nij,nj->ni", Rm, lam * alpha)
+        scale = np.abs(FL) + np.abs(FR) + 1.0
+        assert np.all(np.abs(AdU - (FR - FL)) <= 1e-10 * scale), d
+        # and the flux itself
+        Fh = _stack(oracle.roe_flux(D, d, GAMMA, UL, UR))
+        diss = np.einsum("nij,nj->ni", Rm, np.abs(lam) * alpha)
+        np.testing.assert_allclose(Fh, 0.5 * (FL + FR) - 0.5 * diss, rtol=1e-12, atol=1e-10)
+
+
+def test_roe_average_of_equal_states_is_the_state():
+    U, _ = _rand_U(300, 3, seed=71)
+    W = synth.char_weights(300)
+    for d in range(3):
+        for inv in (False, True):
+            np.testing.assert_allclose(_stack(oracle.roe_char_transform(3, d, GAMMA, U, U, W, inverse=inv)),
+                                       _stack(oracle.char_transform(3, d, GAMMA, U, W, inverse=inv)),
+                                       rtol=1e-13, atol=1e-13)
+
+
+def test_roe_flux_upwinds_supersonic_flow():
+    """All Roe eigenvalues positive (flow at Mach ~5 along x on both sides):
+    the Roe flux is the left state's flux."""
+    n = 400
+    VL = synth.euler3d(n, seed=81)
+    VR = synth.euler3d(n, seed=82)
+    for V in (VL, VR):
+        V[0][:] = 1.0 + 0.2 * (V[0] / 10.0)
+        V[4][:] = 1.0 + 0.2 * (V[4] / 10.0)
+        V[1][:] = 8.0
+        V[2][:] = 0.1 * V[2]
+        V[3][:] = 0.1 * V[3]
+    UL = oracle.cons_from_prim(3, GAMMA, VL)
+    UR = oracle.cons_from_prim(3, GAMMA, VR)
+    Fh = _stack(oracle.roe_flux(3, 0, GAMMA, UL, UR))
+    FL = _stack(oracle.flux(3, 0, GAMMA, UL))
+    np.testing.assert_allclose(Fh, FL, rtol=1e-12, atol=1e-12)
