@@ -45,6 +45,9 @@ def _load():
             "oracle_euler_fused": [ci, ci, dbl, i64, vp, vp, vp, vp],
             "oracle_eig": [ci, ci, dbl, i64, vp, vp, vp, vp],
             "oracle_roe_flux": [ci, ci, dbl, i64, vp, vp, vp, vp],
+            "oracle_flux_prim": [ci, ci, dbl, i64, vp, vp, vp],
+            "oracle_flux_jac_prim": [ci, ci, dbl, i64, vp, vp, vp],
+            "oracle_temperature": [ci, dbl, dbl, i64, vp, vp, vp],
             "oracle_roe_char_transform": [ci, ci, dbl, ci, i64, vp, vp, vp, vp, vp],
             "oracle_rusanov_step": [ci, dbl, dbl, vp, vp],
             "oracle_rusanov_run": [ci, dbl, dbl, ci, vp, vp, vp],
@@ -158,6 +161,25 @@ def euler_fused(D, dj, gamma, U, W, scale=False):
     return _call(_load().oracle_euler_fused, k, n, (D, dj, gamma, n, pu, pw), scale)
 
 
+def flux_prim(D, d, gamma, V, scale=False):
+    """Inviscid flux from primitive variables V (F_d, or all directions for d == -1)."""
+    pv, Vk, n = _planes(V)
+    k = nv(D) * (D if d < 0 else 1)
+    return _call(_load().oracle_flux_prim, k, n, (D, d, gamma, n, pv), scale)
+
+
+def flux_jac_prim(D, d, gamma, V, scale=False):
+    """dF_d/dV, nv*nv planes row-major (rows in U order, columns in V order)."""
+    pv, Vk, n = _planes(V)
+    return _call(_load().oracle_flux_jac_prim, nv(D) ** 2, n, (D, d, gamma, n, pv), scale)
+
+
+def temperature(D, gamma, cv, U, scale=False):
+    """[T] with T = e / c_v."""
+    pu, Uk, n = _planes(U)
+    return _call(_load().oracle_temperature, 1, n, (D, gamma, cv, n, pu), scale)
+
+
 def roe_flux(D, d, gamma, UL, UR, scale=False):
     """Roe flux between UL and UR in direction d (nv planes)."""
     pl, Lk, n = _planes(UL)
@@ -218,5 +240,6 @@ def rusanov_run(n, gamma, cfl, steps, U):
 __all__ = [
     "v_mag2", "prim_from_cons", "cons_from_prim", "eos", "riemann_inv", "flux",
     "flux_jac", "char_transform", "flux_vjp", "euler_fused", "eig", "rusanov_dt",
-    "rusanov_step", "rusanov_run", "roe_flux", "roe_char_transform", "library_path", "nv",
+    "rusanov_step", "rusanov_run", "roe_flux", "roe_char_transform", "flux_prim", "flux_jac_prim", "temperature",
+    "library_path", "nv",
 ]

@@ -296,6 +296,65 @@ template <class T> void matvec_t(int nv, const T* M, const T* x, T* y) {
   }
 }
 
+// Primitive-variable forms (paper section 2.2, Fig. 9: Variables<eos, dim,
+// EnumForm::primitive>, V = (rho, v, p)).
+//   Flux from V: F_d = (rho u, rho u v + p e_d, u (gamma/(gamma-1) p + rho |v|^2/2)),
+//   u = v_d (the same physical flux, written in V).
+template <class T> void flux_prim_d(int D, double g, const double* const* V, int64_t i, int d, T* F) {
+  const T gamma = lit<T>(g), a1 = gamma - lit<T>(1.0);
+  const T rho = lit<T>(V[0][i]), p = lit<T>(V[D + 1][i]);
+  T v[3];
+  for (int k = 0; k < D; ++k) v[k] = lit<T>(V[1 + k][i]);
+  T v2 = v[0] * v[0];
+  for (int k = 1; k < D; ++k) v2 = v2 + v[k] * v[k];
+  const T u = v[d];
+  F[0] = rho * u;
+  for (int k = 0; k < D; ++k) {
+    F[1 + k] = rho * u * v[k];
+    if (k == d) F[1 + k] = F[1 + k] + p;
+  }
+  F[D + 1] = u * (gamma / a1 * p + lit<T>(0.5) * rho * v2);
+}
+
+// Jacobian of that flux with respect to V, B_d = dF_d/dV (row-major, rows in
+// U order, columns in V order), from differentiating the formula above:
+//   row 0    : (u, rho at col 1+d, 0)
+//   row 1+i  : (u v_i, rho (delta_jd v_i + delta_ij u) at col 1+j, delta_id at col nv-1)
+//   row nv-1 : (u |v|^2/2, delta_jd (gamma/(gamma-1) p + rho |v|^2/2) + rho u v_j at col 1+j,
+//               gamma/(gamma-1) u at col nv-1)
+template <class T> void jac_prim_d(int D, double g, const double* const* V, int64_t i, int d, T* B) {
+  const int nv = D + 2;
+  const T gamma = lit<T>(g), a1 = gamma - lit<T>(1.0), zero = lit<T>(0.0), one = lit<T>(1.0);
+  const T rho = lit<T>(V[0][i]), p = lit<T>(V[D + 1][i]);
+  T v[3];
+  for (int k = 0; k < D; ++k) v[k] = lit<T>(V[1 + k][i]);
+  T v2 = v[0] * v[0];
+  for (int k = 1; k < D; ++k) v2 = v2 + v[k] * v[k];
+  const T u = v[d];
+  for (int k = 0; k < nv * nv; ++k) B[k] = zero;
+  B[0] = u;
+  B[1 + d] = rho;
+  for (int r = 0; r < D; ++r) {
+    T* row = B + (1 + r) * nv;
+    row[0] = u * v[r];
+    for (int j = 0; j < D; ++j) {
+      T e = zero;
+      if (j == d) e = e + rho * v[r];
+      if (j == r) e = e + rho * u;
+      row[1 + j] = e;
+    }
+    row[nv - 1] = (r == d) ? one : zero;
+  }
+  T* last = B + (nv - 1) * nv;
+  last[0] = lit<T>(0.5) * u * v2;
+  for (int j = 0; j < D; ++j) {
+    T e = rho * u * v[j];
+    if (j == d) e = e + (gamma / a1 * p + lit<T>(0.5) * rho * v2);
+    last[1 + j] = e;
+  }
+  last[nv - 1] = gamma / a1 * u;
+}
+
 // Roe-averaged state between left and right states (P. L. Roe, J. Comput.
 // Phys. 43, 1981; Toro ch. 11): with w = sqrt(rho),
 //   v^ = (w_L v_L + w_R v_R) / (w_L + w_R),  H^ = (w_L H_L + w_R H_R) / (w_L + w_R),
@@ -518,6 +577,44 @@ void run_fused(int D, int dj, double g, int64_t n, const double* const* U, const
 }
 
 template <class T>
+void run_flux_prim(int D, int dir, double g, int64_t n, const double* const* V, double* const* F,
+                   double* const* sc) {
+  const int nv = D + 2;
+  T f[5];
+  for (int64_t i = 0; i < n; ++i)
+    for (int d = 0; d < D; ++d) {
+      if (dir >= 0 && d != dir) continue;
+      flux_prim_d<T>(D, g, V, i, d, f);
+      const int base = (dir < 0) ? d * nv : 0;
+      for (int k = 0; k < nv; ++k) put(F, sc, base + k, i, f[k]);
+    }
+}
+
+template <class T>
+void run_jac_prim(int D, int d, double g, int64_t n, const double* const* V, double* const* B,
+                  double* const* sc) {
+  const int nv = D + 2;
+  T b[25];
+  for (int64_t i = 0; i < n; ++i) {
+    jac_prim_d<T>(D, g, V, i, d, b);
+    for (int k = 0; k < nv * nv; ++k) put(B, sc, k, i, b[k]);
+  }
+}
+
+template <class T>
+void run_temperature(int D, double g, double cv, int64_t n, const double* const* U, double* const* out,
+                     double* const* sc) {
+  // Temperature of the perfect gas from (rho, e) (paper section 2.2,
+  // "Equations of state", the T_rhoe member of the EOS prototype, Fig. 10):
+  // T = e / c_v, e = (rhoE - rho q) / rho.
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons<T>(D, g, U, i);
+    const T e = (s.rhoE - s.rho * s.q) / s.rho;
+    put(out, sc, 0, i, e / lit<T>(cv));
+  }
+}
+
+template <class T>
 void run_roe_flux(int D, int d, double g, int64_t n, const double* const* UL, const double* const* UR,
                   double* const* F, double* const* sc) {
   // Roe flux between the states UL and UR of each point (direction d).
@@ -704,6 +801,30 @@ int oracle_euler_fused(int D, int dj, double g, int64_t n, const double* const* 
   if (bad_dim(D) || dj < 0 || dj >= D || n < 0 || !(g > 1.0)) return 1;
   run_fused<double>(D, dj, g, n, U, W, out, nullptr);
   if (scale) run_fused<Err>(D, dj, g, n, U, W, nullptr, scale);
+  return 0;
+}
+
+int oracle_flux_prim(int D, int dir, double g, int64_t n, const double* const* V, double* const* F,
+                     double* const* scale) {
+  if (bad_dim(D) || dir < -1 || dir >= D || n < 0 || !(g > 1.0)) return 1;
+  run_flux_prim<double>(D, dir, g, n, V, F, nullptr);
+  if (scale) run_flux_prim<Err>(D, dir, g, n, V, nullptr, scale);
+  return 0;
+}
+
+int oracle_flux_jac_prim(int D, int d, double g, int64_t n, const double* const* V, double* const* B,
+                         double* const* scale) {
+  if (bad_dim(D) || d < 0 || d >= D || n < 0 || !(g > 1.0)) return 1;
+  run_jac_prim<double>(D, d, g, n, V, B, nullptr);
+  if (scale) run_jac_prim<Err>(D, d, g, n, V, nullptr, scale);
+  return 0;
+}
+
+int oracle_temperature(int D, double g, double cv, int64_t n, const double* const* U, double* const* out,
+                       double* const* scale) {
+  if (bad_dim(D) || n < 0 || !(g > 1.0) || !(cv > 0.0)) return 1;
+  run_temperature<double>(D, g, cv, n, U, out, nullptr);
+  if (scale) run_temperature<Err>(D, g, cv, n, U, nullptr, scale);
   return 0;
 }
 

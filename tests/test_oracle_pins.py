@@ -569,3 +569,59 @@ def test_roe_flux_upwinds_supersonic_flow():
     Fh = _stack(oracle.roe_flux(3, 0, GAMMA, UL, UR))
     FL = _stack(oracle.flux(3, 0, GAMMA, UL))
     np.testing.assert_allclose(Fh, FL, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# primitive-variable forms and temperature
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_flux_from_primitives_is_the_flux(D):
+    U, V = _rand_U(1500, D, seed=91)
+    Vp = oracle.prim_from_cons(D, GAMMA, U)
+    for d in [-1, *range(D)]:
+        np.testing.assert_allclose(_stack(oracle.flux_prim(D, d, GAMMA, Vp)), _stack(oracle.flux(D, d, GAMMA, U)),
+                                   rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_primitive_jacobian_chain_rule_and_differences(D):
+    """dF/dV = A(U) dU/dV with dU/dV of U = (rho, rho v, p/(gamma-1) + rho|v|^2/2);
+    and central differences of the primitive flux."""
+    U, V = _rand_U(400, D, seed=93)
+    V = oracle.prim_from_cons(D, GAMMA, U)
+    nv = D + 2
+    n = V[0].shape[0]
+    rho = V[0]
+    v = np.stack(V[1:D + 1], -1)
+    dUdV = np.zeros((n, nv, nv))
+    dUdV[:, 0, 0] = 1.0
+    for i in range(D):
+        dUdV[:, 1 + i, 0] = v[:, i]
+        dUdV[:, 1 + i, 1 + i] = rho
+        dUdV[:, nv - 1, 1 + i] = rho * v[:, i]
+    dUdV[:, nv - 1, 0] = 0.5 * (v ** 2).sum(-1)
+    dUdV[:, nv - 1, nv - 1] = 1.0 / (GAMMA - 1.0)
+    for d in range(D):
+        B = _stack(oracle.flux_jac_prim(D, d, GAMMA, V)).reshape(-1, nv, nv)
+        A = _stack(oracle.flux_jac(D, d, GAMMA, U)).reshape(-1, nv, nv)
+        np.testing.assert_allclose(B, A @ dUdV, rtol=1e-11, atol=1e-11)
+        for j in range(nv):
+            h = 1e-6 * np.maximum(1.0, np.abs(V[j]))
+            Vp = [x.copy() for x in V]
+            Vm = [x.copy() for x in V]
+            Vp[j] += h
+            Vm[j] -= h
+            fd = (_stack(oracle.flux_prim(D, d, GAMMA, Vp)) - _stack(oracle.flux_prim(D, d, GAMMA, Vm))) / (2 * h)[:, None]
+            assert np.all(np.abs(fd - B[:, :, j]) <= 1e-6 * (np.abs(B).max(axis=(1, 2))[:, None] + 1.0))
+
+
+@pytest.mark.parametrize("D", [1, 3])
+def test_temperature_is_the_ideal_gas_law(D):
+    """With the paper's c_p = 7/2, c_v = 5/2 (gamma = 7/5, R = c_p - c_v = 1):
+    p = rho R T, i.e. T = p / rho; for another c_v, T scales as 1/c_v."""
+    U, V = _rand_U(1000, D, seed=95)
+    T = oracle.temperature(D, GAMMA, 2.5, U)[0]
+    np.testing.assert_allclose(T, V[D + 1] / V[0], rtol=1e-13)
+    T2 = oracle.temperature(D, GAMMA, 5.0, U)[0]
+    np.testing.assert_allclose(T2, 0.5 * T, rtol=1e-15)
