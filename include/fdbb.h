@@ -87,7 +87,7 @@ typedef enum {
  *               derived quantity (v, |v|^2/2, p, H, c^2) is non-zero with
  *               magnitude outside [2^-24, 2^24], or not finite, is computed in
  *               IEEE double instead.  Outputs that are copies of an input are
- *               bit-exact.  The inverse characteristic transform always uses
+ *               bit-exact.  The inverse characteristic transforms always use
  *               IEEE double.  On GPUs whose FP64 rate is a small fraction of
  *               the FP32 rate (GB300: 1/64) this is the fast FP64-storage form.
  */
@@ -206,6 +206,62 @@ FDBB_API fdbb_status fdbb_euler_fused(int dim, int dir_jac, double gamma, int64_
 FDBB_API fdbb_status fdbb_flux_vjp(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
                           const void *const *U, const void *const *G, void *const *gU,
                           fdbb_stream_t stream);
+
+/*
+ * Primitive-variable forms (paper section 2.2, Fig. 9: the building blocks
+ * evaluated from V = (rho, v, p) instead of U).
+ * fdbb_flux_prim: the inviscid flux of fdbb_flux computed from V,
+ *   F_d = (rho u, rho u v + p e_d, u (gamma/(gamma-1) p + rho |v|^2/2)),
+ *   u = v_dir; dir == -1 writes all columns, direction-major.
+ * fdbb_flux_jac_prim: B_dir = dF_dir/dV, nv*nv planes row-major, rows in U
+ *   order, columns in V order:
+ *   row 0: (u, rho at col 1+dir, 0);
+ *   row 1+i: (u v_i, rho (delta_{j,dir} v_i + delta_{ij} u) at col 1+j, delta_{i,dir});
+ *   row nv-1: (u |v|^2/2, delta_{j,dir} (gamma/(gamma-1) p + rho |v|^2/2)
+ *              + rho u v_j at col 1+j, gamma/(gamma-1) u).
+ * V: nv planes in; F / B: nv (dim*nv) / nv*nv planes out.
+ */
+FDBB_API fdbb_status fdbb_flux_prim(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
+                                    const void *const *V, void *const *F, fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_flux_jac_prim(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
+                                        const void *const *V, void *const *B, fdbb_stream_t stream);
+
+/*
+ * Temperature of the perfect gas (paper section 2.2, "Equations of state":
+ * the T_rhoe member of the EOS prototype, Fig. 10): T = e / c_v with the
+ * specific internal energy e = (rhoE - |m|^2/(2 rho)) / rho.  cv > 0 is the
+ * specific heat at constant volume (the paper's EOSidealGas<Cp = 7/2,
+ * Cv = 5/2> gives gamma = 7/5 and R = Cp - Cv = 1, so T = p / rho).
+ * U: nv planes in; T: one plane out.
+ */
+FDBB_API fdbb_status fdbb_temperature(int dim, double gamma, double cv, int64_t n, fdbb_dtype t,
+                                      const void *const *U, void *T, fdbb_stream_t stream);
+
+/*
+ * Roe flux between two states per point (the step that follows the
+ * point-wise blocks in a finite-volume solver; the paper names the inviscid
+ * flux, section 2.2, and the characteristic variables, section 1):
+ *   Fh = (F_dir(U_L) + F_dir(U_R))/2 - 1/2 R^ (|lambda^| * (L^ (U_R - U_L))),
+ * where R^, L^ = R^{-1} and lambda^ are the eigenvectors and eigenvalues
+ * defined at fdbb_char_transform, evaluated at the Roe-averaged state
+ * (P. L. Roe, J. Comput. Phys. 43, 1981): with w = sqrt(rho),
+ *   v^ = (w_L v_L + w_R v_R)/(w_L + w_R),  H^ likewise,
+ *   c^2 = (gamma - 1)(H^ - |v^|^2/2).
+ * No entropy fix.  U_L, U_R: nv planes each; F: nv planes.
+ */
+FDBB_API fdbb_status fdbb_roe_flux(int dim, int dir, double gamma, int64_t n, fdbb_dtype t,
+                                   const void *const *UL, const void *const *UR, void *const *F,
+                                   fdbb_stream_t stream);
+
+/*
+ * Characteristic transform at the Roe-averaged state of (U_L, U_R):
+ * inverse == 0: Y = L^ W; inverse != 0: Y = R^ W.  U_L, U_R, W: nv planes
+ * each; Y: nv planes.  (For FDBB_F64_DW the inverse runs in IEEE double.)
+ */
+FDBB_API fdbb_status fdbb_roe_char_transform(int dim, int dir, double gamma, int64_t n,
+                                             fdbb_dtype t, int inverse, const void *const *UL,
+                                             const void *const *UR, const void *const *W,
+                                             void *const *Y, fdbb_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched finite-volume steps (the serving workload).

@@ -182,6 +182,55 @@ def flux_vjp(U, G, dir: int, gamma: float = GAMMA, out=None, stream=None, dw: bo
     return gU
 
 
+def flux_prim(V, dir: int = -1, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
+    """Inviscid flux from primitive variables V: F_dir, or all directions for dir == -1."""
+    D = _dim(V)
+    n, dt, dev = _info(V)
+    k = (D + 2) * (D if dir < 0 else 1)
+    F = out if out is not None else _alloc(k, n, dt, dev)
+    capi.call("fdbb_flux_prim", D, dir, gamma, n, _code(dt, dw), _ptrs(V), _ptrs(F), _stream(dev, stream))
+    return F
+
+
+def flux_jac_prim(V, dir: int, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
+    """dF_dir/dV, nv*nv planes row-major."""
+    D = _dim(V)
+    n, dt, dev = _info(V)
+    B = out if out is not None else _alloc((D + 2) ** 2, n, dt, dev)
+    capi.call("fdbb_flux_jac_prim", D, dir, gamma, n, _code(dt, dw), _ptrs(V), _ptrs(B), _stream(dev, stream))
+    return B
+
+
+def temperature(U, cv: float = 2.5, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
+    """T = e / c_v (default c_v = 5/2 of the paper's perfect gas, so T = p / rho)."""
+    D = _dim(U)
+    n, dt, dev = _info(U)
+    T = out if out is not None else torch.empty(n, dtype=dt, device=dev)
+    capi.call("fdbb_temperature", D, gamma, cv, n, _code(dt, dw), _ptrs(U), T.data_ptr(), _stream(dev, stream))
+    return T
+
+
+def roe_flux(UL, UR, dir: int, gamma: float = GAMMA, out=None, stream=None, dw: bool = False):
+    """Roe flux between the states UL and UR of each point (nv planes)."""
+    D = _dim(UL)
+    n, dt, dev = _info(list(UL) + list(UR))
+    F = out if out is not None else _alloc(D + 2, n, dt, dev)
+    capi.call("fdbb_roe_flux", D, dir, gamma, n, _code(dt, dw), _ptrs(UL), _ptrs(UR), _ptrs(F),
+              _stream(dev, stream))
+    return F
+
+
+def roe_char_transform(UL, UR, W, dir: int, gamma: float = GAMMA, inverse: bool = False, out=None,
+                       stream=None, dw: bool = False):
+    """L^ W (or R^ W) at the Roe-averaged state of (UL, UR)."""
+    D = _dim(UL)
+    n, dt, dev = _info(list(UL) + list(UR) + list(W))
+    Y = out if out is not None else _alloc(D + 2, n, dt, dev)
+    capi.call("fdbb_roe_char_transform", D, dir, gamma, n, _code(dt, dw), int(bool(inverse)), _ptrs(UL),
+              _ptrs(UR), _ptrs(W), _ptrs(Y), _stream(dev, stream))
+    return Y
+
+
 def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: int = 1 << 22,
                      device=None, dw: bool = False, work=None):
     """fdbb_euler_fused over fields in pinned HOST memory.

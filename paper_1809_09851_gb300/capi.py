@@ -34,6 +34,11 @@ SIGNATURES = {
     "fdbb_char_transform": [_i, _i, _d, _i64, _i, _i, _PP, _PP, _PP, _vp],
     "fdbb_euler_fused": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _PP, _PP, _vp],
     "fdbb_flux_vjp": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _vp],
+    "fdbb_roe_flux": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _vp],
+    "fdbb_flux_prim": [_i, _i, _d, _i64, _i, _PP, _PP, _vp],
+    "fdbb_flux_jac_prim": [_i, _i, _d, _i64, _i, _PP, _PP, _vp],
+    "fdbb_temperature": [_i, _d, _d, _i64, _i, _PP, _vp, _vp],
+    "fdbb_roe_char_transform": [_i, _i, _d, _i64, _i, _i, _PP, _PP, _PP, _PP, _vp],
 }
 
 

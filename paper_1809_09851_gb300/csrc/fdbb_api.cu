@@ -77,12 +77,15 @@ fdbb_status take_out1(KArgs& a, int slot, void* p) {
   return FDBB_OK;
 }
 
-KArgs make_args(int64_t n, double gamma) {
+// cv: specific heat at constant volume for the temperature (0: R = 1, i.e.
+// c_v = 1/(gamma - 1)).
+KArgs make_args(int64_t n, double gamma, double cv = 0.0) {
   KArgs a = {};
   a.n = n;
   const double g = gamma, a1 = gamma - 1.0;
-  const double kd[6] = {g, a1, 3.0 - g, 2.0 / a1, 1.0 / a1, -g};
-  for (int i = 0; i < 6; ++i) {
+  const double tcv = cv > 0.0 ? 1.0 / (a1 * cv) : 1.0;
+  const double kd[8] = {g, a1, 3.0 - g, 2.0 / a1, 1.0 / a1, -g, g / a1, tcv};
+  for (int i = 0; i < 8; ++i) {
     a.kd[i] = kd[i];
     a.kf[i] = static_cast<float>(kd[i]);
     a.kl[i] = static_cast<float>(kd[i] - static_cast<double>(a.kf[i]));
@@ -264,6 +267,75 @@ fdbb_status fdbb_euler_fused(int dim, int dir_jac, double gamma, int64_t n, fdbb
     // W is not needed: leave in[nv] NULL so the kernel does not read it.
   }
   return launch(t, OpKind::Fused, dim, dir_jac, a, stream);
+}
+
+fdbb_status fdbb_flux_prim(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* V,
+                           void* const* F, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < -1 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, V, nv));
+  FDBB_TRY(take_out(a, 0, F, dir < 0 ? dim * nv : nv, false));
+  return launch(t, dir < 0 ? OpKind::FluxPrimAll : OpKind::FluxPrim, dim, dir, a, stream);
+}
+
+fdbb_status fdbb_flux_jac_prim(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* V,
+                               void* const* B, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, V, nv));
+  FDBB_TRY(take_out(a, 0, B, nv * nv, false));
+  return launch(t, OpKind::JacPrim, dim, dir, a, stream);
+}
+
+fdbb_status fdbb_temperature(int dim, double gamma, double cv, int64_t n, fdbb_dtype t, const void* const* U,
+                             void* T, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  FDBB_TRY(check_gamma(gamma));
+  if (!(cv > 0.0) || !std::isfinite(cv)) return FDBB_ERR_ARG;
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma, cv);
+  FDBB_TRY(take_in(a, 0, U, dim + 2));
+  if (T == nullptr) return FDBB_ERR_NULLPTR;
+  FDBB_TRY(take_out1(a, 0, T));
+  return launch(t, OpKind::Temp, dim, 0, a, stream);
+}
+
+fdbb_status fdbb_roe_flux(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* UL,
+                          const void* const* UR, void* const* F, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, UL, nv));
+  FDBB_TRY(take_in(a, nv, UR, nv));
+  FDBB_TRY(take_out(a, 0, F, nv, false));
+  return launch(t, OpKind::RoeFlux, dim, dir, a, stream);
+}
+
+fdbb_status fdbb_roe_char_transform(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, int inverse,
+                                    const void* const* UL, const void* const* UR, const void* const* W,
+                                    void* const* Y, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, UL, nv));
+  FDBB_TRY(take_in(a, nv, UR, nv));
+  FDBB_TRY(take_in(a, 2 * nv, W, nv));
+  FDBB_TRY(take_out(a, 0, Y, nv, false));
+  return launch(t, inverse ? OpKind::RoeCharInv : OpKind::RoeCharFwd, dim, dir, a, stream);
 }
 
 fdbb_status fdbb_flux_vjp(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,

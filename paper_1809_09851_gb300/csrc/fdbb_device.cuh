@@ -225,6 +225,8 @@ __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double abs_(double x) { return fabs(x); }
+__device__ __forceinline__ float abs_(float x) { return fabsf(x); }
 __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
 
@@ -236,6 +238,8 @@ template <class R> struct Consts {
   R ta1;    // 2 / (gamma - 1)
   R ia1;    // 1 / (gamma - 1)
   R mg;     // -gamma
+  R gia1;   // gamma / (gamma - 1)
+  R tcv;    // 1 / ((gamma - 1) c_v): T = p / rho * tcv
 };
 
 // ---------------------------------------------------------------------------
@@ -444,6 +448,96 @@ __device__ __forceinline__ void flux_vjp_pt(const Pt<R, D>& s, const Consts<R>& 
     if (j != d) y[1 + j] = fma_(u, g[1 + j], -(k.a1 * s.v[j] * z));
   y[1 + d] = g[0] + sigma + fma_(R(2) * u, gd, fma_(s.H, ge, -(k.a1 * u * z)));
   y[nv - 1] = fma_(k.a1, gd, k.g * u * ge);
+}
+
+// State from primitive variables (rho, v, p set): m = rho v, q = |v|^2/2,
+// rhoE = p/(gamma-1) + rho q (paper section 2.2, Fig. 9, the primitive form).
+template <class R, int D, class G>
+__device__ __forceinline__ void derive_prim(Pt<R, D>& s, const Consts<R>& k, G& g) {
+  R v2 = s.v[0] * s.v[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) v2 = fma_(s.v[i], s.v[i], v2);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    s.m[i] = s.rho * s.v[i];
+    g.check(s.m[i]);
+  }
+  s.q = R(0.5f) * v2;
+  s.rq = s.rho * s.q;
+  s.rE = fma_(s.p, k.ia1, s.rq);
+  g.check(s.q);
+  g.check(s.rE);
+}
+
+// Entry of B_d = dF_d/dV (rows in U order, columns in V order), u = v_d:
+//   row 0: (u, rho at col 1+d, 0); row 1+i: (u v_i, rho (delta_jd v_i +
+//   delta_ij u), delta_id); row nv-1: (u q, delta_jd (gamma/(gamma-1) p +
+//   rho q) + rho u v_j, gamma/(gamma-1) u).
+template <int D, int d, class R>
+__device__ __forceinline__ R jacp_entry(const Pt<R, D>& s, const Consts<R>& k, int row, int col) {
+  constexpr int nv = D + 2;
+  const R u = s.v[d];
+  if (row == 0) return col == 0 ? u : (col == 1 + d ? s.rho : R(0));
+  if (row == nv - 1) {
+    if (col == 0) return u * s.q;
+    if (col == nv - 1) return k.gia1 * u;
+    const R e = s.m[col - 1] * u;  // rho v_j u
+    return col == 1 + d ? e + fma_(k.gia1, s.p, s.rq) : e;
+  }
+  const int i = row - 1;
+  if (col == 0) return u * s.v[i];
+  if (col == nv - 1) return i == d ? R(1) : R(0);
+  const int j = col - 1;
+  if (j == d && j == i) return s.m[i] + s.rho * u;  // rho v_i + rho u
+  if (j == d) return s.m[i];
+  if (j == i) return s.rho * u;
+  return R(0);
+}
+
+// Roe-averaged state of (L, R) (P. L. Roe, J. Comput. Phys. 43, 1981): with
+// w = sqrt(rho), v^ = (w_L v_L + w_R v_R)/(w_L + w_R), H^ likewise,
+// q^ = |v^|^2/2, c^2 = (gamma-1)(H^ - q^).  Sets the fields the
+// characteristic formulas read (v, q, H, c2).
+template <class R, int D, class G>
+__device__ __forceinline__ void roe_state(const Pt<R, D>& L, const Pt<R, D>& Rt, const Consts<R>& k, Pt<R, D>& s,
+                                          G& g) {
+  const R wL = sqrt_(L.rho), wR = sqrt_(Rt.rho);
+  const R iw = rcp_(wL + wR);
+  R v2 = R(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    s.v[i] = fma_(wL, L.v[i], wR * Rt.v[i]) * iw;
+    v2 = (i == 0) ? s.v[i] * s.v[i] : fma_(s.v[i], s.v[i], v2);
+    g.check(s.v[i]);
+  }
+  s.H = fma_(wL, L.H, wR * Rt.H) * iw;
+  s.q = R(0.5f) * v2;
+  s.c2 = k.a1 * (s.H - s.q);
+  g.check(s.H);
+  g.check(s.q);
+  g.check(s.c2);
+}
+
+// Roe flux in direction d: (F_d(L) + F_d(R))/2 - 1/2 R^ (|lambda^| * (L^ (U_R - U_L))).
+template <int D, int d, class R>
+__device__ __forceinline__ void roe_flux_pt(const Pt<R, D>& L, const Pt<R, D>& Rt, const Pt<R, D>& s,
+                                            const Consts<R>& k, R* Fh) {
+  constexpr int nv = D + 2;
+  R dU[nv], alpha[nv], beta[nv], diss[nv];
+  dU[0] = Rt.rho - L.rho;
+#pragma unroll
+  for (int i = 0; i < D; ++i) dU[1 + i] = Rt.m[i] - L.m[i];
+  dU[nv - 1] = Rt.rE - L.rE;
+  char_fwd<D, d>(s, k, dU, alpha);
+  const R u = s.v[d], c = sqrt_(s.c2);
+  beta[0] = abs_(u - c) * alpha[0];
+#pragma unroll
+  for (int q = 1; q < nv - 1; ++q) beta[q] = abs_(u) * alpha[q];
+  beta[nv - 1] = abs_(u + c) * alpha[nv - 1];
+  char_inv<D, d>(s, k, beta, diss);
+#pragma unroll
+  for (int q = 0; q < nv; ++q)
+    Fh[q] = R(0.5f) * (flux_comp<D, d>(L, q) + flux_comp<D, d>(Rt, q)) - R(0.5f) * diss[q];
 }
 
 }  // namespace fdbb

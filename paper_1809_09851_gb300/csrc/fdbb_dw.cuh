@@ -137,6 +137,8 @@ __device__ __forceinline__ dw rsqrt_(dw x) {
 
 __device__ __forceinline__ dw operator/(dw a, dw b) { return a * rcp_(b); }
 
+__device__ __forceinline__ dw abs_(dw x) { return x.hi < 0.0f ? -x : x; }
+
 __device__ __forceinline__ dw sqrt_(dw x) {
   if (x.hi == 0.0f) return dw(0.0f);
   return x * rsqrt_(x);
@@ -160,7 +162,7 @@ struct DwGuard {
   bool ok = true;
   __device__ __forceinline__ void check(dw x) {
     const float a = fabsf(x.hi);
-    ok = ok && ((a >= 0x1p-24f && a <= 0x1p24f) || a == 0.0f);
+    ok &= ((a >= 0x1p-24f) & (a <= 0x1p24f)) | (a == 0.0f);  // NaN compares false
   }
 };
 
@@ -172,15 +174,16 @@ struct DwGuard {
 __device__ __forceinline__ dw dw_from_double(double x, DwGuard& g) {
   const uint32_t H = static_cast<uint32_t>(__double2hiint(x));
   const uint32_t L = static_cast<uint32_t>(__double2loint(x));
-  if (((H << 1) | L) == 0u) return dw(0.0f);
+  const bool zero = ((H << 1) | L) == 0u;
   const uint32_t E = (H >> 20) & 0x7FFu;
-  g.ok = g.ok && (E - 999u) < 48u;                              // 2^-24 <= |x| < 2^24
+  g.ok &= zero | ((E - 999u) < 48u);                            // 0 or 2^-24 <= |x| < 2^24
   const uint32_t sign = H & 0x80000000u;
   const uint32_t t = (H & 0x7FFFFFFFu) - (896u << 20);        // exponent 1023 -> 127 bias
   const uint32_t hb = __funnelshift_l(L, t, 3) | sign;          // sign | exp | top 23 mantissa bits
   const uint32_t base = (hb & 0xFF800000u) - (23u << 23);       // sign | 2^(e-23)
   const uint32_t yb = base | ((L >> 6) & 0x007FFFFFu);          // 2^(e-23) * (1 + next 23 bits)
-  return dw(__uint_as_float(hb), __fsub_rn(__uint_as_float(yb), __uint_as_float(base)));
+  const float lo = __fsub_rn(__uint_as_float(yb), __uint_as_float(base));
+  return dw(zero ? 0.0f : __uint_as_float(hb), zero ? 0.0f : lo);
 }
 
 __device__ __forceinline__ dw dw_from_double_unchecked(double x) {
@@ -197,19 +200,20 @@ __device__ __forceinline__ double dw_to_double(dw x) {
   const uint32_t f = __float_as_uint(x.hi);
   const uint32_t mag = f & 0x7FFFFFFFu;
   const uint32_t sign = f & 0x80000000u;
-  if (mag < 0x00800000u) return __hiloint2double(static_cast<int>(sign), 0);  // |x| < 2^-126
   const uint32_t H = ((mag >> 3) + (896u << 20)) | sign;
   const uint32_t L = f << 29;
-  int64_t bits = static_cast<int64_t>((static_cast<uint64_t>(H) << 32) | L);
+  const int64_t bits = static_cast<int64_t>((static_cast<uint64_t>(H) << 32) | L);
   const uint32_t ebits = mag & 0x7F800000u;
-  if (ebits >= (45u << 23)) {  // |hi| >= 2^-82: the scale 2^(45 - e_hi) is a normal float
-    const float scale = __uint_as_float(((299u << 23) - ebits) | sign);
-    const float k = __fmaf_rn(x.lo, scale, 12582912.0f);  // round to an integer via 1.5 * 2^23
-    const int32_t ki = static_cast<int32_t>(__float_as_uint(k)) - 0x4B400000;
-    const int64_t unit = ((mag & 0x007FFFFFu) == 0u && ki < 0) ? 256 : 128;
-    bits += static_cast<int64_t>(ki) * unit;
-  }
-  return __longlong_as_double(bits);
+  // lo in units of 2^(e_hi - 45); only when |hi| >= 2^-82, where the scale
+  // 2^(45 - e_hi) is a normal float (below that lo is dropped)
+  const float scale = __uint_as_float(((299u << 23) - ebits) | sign);
+  const float k = __fmaf_rn(x.lo, scale, 12582912.0f);  // round to an integer via 1.5 * 2^23
+  const int32_t ki0 = static_cast<int32_t>(__float_as_uint(k)) - 0x4B400000;
+  const int32_t ki = ebits >= (45u << 23) ? ki0 : 0;
+  const int64_t unit = ((mag & 0x007FFFFFu) == 0u && ki < 0) ? 256 : 128;
+  const int64_t out = bits + static_cast<int64_t>(ki) * unit;
+  // |hi| < 2^-126 (zero or subnormal): a signed zero
+  return mag < 0x00800000u ? __hiloint2double(static_cast<int>(sign), 0) : __longlong_as_double(out);
 }
 
 }  // namespace fdbb

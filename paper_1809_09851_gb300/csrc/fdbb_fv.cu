@@ -101,35 +101,53 @@ template <class T> __device__ __forceinline__ Consts<T> fv_consts(double g) {
   return {T(g), T(a1), T(3.0 - g), T(2.0 / a1), T(1.0 / a1), T(-g)};
 }
 
+// Derived state for the finite-volume kernels.  FP64 grids use the IEEE
+// derivation of the point-wise blocks.  FP32 grids use the hardware
+// reciprocal and square-root approximations (relative error ~2^-22) and a
+// plain internal-energy difference: the serving flows are smooth and
+// subsonic, and the FP32 state's tolerance against the FP64 oracle is 2e-5.
+__device__ __forceinline__ float fv_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fv_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double fv_sqrt(double x) { return sqrt(x); }
+
+__device__ __forceinline__ void fv_derive(Pt<double, 3>& s, const Consts<double>& k) {
+  NoGuard g;
+  derive(s, k, g);
+}
+__device__ __forceinline__ void fv_derive(Pt<float, 3>& s, const Consts<float>& k) {
+  s.r = fv_rcp(s.rho);
+  s.v[0] = s.m[0] * s.r;
+  s.v[1] = s.m[1] * s.r;
+  s.v[2] = s.m[2] * s.r;
+  s.rq = 0.5f * fmaf(s.m[2], s.v[2], fmaf(s.m[1], s.v[1], s.m[0] * s.v[0]));
+  s.q = s.rq * s.r;
+  s.p = k.a1 * (s.rE - s.rq);
+  s.H = (s.rE + s.p) * s.r;
+  s.c2 = k.g * s.p * s.r;
+}
+
 // Derived state of the cell at linear index c of the planes P.
 template <class T>
 __device__ __forceinline__ void cell_state(void* const* P, int64_t c, const Consts<T>& k, Pt<T, 3>& s) {
-  NoGuard g;
   s.rho = ldg<T>(P[0], c);
   s.m[0] = ldg<T>(P[1], c);
   s.m[1] = ldg<T>(P[2], c);
   s.m[2] = ldg<T>(P[3], c);
   s.rE = ldg<T>(P[4], c);
-  derive(s, k, g);
+  fv_derive(s, k);
 }
 
 template <class T> __device__ __forceinline__ T wave_speed_sum(const Pt<T, 3>& s) {
-  const T c = sqrt_(s.c2);
+  const T c = fv_sqrt(s.c2);
   return (fabs(s.v[0]) + c) + (fabs(s.v[1]) + c) + (fabs(s.v[2]) + c);
-}
-
-// Rusanov face flux in direction d between left state L and right state R,
-// accumulated as  acc += sign * Fh.
-template <class T, int d>
-__device__ __forceinline__ void face_flux(const Pt<T, 3>& L, const Pt<T, 3>& R, T (&Fh)[5]) {
-  const T cL = sqrt_(L.c2), cR = sqrt_(R.c2);
-  const T sL = fabs(L.v[d]) + cL, sR = fabs(R.v[d]) + cR;
-  const T sm = sL > sR ? sL : sR;
-  const T uL[5] = {L.rho, L.m[0], L.m[1], L.m[2], L.rE};
-  const T uR[5] = {R.rho, R.m[0], R.m[1], R.m[2], R.rE};
-#pragma unroll
-  for (int q = 0; q < 5; ++q)
-    Fh[q] = T(0.5f) * (flux_comp<3, d>(L, q) + flux_comp<3, d>(R, q)) - T(0.5f) * sm * (uR[q] - uL[q]);
 }
 
 template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_max_speed(const __grid_constant__ FvArgs a) {
@@ -159,16 +177,18 @@ template <class T> struct PlaneTile {
   T v[kSlotVals][kSlots];
 };
 
-// State, the three flux columns and the three wave speeds |v_d| + c of the
-// cell (x, y, z) of grid g, into slot `slot` of plane tile P.
+// State, the three flux columns and the three wave speeds |v_d| + c of a cell
+// given its conservative values u, into slot `slot` of plane tile P.
 template <class T>
-__device__ __forceinline__ void fill_slot(const fdbb_fv_grid& g, int x, int y, int z, const Consts<T>& k,
-                                          PlaneTile<T>& P, int slot) {
-  const int n = g.n;
+__device__ __forceinline__ void put_slot(const T (&u)[5], const Consts<T>& k, PlaneTile<T>& P, int slot) {
   Pt<T, 3> s;
-  cell_state<T>(g.U, ((int64_t)z * n + y) * n + x, k, s);
-  const T c = sqrt_(s.c2);
-  const T u[5] = {s.rho, s.m[0], s.m[1], s.m[2], s.rE};
+  s.rho = u[0];
+  s.m[0] = u[1];
+  s.m[1] = u[2];
+  s.m[2] = u[3];
+  s.rE = u[4];
+  fv_derive(s, k);
+  const T c = fv_sqrt(s.c2);
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     P.v[q][slot] = u[q];
@@ -180,6 +200,19 @@ __device__ __forceinline__ void fill_slot(const fdbb_fv_grid& g, int x, int y, i
   P.v[21][slot] = fabs(s.v[1]) + c;
   P.v[22][slot] = fabs(s.v[2]) + c;
 }
+
+template <class T>
+__device__ __forceinline__ void load_cell(const fdbb_fv_grid& g, int x, int y, int z, T (&u)[5]) {
+  const int64_t c = ((int64_t)z * g.n + y) * g.n + x;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) u[q] = ldg<T>(g.U[q], c);
+}
+
+// Conservative values of this thread's (at most two) slots of one plane tile.
+constexpr int kSlotsPerThread = (kSlots + kFvThreads - 1) / kFvThreads;
+template <class T> struct SlotRaw {
+  T u[kSlotsPerThread][5];
+};
 
 // Rusanov flux through the face between slot l (left) and slot r (right) in
 // direction d, from plane tiles PL and PR.
@@ -227,19 +260,34 @@ template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_st
     }
     const int x = x0 + lx, y = y0 + ly;
     const bool active = x < n && y < n;
-    auto fill = [&](PlaneTile<T>& P, int z) {
-      for (int sl = tid; sl < kSlots; sl += kFvThreads) {
-        const int sx = sl % kSX, sy = sl / kSX;
-        fill_slot<T>(g, (x0 + sx - 1 + n) % n, (y0 + sy - 1 + n) % n, z, k, P, sl);
+    // this thread's slots of a plane tile: cells with a periodic halo
+    auto load_plane = [&](SlotRaw<T>& r, int z) {
+#pragma unroll
+      for (int j = 0; j < kSlotsPerThread; ++j) {
+        const int sl = tid + j * kFvThreads;
+        if (sl < kSlots)
+          load_cell<T>(g, (x0 + sl % kSX - 1 + n) % n, (y0 + sl / kSX - 1 + n) % n, z, r.u[j]);
       }
     };
+    auto fill = [&](PlaneTile<T>& P, const SlotRaw<T>& r) {
+#pragma unroll
+      for (int j = 0; j < kSlotsPerThread; ++j) {
+        const int sl = tid + j * kFvThreads;
+        if (sl < kSlots) put_slot<T>(r.u[j], k, P, sl);
+      }
+    };
+    SlotRaw<T> raw;
+    load_plane(raw, z0);
+    fill(tiles[0], raw);
+    load_plane(raw, z0 + 1 == n ? 0 : z0 + 1);  // in flight during the prologue
     // lower z face of the first plane: the own cell of plane z0 - 1 (periodic)
-    fill(tiles[0], z0);
     T zlo[5];
     __syncthreads();
     if (active) {
       PlaneTile<T>& P1 = tiles[1];  // its own slot only, as scratch for the face
-      fill_slot<T>(g, x, y, z0 == 0 ? n - 1 : z0 - 1, k, P1, own);
+      T u[5];
+      load_cell<T>(g, x, y, z0 == 0 ? n - 1 : z0 - 1, u);
+      put_slot<T>(u, k, P1, own);
       face<T, 2>(P1, own, tiles[0], own, zlo);
     }
     __syncthreads();
@@ -247,7 +295,8 @@ template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_st
     for (int z = z0; z < z1; ++z) {
       const PlaneTile<T>& C = tiles[(z - z0) & 1];
       PlaneTile<T>& N = tiles[((z - z0) & 1) ^ 1];
-      fill(N, z + 1 == n ? 0 : z + 1);
+      fill(N, raw);  // plane z + 1
+      if (z + 1 < z1) load_plane(raw, z + 2 >= n ? z + 2 - n : z + 2);  // prefetch plane z + 2
       __syncthreads();
       if (active) {
         T lo[5], hi[5], div[5];
@@ -278,8 +327,7 @@ template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_st
         Nw.m[1] = un[2];
         Nw.m[2] = un[3];
         Nw.rE = un[4];
-        NoGuard ng;
-        derive(Nw, k, ng);
+        fv_derive(Nw, k);
         const T w = wave_speed_sum(Nw);
         vmax = w > vmax ? w : vmax;
       }

@@ -7,10 +7,11 @@
 
 namespace fdbb {
 
-constexpr int kMaxIn = 10;   // U (nv) + W or G (nv)
+constexpr int kMaxIn = 15;   // U (nv) + W or G (nv); U_L, U_R, W (3 nv) for the Roe transform
 constexpr int kMaxOut = 45;  // fused 3D: 15 flux + 25 Jacobian + 5 characteristic
 
-enum class OpKind { VMag2, Prim, Cons, Eos, Riemann, Flux, FluxAll, Jac, CharFwd, CharInv, Fused, Vjp };
+enum class OpKind { VMag2, Prim, Cons, Eos, Riemann, Flux, FluxAll, Jac, CharFwd, CharInv, Fused, Vjp, RoeFlux,
+                    RoeCharFwd, RoeCharInv, FluxPrim, FluxPrimAll, JacPrim, Temp };
 
 // Kernel parameter block (passed by value as a __grid_constant__).
 struct KArgs {
@@ -18,9 +19,10 @@ struct KArgs {
   void* out[kMaxOut];
   int64_t n;
   int nin;       // input planes in use (the leading non-NULL entries of in[])
-  double kd[6];  // gamma, gamma-1, 3-gamma, 2/(gamma-1), 1/(gamma-1), -gamma
-  float kf[6];   // the same, rounded once to float
-  float kl[6];   // kd - kf rounded to float: (kf, kl) is the double-word constant
+  double kd[8];  // gamma, gamma-1, 3-gamma, 2/(gamma-1), 1/(gamma-1), -gamma,
+                 // gamma/(gamma-1), 1/((gamma-1) c_v)
+  float kf[8];   // the same, rounded once to float
+  float kl[8];   // kd - kf rounded to float: (kf, kl) is the double-word constant
 };
 
 struct LaunchReq {

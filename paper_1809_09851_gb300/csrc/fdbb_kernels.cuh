@@ -42,14 +42,14 @@ template <class T> __device__ __forceinline__ T* outp(const KArgs& a, int k) {
 
 template <class R> __device__ __forceinline__ Consts<R> consts(const KArgs& a);
 template <> __device__ __forceinline__ Consts<double> consts<double>(const KArgs& a) {
-  return {a.kd[0], a.kd[1], a.kd[2], a.kd[3], a.kd[4], a.kd[5]};
+  return {a.kd[0], a.kd[1], a.kd[2], a.kd[3], a.kd[4], a.kd[5], a.kd[6], a.kd[7]};
 }
 template <> __device__ __forceinline__ Consts<float> consts<float>(const KArgs& a) {
-  return {a.kf[0], a.kf[1], a.kf[2], a.kf[3], a.kf[4], a.kf[5]};
+  return {a.kf[0], a.kf[1], a.kf[2], a.kf[3], a.kf[4], a.kf[5], a.kf[6], a.kf[7]};
 }
 template <> __device__ __forceinline__ Consts<dw> consts<dw>(const KArgs& a) {
-  return {dw(a.kf[0], a.kl[0]), dw(a.kf[1], a.kl[1]), dw(a.kf[2], a.kl[2]),
-          dw(a.kf[3], a.kl[3]), dw(a.kf[4], a.kl[4]), dw(a.kf[5], a.kl[5])};
+  return {dw(a.kf[0], a.kl[0]), dw(a.kf[1], a.kl[1]), dw(a.kf[2], a.kl[2]), dw(a.kf[3], a.kl[3]),
+          dw(a.kf[4], a.kl[4]), dw(a.kf[5], a.kl[5]), dw(a.kf[6], a.kl[6]), dw(a.kf[7], a.kl[7])};
 }
 
 // ---------------------------------------------------------------------------
@@ -451,6 +451,180 @@ template <int D, int d> struct OpVjp {
   }
 };
 
+// Roe flux between U_L (planes 0..nv-1) and U_R (nv..2nv-1) in direction d.
+template <int D, int d> struct OpRoeFlux {
+  static constexpr int kIn = 2 * (D + 2);
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
+    constexpr int nv = D + 2;
+    typename GuardOf<R>::type g;
+    Pt<R, D> L[VW], Rt[VW], s[VW];
+    load_U<T, VW, D>(src, 0, L, g);
+    load_U<T, VW, D>(src, nv, Rt, g);
+    derive_all<VW, D>(L, k, g);
+    derive_all<VW, D>(Rt, k, g);
+#pragma unroll
+    for (int j = 0; j < VW; ++j) roe_state(L[j], Rt[j], k, s[j], g);
+    if (!g.ok) return false;
+    R y[VW][nv];
+#pragma unroll
+    for (int j = 0; j < VW; ++j) roe_flux_pt<D, d>(L[j], Rt[j], s[j], k, y[j]);
+    store_field<T, VW, nv>(a, 0, i0, cnt, y);
+    return true;
+  }
+};
+
+// Characteristic transform at the Roe-averaged state of U_L (planes 0..nv-1)
+// and U_R (nv..2nv-1) applied to W (2nv..3nv-1).
+template <int D, int d, bool INV> struct OpRoeChar {
+  static constexpr int kIn = 3 * (D + 2);
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
+    constexpr int nv = D + 2;
+    typename GuardOf<R>::type g;
+    Pt<R, D> L[VW], Rt[VW], s[VW];
+    load_U<T, VW, D>(src, 0, L, g);
+    load_U<T, VW, D>(src, nv, Rt, g);
+    R w[VW][nv], y[VW][nv];
+    load_field<T, VW, nv>(src, 2 * nv, w, g);
+    derive_all<VW, D>(L, k, g);
+    derive_all<VW, D>(Rt, k, g);
+#pragma unroll
+    for (int j = 0; j < VW; ++j) roe_state(L[j], Rt[j], k, s[j], g);
+    if (!g.ok) return false;
+#pragma unroll
+    for (int j = 0; j < VW; ++j) {
+      if constexpr (INV)
+        char_inv<D, d>(s[j], k, w[j], y[j]);
+      else
+        char_fwd<D, d>(s[j], k, w[j], y[j]);
+    }
+    store_field<T, VW, nv>(a, 0, i0, cnt, y);
+    return true;
+  }
+};
+
+// Primitive state (rho, v, p) of VW points from planes base..base+D+1; for
+// double-word the loaded doubles of rho and v stay available (raw.rho,
+// raw.m[i]) for outputs that are copies of them.
+template <class T, int VW, int D, class R, class G, class Src>
+__device__ __forceinline__ void load_V(const Src& src, int base, Pt<R, D> (&s)[VW], G& g) {
+  typename Storage<T>::L raw[VW];
+  src.raw(base, raw, 1.0f);
+#pragma unroll
+  for (int j = 0; j < VW; ++j) {
+    s[j].rho = to_compute<R, G>(raw[j], g);
+    if constexpr (std::is_same<R, dw>::value) s[j].raw.rho = raw[j];
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    src.raw(base + 1 + i, raw, 0.0f);
+#pragma unroll
+    for (int j = 0; j < VW; ++j) {
+      s[j].v[i] = to_compute<R, G>(raw[j], g);
+      if constexpr (std::is_same<R, dw>::value) s[j].raw.m[i] = raw[j];
+    }
+  }
+  src.raw(base + D + 1, raw, 1.0f);
+#pragma unroll
+  for (int j = 0; j < VW; ++j) s[j].p = to_compute<R, G>(raw[j], g);
+}
+
+// Inviscid flux from primitive variables V (planes 0..nv-1): column d, or
+// all columns when d == -1 (paper section 2.2, Figs. 9 and 11).
+template <int D, int d> struct OpFluxPrim {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
+    typename GuardOf<R>::type g;
+    Pt<R, D> s[VW];
+    load_V<T, VW, D>(src, 0, s, g);
+#pragma unroll
+    for (int j = 0; j < VW; ++j) derive_prim(s[j], k, g);
+    if (!g.ok) return false;
+    constexpr int dlo = d >= 0 ? d : 0, dhi = d >= 0 ? d : D - 1;
+#pragma unroll
+    for (int dd = dlo; dd <= dhi; ++dd) {
+      const int base = d >= 0 ? 0 : dd * (D + 2);
+#pragma unroll
+      for (int c = 0; c < D + 2; ++c) {
+        T* o = outp<T>(a, base + c);
+        if (!o) continue;
+        R x[VW];
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+          if (dd == 0) x[j] = flux_comp<D, 0>(s[j], c);
+          if constexpr (D > 1) if (dd == 1) x[j] = flux_comp<D, (D > 1 ? 1 : 0)>(s[j], c);
+          if constexpr (D > 2) if (dd == 2) x[j] = flux_comp<D, (D > 2 ? 2 : 0)>(s[j], c);
+        }
+        store<T, VW, R>(o, i0, cnt, x);
+      }
+    }
+    return true;
+  }
+};
+
+// B_d = dF_d/dV, nv*nv planes row-major.
+template <int D, int d> struct OpJacPrim {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
+    constexpr int nv = D + 2;
+    typename GuardOf<R>::type g;
+    Pt<R, D> s[VW];
+    load_V<T, VW, D>(src, 0, s, g);
+#pragma unroll
+    for (int j = 0; j < VW; ++j) derive_prim(s[j], k, g);
+    if (!g.ok) return false;
+#pragma unroll
+    for (int row = 0; row < nv; ++row) {
+#pragma unroll
+      for (int col = 0; col < nv; ++col) {
+        T* o = outp<T>(a, row * nv + col);
+        if (!o) continue;
+        if constexpr (std::is_same<R, dw>::value) {
+          if (row == 0 && (col == 0 || col == 1 + d)) {  // u and rho: copies of the inputs
+            double raw[VW];
+#pragma unroll
+            for (int j = 0; j < VW; ++j) raw[j] = col == 0 ? s[j].raw.m[d] : s[j].raw.rho;
+            store_raw<T, VW>(o, i0, cnt, raw);
+            continue;
+          }
+        }
+        R x[VW];
+#pragma unroll
+        for (int j = 0; j < VW; ++j) x[j] = jacp_entry<D, d>(s[j], k, row, col);
+        store<T, VW, R>(o, i0, cnt, x);
+      }
+    }
+    return true;
+  }
+};
+
+// Temperature T = e / c_v = p / rho / ((gamma - 1) c_v) (paper section 2.2,
+// "Equations of state", T_rhoe of the EOS prototype, Fig. 10).
+template <int D> struct OpTemp {
+  static constexpr int kIn = D + 2;
+  template <class T, int VW, class R, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+                                               int cnt) {
+    typename GuardOf<R>::type g;
+    Pt<R, D> s[VW];
+    load_U<T, VW, D>(src, 0, s, g);
+    derive_all<VW, D>(s, k, g);
+    if (!g.ok) return false;
+    R x[VW];
+#pragma unroll
+    for (int j = 0; j < VW; ++j) x[j] = s[j].p * s[j].r * k.tcv;
+    store<T, VW, R>(outp<T>(a, 0), i0, cnt, x);
+    return true;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies and mbarriers (sm_90+ PTX, used on sm_103a)
 // ---------------------------------------------------------------------------
@@ -649,10 +823,12 @@ template <class Op, class T, class R> cudaError_t launch_staged(const KArgs& a, 
   return cudaGetLastError();
 }
 
-// The staged kernel pays off once every SM has a few tiles to stream.
+// The staged kernel pays off once every SM has a few tiles to stream, and
+// while its two-stage ring leaves room for more than one block per SM.
 template <class Op, class T, class R> cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
   constexpr int TILE = kThreads * Width<T, R>::VW;
-  if (a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn)
+  const size_t ring = (size_t)kStages * a.nin * TILE * sizeof(T);
+  if (a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn && ring <= (100u << 10))
     return launch_staged<Op, T, R>(a, stream);
   return launch_direct<Op, T, R>(a, stream);
 }
@@ -666,11 +842,13 @@ template <int D, class T, class R> cudaError_t dispatch_dim(const LaunchReq& r, 
     case OpKind::Cons: return launch_op<OpCons<D>, T, R>(a, r.stream);
     case OpKind::Eos: return launch_op<OpEos<D>, T, R>(a, r.stream);
     case OpKind::FluxAll: return launch_op<OpFlux<D, -1>, T, R>(a, r.stream);
+    case OpKind::FluxPrimAll: return launch_op<OpFluxPrim<D, -1>, T, R>(a, r.stream);
+    case OpKind::Temp: return launch_op<OpTemp<D>, T, R>(a, r.stream);
     default: break;
   }
-  // The inverse characteristic transform adds input components directly
+  // The inverse characteristic transforms add input components directly
   // (a1 + a2 + an); in double-word arithmetic such sums of exact inputs are
-  // not accurate relative to their own magnitude, so it always runs in the
+  // not accurate relative to their own magnitude, so they always run in the
   // storage's own IEEE type.
   using RI = typename std::conditional<std::is_same<R, dw>::value, double, R>::type;
 #define FDBB_DIR_CASES(OPK, OPT, RT)                                                          \
@@ -687,6 +865,23 @@ template <int D, class T, class R> cudaError_t dispatch_dim(const LaunchReq& r, 
     FDBB_DIR_CASES(OpKind::Jac, OpJac, R)
     FDBB_DIR_CASES(OpKind::Fused, OpFused, R)
     FDBB_DIR_CASES(OpKind::Vjp, OpVjp, R)
+    FDBB_DIR_CASES(OpKind::RoeFlux, OpRoeFlux, R)
+    FDBB_DIR_CASES(OpKind::FluxPrim, OpFluxPrim, R)
+    FDBB_DIR_CASES(OpKind::JacPrim, OpJacPrim, R)
+    case OpKind::RoeCharFwd:
+      if (d == 0) return launch_op<OpRoeChar<D, 0, false>, T, R>(a, r.stream);
+      if constexpr (D > 1)
+        if (d == 1) return launch_op<OpRoeChar<D, (D > 1 ? 1 : 0), false>, T, R>(a, r.stream);
+      if constexpr (D > 2)
+        if (d == 2) return launch_op<OpRoeChar<D, (D > 2 ? 2 : 0), false>, T, R>(a, r.stream);
+      return cudaErrorInvalidValue;
+    case OpKind::RoeCharInv:
+      if (d == 0) return launch_op<OpRoeChar<D, 0, true>, T, RI>(a, r.stream);
+      if constexpr (D > 1)
+        if (d == 1) return launch_op<OpRoeChar<D, (D > 1 ? 1 : 0), true>, T, RI>(a, r.stream);
+      if constexpr (D > 2)
+        if (d == 2) return launch_op<OpRoeChar<D, (D > 2 ? 2 : 0), true>, T, RI>(a, r.stream);
+      return cudaErrorInvalidValue;
     case OpKind::CharFwd:
       if (d == 0) return launch_op<OpChar<D, 0, false>, T, R>(a, r.stream);
       if constexpr (D > 1)

@@ -338,3 +338,61 @@ def test_fused_over_host_buffers_matches_device_call():
     Fd, Ad, Yd = blocks.euler_fused([u.to(DEV) for u in hU], [w.to(DEV) for w in hW], 0, G)
     for h, d in zip([*out[0], *out[1], *out[2]], [*Fd, *Ad, *Yd]):
         assert torch.equal(h, d.cpu())
+
+
+# ---------------------------------------------------------------------------
+# Roe flux and Roe-averaged characteristic transform
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype,dw", [(torch.float64, False), (torch.float64, True), (torch.float32, False),
+                                      (torch.bfloat16, False)], ids=["f64", "f64dw", "f32", "bf16"])
+@pytest.mark.parametrize("n", [7, 4099])
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_roe_blocks(D, n, dtype, dw):
+    _, UL, W = fields(n, D, seed=300)
+    _, UR, _ = fields(n, D, seed=301)
+    ULd, ULq = quantise(UL, dtype)
+    URd, URq = quantise(UR, dtype)
+    Wd, Wq = quantise(W, dtype)
+    for d in range(D):
+        ref, S = oracle.roe_flux(D, d, G, ULq, URq, scale=True)
+        check(host(blocks.roe_flux(ULd, URd, d, G, dw=dw)), ref, S, dtype, f"roe flux {d}")
+        for inv in (False, True):
+            ref, S = oracle.roe_char_transform(D, d, G, ULq, URq, Wq, inverse=inv, scale=True)
+            check(host(blocks.roe_char_transform(ULd, URd, Wd, d, G, inverse=inv, dw=dw)), ref, S, dtype,
+                  f"roe char {d} inv={inv}")
+
+
+@pytest.mark.parametrize("dw", [False, True], ids=["f64", "f64dw"])
+def test_roe_flux_staged_path(dw):
+    n, D = 4 * 152 * 512 + 333, 3
+    _, UL, _ = fields(n, D, seed=310)
+    _, UR, _ = fields(n, D, seed=311)
+    ULd, _ = quantise(UL, torch.float64)
+    URd, _ = quantise(UR, torch.float64)
+    ref, S = oracle.roe_flux(D, 1, G, UL, UR, scale=True)
+    check(host(blocks.roe_flux(ULd, URd, 1, G, dw=dw)), ref, S, torch.float64, "staged roe flux")
+
+
+# ---------------------------------------------------------------------------
+# primitive-variable forms and temperature
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype,dw", [(torch.float64, False), (torch.float64, True), (torch.float32, False),
+                                      (torch.bfloat16, False)], ids=["f64", "f64dw", "f32", "bf16"])
+@pytest.mark.parametrize("n", [7, 4099])
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_primitive_forms_and_temperature(D, n, dtype, dw):
+    V, U, _ = fields(n, D, seed=400)
+    Vd, Vq = quantise(V, dtype)
+    Ud, Uq = quantise(U, dtype)
+    ref, S = oracle.flux_prim(D, -1, G, Vq, scale=True)
+    check(host(blocks.flux_prim(Vd, -1, G, dw=dw)), ref, S, dtype, "flux_prim all")
+    for d in range(D):
+        ref, S = oracle.flux_prim(D, d, G, Vq, scale=True)
+        check(host(blocks.flux_prim(Vd, d, G, dw=dw)), ref, S, dtype, f"flux_prim {d}")
+        ref, S = oracle.flux_jac_prim(D, d, G, Vq, scale=True)
+        check(host(blocks.flux_jac_prim(Vd, d, G, dw=dw)), ref, S, dtype, f"flux_jac_prim {d}")
+    for cv in (2.5, 0.7):
+        ref, S = oracle.temperature(D, G, cv, Uq, scale=True)
+        check(host([blocks.temperature(Ud, cv, G, dw=dw)]), ref, S, dtype, f"temperature cv={cv}")
