@@ -396,14 +396,16 @@ def run_e2e(args, U, W, out, stream, dev, world):
     from paper_1809_09851_gb300 import blocks
     n = U[0].shape[0]
     steps = max(1, min(args.e2e_steps, args.steps))
-    hU = [u.cpu().pin_memory() for u in U]
-    hW = [w.cpu().pin_memory() for w in W]
-    F, A, Y = out
-    hF = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in F]
-    hA = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in A]
-    hY = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in Y]
-    h2d = sum(t.numel() * t.element_size() for t in hU + hW)
-    d2h = sum(t.numel() * t.element_size() for t in hF + hA + hY)
+    # host fields as single pinned (planes, n) tensors, one row per plane
+    hIn = torch.empty(2 * NV, n, dtype=torch.float64, pin_memory=True)
+    for k, t in enumerate(list(U) + list(W)):
+        hIn[k].copy_(t)
+    hOut = torch.empty(PLANES_OUT, n, dtype=torch.float64, pin_memory=True)
+    rows_in, rows_out = list(hIn.unbind(0)), list(hOut.unbind(0))
+    hU, hW = rows_in[:NV], rows_in[NV:]
+    hF, hA, hY = rows_out[:D * NV], rows_out[D * NV:D * NV + NV * NV], rows_out[D * NV + NV * NV:]
+    h2d = hIn.numel() * hIn.element_size()
+    d2h = hOut.numel() * hOut.element_size()
     with torch.cuda.stream(stream):
         work = blocks.euler_fused_host(hU, hW, (hF, hA, hY), 0, GAMMA, chunk=args.e2e_chunk, device=dev,
                                        dw=True)
@@ -416,7 +418,7 @@ def run_e2e(args, U, W, out, stream, dev, world):
         e1.record(stream)
         torch.cuda.synchronize()
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
-    del hU, hW, hF, hA, hY, work
+    del hU, hW, hF, hA, hY, rows_in, rows_out, hIn, hOut, work
     return {"value": round(world * n * steps / t / 1e9, 4), "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": round(t * 1e3 / steps, 3), "chunk_points": args.e2e_chunk,

@@ -236,7 +236,8 @@ def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: i
     """fdbb_euler_fused over fields in pinned HOST memory.
 
     U (nv planes) and W (nv planes) are pinned CPU tensors and ``out`` the
-    (F, A, Y) plane lists, also pinned CPU tensors.  The points are processed
+    (F, A, Y) plane lists, also pinned CPU tensors (rows of one pinned
+    (planes, n) tensor copy fastest).  The points are processed
     in chunks of ``chunk`` through device staging buffers on three streams, so
     that the host-to-device copy of chunk i+1, the kernel on chunk i and the
     device-to-host copy of chunk i-1 overlap.  ``work`` may hold the staging

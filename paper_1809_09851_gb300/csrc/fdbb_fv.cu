@@ -216,13 +216,38 @@ template <class T> struct SlotRaw {
 
 // Rusanov flux through the face between slot l (left) and slot r (right) in
 // direction d, from plane tiles PL and PR.
-template <class T, int d>
-__device__ __forceinline__ void face(const PlaneTile<T>& PL, int l, const PlaneTile<T>& PR, int r, T (&Fh)[5]) {
-  const T sl = PL.v[20 + d][l], sr = PR.v[20 + d][r];
-  const T sm = sl > sr ? sl : sr;
+// What a face needs from one side in direction d: U, F_d(U) and |v_d| + c.
+template <class T> struct Side {
+  T u[5], f[5], s;
+};
+template <class T, int d> __device__ __forceinline__ Side<T> side(const PlaneTile<T>& P, int slot) {
+  Side<T> x;
 #pragma unroll
-  for (int q = 0; q < 5; ++q)
-    Fh[q] = T(0.5f) * (PL.v[5 + 5 * d + q][l] + PR.v[5 + 5 * d + q][r]) - T(0.5f) * sm * (PR.v[q][r] - PL.v[q][l]);
+  for (int q = 0; q < 5; ++q) {
+    x.u[q] = P.v[q][slot];
+    x.f[q] = P.v[5 + 5 * d + q][slot];
+  }
+  x.s = P.v[20 + d][slot];
+  return x;
+}
+// Same, reusing U already in registers.
+template <class T, int d> __device__ __forceinline__ Side<T> side(const PlaneTile<T>& P, int slot, const T (&u)[5]) {
+  Side<T> x;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    x.u[q] = u[q];
+    x.f[q] = P.v[5 + 5 * d + q][slot];
+  }
+  x.s = P.v[20 + d][slot];
+  return x;
+}
+
+// Rusanov flux through the face between the left side L and the right side R.
+template <class T>
+__device__ __forceinline__ void face(const Side<T>& L, const Side<T>& R, T (&Fh)[5]) {
+  const T sm = L.s > R.s ? L.s : R.s;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) Fh[q] = T(0.5f) * (L.f[q] + R.f[q]) - T(0.5f) * sm * (R.u[q] - L.u[q]);
 }
 
 // One step of every grid.  A block takes tiles of 32 x 8 cells in (x, y) and
@@ -288,7 +313,7 @@ template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_st
       T u[5];
       load_cell<T>(g, x, y, z0 == 0 ? n - 1 : z0 - 1, u);
       put_slot<T>(u, k, P1, own);
-      face<T, 2>(P1, own, tiles[0], own, zlo);
+      face<T>(side<T, 2>(P1, own), side<T, 2>(tiles[0], own), zlo);
     }
     __syncthreads();
     T vmax = T(0);
@@ -299,16 +324,20 @@ template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_st
       if (z + 1 < z1) load_plane(raw, z + 2 >= n ? z + 2 - n : z + 2);  // prefetch plane z + 2
       __syncthreads();
       if (active) {
-        T lo[5], hi[5], div[5];
-        face<T, 0>(C, own - 1, C, own, lo);
-        face<T, 0>(C, own, C, own + 1, hi);
+        T lo[5], hi[5], div[5], uc[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) uc[q] = C.v[q][own];  // the cell's own state, read once
+        const Side<T> cx = side<T, 0>(C, own, uc);
+        face<T>(side<T, 0>(C, own - 1), cx, lo);
+        face<T>(cx, side<T, 0>(C, own + 1), hi);
 #pragma unroll
         for (int q = 0; q < 5; ++q) div[q] = T(0) + (hi[q] - lo[q]);
-        face<T, 1>(C, own - kSX, C, own, lo);
-        face<T, 1>(C, own, C, own + kSX, hi);
+        const Side<T> cy = side<T, 1>(C, own, uc);
+        face<T>(side<T, 1>(C, own - kSX), cy, lo);
+        face<T>(cy, side<T, 1>(C, own + kSX), hi);
 #pragma unroll
         for (int q = 0; q < 5; ++q) div[q] = div[q] + (hi[q] - lo[q]);
-        face<T, 2>(C, own, N, own, hi);
+        face<T>(side<T, 2>(C, own, uc), side<T, 2>(N, own), hi);
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           div[q] = div[q] + (hi[q] - zlo[q]);
@@ -319,7 +348,7 @@ template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_st
         T un[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-          un[q] = C.v[q][own] - lam * div[q];
+          un[q] = uc[q] - lam * div[q];
           static_cast<T*>(g.Unew[q])[c] = un[q];
         }
         Nw.rho = un[0];
