@@ -56,6 +56,25 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = ci
+        eos_sig = {
+            "oracle_eos_prim_from_cons": [vp, ci, i64, vp, vp, vp],
+            "oracle_eos_cons_from_prim": [vp, ci, i64, vp, vp, vp],
+            "oracle_eos_pc": [vp, ci, i64, vp, vp, vp],
+            "oracle_eos_temperature": [vp, ci, i64, vp, vp, vp],
+            "oracle_eos_flux": [vp, ci, ci, i64, vp, vp, vp],
+            "oracle_eos_flux_jac": [vp, ci, ci, i64, vp, vp, vp],
+            "oracle_eos_char_transform": [vp, ci, ci, ci, i64, vp, vp, vp, vp],
+            "oracle_eos_flux_vjp": [vp, ci, ci, i64, vp, vp, vp, vp],
+            "oracle_eos_euler_fused": [vp, ci, ci, i64, vp, vp, vp, vp],
+            "oracle_eos_flux_prim": [vp, ci, ci, i64, vp, vp, vp],
+            "oracle_eos_flux_jac_prim": [vp, ci, ci, i64, vp, vp, vp],
+            "oracle_eos_eig": [vp, ci, ci, i64, vp, vp, vp, vp, vp],
+            "oracle_eos_point": [vp, i64, vp, vp, vp, vp],
+        }
+        for name, args in eos_sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ci
         lib.oracle_rusanov_dt.argtypes = [ci, dbl, dbl, vp]
         lib.oracle_rusanov_dt.restype = dbl
         _lib = lib
@@ -237,9 +256,129 @@ def rusanov_run(n, gamma, cfl, steps, U):
     return Uk, dts[:steps]
 
 
+# ---------------------------------------------------------------------------
+# General equations of state (paper section 2.2, "Equations of state").
+# An EOS is a dict: {"kind": "nasg", "gamma", "p_inf", "b", "q", "cv"} (the
+# Noble-Abel stiffened gas) or {"kind": "vdw", "gamma", "a", "b", "cv"} (van
+# der Waals); missing parameters are 0 (cv: 1).
+# ---------------------------------------------------------------------------
+
+_EOS_KINDS = {"nasg": 1, "vdw": 2}
+
+
+def _eos(eos):
+    kind = _EOS_KINDS[eos["kind"]]
+    prm = np.array([kind, eos["gamma"], eos.get("p_inf", 0.0), eos.get("b", 0.0), eos.get("q", 0.0),
+                    eos.get("a", 0.0), eos.get("cv", 1.0)], dtype=np.float64)
+    return prm, ctypes.c_void_p(prm.ctypes.data)
+
+
+def _call_eos(name, eos, nout, n, args, scale):
+    prm, pp = _eos(eos)
+    po, out = _new(nout, n)
+    ps, sc = _new(nout, n) if scale else (None, None)
+    rc = getattr(_load(), name)(pp, *args, po, ps)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments ({name})")
+    return (out, sc) if scale else out
+
+
+def eos_prim_from_cons(eos, D, U, scale=False):
+    pu, Uk, n = _planes(U)
+    return _call_eos("oracle_eos_prim_from_cons", eos, nv(D), n, (D, n, pu), scale)
+
+
+def eos_cons_from_prim(eos, D, V, scale=False):
+    pv, Vk, n = _planes(V)
+    return _call_eos("oracle_eos_cons_from_prim", eos, nv(D), n, (D, n, pv), scale)
+
+
+def eos_pc(eos, D, U, scale=False):
+    """[p, c] under a general EOS."""
+    pu, Uk, n = _planes(U)
+    return _call_eos("oracle_eos_pc", eos, 2, n, (D, n, pu), scale)
+
+
+def eos_temperature(eos, D, U, scale=False):
+    pu, Uk, n = _planes(U)
+    return _call_eos("oracle_eos_temperature", eos, 1, n, (D, n, pu), scale)
+
+
+def eos_flux(eos, D, d, U, scale=False):
+    pu, Uk, n = _planes(U)
+    k = nv(D) * (D if d < 0 else 1)
+    return _call_eos("oracle_eos_flux", eos, k, n, (D, d, n, pu), scale)
+
+
+def eos_flux_jac(eos, D, d, U, scale=False):
+    pu, Uk, n = _planes(U)
+    return _call_eos("oracle_eos_flux_jac", eos, nv(D) ** 2, n, (D, d, n, pu), scale)
+
+
+def eos_char_transform(eos, D, d, U, W, inverse=False, scale=False):
+    pu, Uk, n = _planes(U)
+    pw, Wk, _ = _planes(W, n)
+    return _call_eos("oracle_eos_char_transform", eos, nv(D), n, (D, d, int(bool(inverse)), n, pu, pw), scale)
+
+
+def eos_flux_vjp(eos, D, d, U, G, scale=False):
+    pu, Uk, n = _planes(U)
+    pg, Gk, _ = _planes(G, n)
+    return _call_eos("oracle_eos_flux_vjp", eos, nv(D), n, (D, d, n, pu, pg), scale)
+
+
+def eos_euler_fused(eos, D, dj, U, W, scale=False):
+    pu, Uk, n = _planes(U)
+    pw, Wk, _ = _planes(W, n)
+    k = D * nv(D) + nv(D) ** 2 + nv(D)
+    return _call_eos("oracle_eos_euler_fused", eos, k, n, (D, dj, n, pu, pw), scale)
+
+
+def eos_flux_prim(eos, D, d, V, scale=False):
+    pv, Vk, n = _planes(V)
+    k = nv(D) * (D if d < 0 else 1)
+    return _call_eos("oracle_eos_flux_prim", eos, k, n, (D, d, n, pv), scale)
+
+
+def eos_flux_jac_prim(eos, D, d, V, scale=False):
+    pv, Vk, n = _planes(V)
+    return _call_eos("oracle_eos_flux_jac_prim", eos, nv(D) ** 2, n, (D, d, n, pv), scale)
+
+
+def eos_eig(eos, D, d, U):
+    """(R, L, lam, aux) with aux = [p, p_rho, p_e, T, e] per point."""
+    prm, pp = _eos(eos)
+    pu, Uk, n = _planes(U)
+    k = nv(D)
+    pr, R = _new(k * k, n)
+    pl, L = _new(k * k, n)
+    pm, lam = _new(k, n)
+    pa, aux = _new(5, n)
+    if _load().oracle_eos_eig(pp, D, d, n, pu, pr, pl, pm, pa) != 0:
+        raise ValueError("oracle rejected the arguments (oracle_eos_eig)")
+    return R, L, lam, aux
+
+
+def eos_point(eos, rho, e):
+    """EOS functions at points: ([p, p_rho, p_e, T] at (rho, e),
+    [rho e, d(rho e)/drho|_p, d(rho e)/dp|_rho] at (rho, p = e))."""
+    prm, pp = _eos(eos)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    n = rho.shape[0]
+    p1, a = _new(4, n)
+    p2, z = _new(3, n)
+    if _load().oracle_eos_point(pp, n, ctypes.c_void_p(rho.ctypes.data), ctypes.c_void_p(e.ctypes.data),
+                                p1, p2) != 0:
+        raise ValueError("oracle rejected the arguments (oracle_eos_point)")
+    return a, z
+
+
 __all__ = [
     "v_mag2", "prim_from_cons", "cons_from_prim", "eos", "riemann_inv", "flux",
     "flux_jac", "char_transform", "flux_vjp", "euler_fused", "eig", "rusanov_dt",
     "rusanov_step", "rusanov_run", "roe_flux", "roe_char_transform", "flux_prim", "flux_jac_prim", "temperature",
-    "library_path", "nv",
+    "eos_prim_from_cons", "eos_cons_from_prim", "eos_pc", "eos_temperature", "eos_flux", "eos_flux_jac",
+    "eos_char_transform", "eos_flux_vjp", "eos_euler_fused", "eos_flux_prim", "eos_flux_jac_prim", "eos_eig",
+    "eos_point", "library_path", "nv",
 ]

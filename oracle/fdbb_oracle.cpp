@@ -112,6 +112,9 @@ template <class T> struct State {
   T p;                // pressure p = (gamma - 1) (rhoE - rho q)
   T c;                // speed of sound c = sqrt(gamma p / rho)
   T H;                // total specific enthalpy H = (rhoE + p) / rho
+  // Set only by the general-EOS state (state_from_cons_eos):
+  T e;                // specific internal energy
+  T dp[5];            // dp/dU: dp/drho, dp/dm_1..dp/dm_D, dp/drhoE (others unused)
 };
 
 template <class T>
@@ -650,6 +653,465 @@ void run_roe_char(int D, int d, double g, int inverse, int64_t n, const double* 
 }
 
 // ---------------------------------------------------------------------------
+// General equations of state (paper section 2.2, "Equations of state": a
+// user EOS of the form f(p, V, T) = 0 supplies p(rho, e) and T(rho, e),
+// Fig. 10).  The paper prints no EOS besides the ideal gas; two standard
+// families stand in for user EOS here:
+//
+//  NASG, the Noble-Abel stiffened gas (O. Le Metayer and R. Saurel, Phys.
+//  Fluids 28, 046102, 2016), parameters gamma, p_inf, b, q, c_v:
+//     p(rho, e)   = (gamma - 1)(e - q) rho / (1 - b rho) - gamma p_inf
+//     T(rho, e)   = (e - q - p_inf (1/rho - b)) / c_v
+//     rho e(rho,p) = (p + gamma p_inf)(1 - b rho)/(gamma - 1) + rho q
+//  (the ideal gas for p_inf = b = q = 0, the stiffened gas for b = 0);
+//
+//  van der Waals with caloric law e = c_v T - a rho, parameters gamma, a, b, c_v:
+//     p(rho, e)   = (gamma - 1)(rho e + a rho^2)/(1 - b rho) - a rho^2
+//     T(rho, e)   = (e + a rho) / c_v
+//     rho e(rho,p) = (p + a rho^2)(1 - b rho)/(gamma - 1) - a rho^2.
+//
+// The partial derivatives p_rho = dp/drho at constant e, p_e = dp/de at
+// constant rho, and those of rho e(rho, p) are written out by hand below.
+// Everything else follows from the definitions:
+//   speed of sound  c^2 = dp/drho at constant entropy = p_rho + p_e p / rho^2
+//   (de = p / rho^2 drho along an isentrope), and the Euler algebra of the
+//   ideal-gas functions above with the pressure gradient dp/dU in place of
+//   the ideal-gas one.
+// ---------------------------------------------------------------------------
+
+enum { EOS_NASG = 1, EOS_VDW = 2 };
+
+struct EosModel {
+  int kind;
+  double gamma, p_inf, b, q, a, cv;
+};
+
+// params = {kind, gamma, p_inf, b, q, a, cv}
+inline bool eos_from_params(const double* prm, EosModel& M) {
+  if (!prm) return false;
+  M.kind = (int)prm[0];
+  M.gamma = prm[1];
+  M.p_inf = prm[2];
+  M.b = prm[3];
+  M.q = prm[4];
+  M.a = prm[5];
+  M.cv = prm[6];
+  if (M.kind != EOS_NASG && M.kind != EOS_VDW) return false;
+  if (!(M.gamma > 1.0) || !(M.cv > 0.0) || !(M.b >= 0.0)) return false;
+  if (M.kind == EOS_NASG && !(M.p_inf >= 0.0)) return false;
+  if (M.kind == EOS_VDW && !(M.a >= 0.0)) return false;
+  return true;
+}
+
+// p, p_rho = dp/drho|_e and p_e = dp/de|_rho at (rho, e).
+template <class T> void eos_p(const EosModel& M, T rho, T e, T& p, T& p_rho, T& p_e) {
+  const T g = lit<T>(M.gamma), a1 = g - lit<T>(1.0), one = lit<T>(1.0);
+  const T b = lit<T>(M.b);
+  const T den = one - b * rho;  // 1 - b rho
+  if (M.kind == EOS_NASG) {
+    const T q = lit<T>(M.q), pinf = lit<T>(M.p_inf);
+    // d/drho [rho / (1 - b rho)] = 1 / (1 - b rho)^2
+    p = a1 * (e - q) * rho / den - g * pinf;
+    p_rho = a1 * (e - q) / (den * den);
+    p_e = a1 * rho / den;
+  } else {
+    const T a = lit<T>(M.a);
+    const T num = rho * e + a * rho * rho;  // rho e + a rho^2
+    p = a1 * num / den - a * rho * rho;
+    // d/drho [num / den] = ((e + 2 a rho) den + b num) / den^2
+    p_rho = a1 * ((e + lit<T>(2.0) * a * rho) * den + b * num) / (den * den) - lit<T>(2.0) * a * rho;
+    p_e = a1 * rho / den;
+  }
+}
+
+// Temperature T(rho, e).
+template <class T> T eos_T(const EosModel& M, T rho, T e) {
+  const T cv = lit<T>(M.cv);
+  if (M.kind == EOS_NASG) {
+    const T one = lit<T>(1.0);
+    return (e - lit<T>(M.q) - lit<T>(M.p_inf) * (one / rho - lit<T>(M.b))) / cv;
+  }
+  return (e + lit<T>(M.a) * rho) / cv;
+}
+
+// Internal energy density rho e(rho, p) and its partial derivatives
+// z_rho = d(rho e)/drho|_p, z_p = d(rho e)/dp|_rho.
+template <class T> void eos_rhoe(const EosModel& M, T rho, T p, T& z, T& z_rho, T& z_p) {
+  const T g = lit<T>(M.gamma), a1 = g - lit<T>(1.0), one = lit<T>(1.0);
+  const T b = lit<T>(M.b);
+  const T den = one - b * rho;
+  if (M.kind == EOS_NASG) {
+    const T q = lit<T>(M.q), pinf = lit<T>(M.p_inf);
+    const T pp = p + g * pinf;
+    z = pp * den / a1 + rho * q;
+    z_rho = q - b * pp / a1;
+    z_p = den / a1;
+  } else {
+    const T a = lit<T>(M.a);
+    const T pp = p + a * rho * rho;
+    z = pp * den / a1 - a * rho * rho;
+    // d/drho: (2 a rho (1 - b rho) - b (p + a rho^2)) / (gamma - 1) - 2 a rho
+    z_rho = (lit<T>(2.0) * a * rho * den - b * pp) / a1 - lit<T>(2.0) * a * rho;
+    z_p = den / a1;
+  }
+}
+
+// Conservative state under a general EOS: e = (rhoE - rho q)/rho, p and c as
+// above, H = (rhoE + p)/rho and the pressure gradient dp/dU by the chain rule
+// through e(rho, m, rhoE):
+//   de/drho = (q - e)/rho,  de/dm_j = -v_j/rho,  de/drhoE = 1/rho, so
+//   dp/drho = p_rho + p_e (q - e)/rho, dp/dm_j = -p_e v_j/rho, dp/drhoE = p_e/rho.
+template <class T>
+State<T> state_from_cons_eos(int D, const EosModel& M, const double* const* U, int64_t i) {
+  State<T> s;
+  s.D = D;
+  s.gamma = lit<T>(M.gamma);
+  s.a1 = s.gamma - lit<T>(1.0);
+  s.rho = lit<T>(U[0][i]);
+  for (int k = 0; k < 3; ++k) s.m[k] = lit<T>(0.0);
+  for (int k = 0; k < D; ++k) s.m[k] = lit<T>(U[1 + k][i]);
+  s.rhoE = lit<T>(U[D + 1][i]);
+  for (int k = 0; k < 3; ++k) s.v[k] = lit<T>(0.0);
+  for (int k = 0; k < D; ++k) s.v[k] = s.m[k] / s.rho;
+  T v2 = s.v[0] * s.v[0];
+  for (int k = 1; k < D; ++k) v2 = v2 + s.v[k] * s.v[k];
+  s.q = lit<T>(0.5) * v2;
+  s.e = (s.rhoE - s.rho * s.q) / s.rho;
+  T p_rho, p_e;
+  eos_p(M, s.rho, s.e, s.p, p_rho, p_e);
+  s.c = sqrt_(p_rho + p_e * s.p / (s.rho * s.rho));
+  s.H = (s.rhoE + s.p) / s.rho;
+  for (int k = 0; k < 5; ++k) s.dp[k] = lit<T>(0.0);
+  s.dp[0] = p_rho + p_e * (s.q - s.e) / s.rho;
+  for (int k = 0; k < D; ++k) s.dp[1 + k] = -(p_e * s.v[k] / s.rho);
+  s.dp[D + 1] = p_e / s.rho;
+  return s;
+}
+
+// A_d = dF_d/dU under a general EOS, differentiating the flux of flux_d term
+// by term with dp/dU from the state (u = v_d):
+//   row 0    : e_{1+d}
+//   row 1+i  : d(m_i u)/dU + delta_id dp/dU, with d(m_i u)/drho = -u v_i,
+//              d(m_i u)/dm_j = delta_ij u + delta_jd v_i
+//   row nv-1 : d(u rho H)/dU = u (dp/dU) + (-u H, delta_jd H, u)
+template <class T> void jacobian_eos_d(const State<T>& s, int d, T* A) {
+  const int D = s.D, nv = D + 2;
+  const T zero = lit<T>(0.0), one = lit<T>(1.0);
+  for (int k = 0; k < nv * nv; ++k) A[k] = zero;
+  const T u = s.v[d];
+  A[0 * nv + (1 + d)] = one;
+  for (int i = 0; i < D; ++i) {
+    T* row = A + (1 + i) * nv;
+    row[0] = -(u * s.v[i]);
+    for (int j = 0; j < D; ++j) {
+      T e = zero;
+      if (j == i) e = e + u;
+      if (j == d) e = e + s.v[i];
+      row[1 + j] = e;
+    }
+    if (i == d)
+      for (int k = 0; k < nv; ++k) row[k] = row[k] + s.dp[k];
+  }
+  T* last = A + (nv - 1) * nv;
+  last[0] = u * s.dp[0] - u * s.H;
+  for (int j = 0; j < D; ++j) {
+    last[1 + j] = u * s.dp[1 + j];
+    if (j == d) last[1 + j] = last[1 + j] + s.H;
+  }
+  last[nv - 1] = u * s.dp[nv - 1] + u;
+}
+
+// Right eigenvectors of A_d under a general EOS (columns of R, eigenvalues
+// u - c, u, ..., u, u + c):
+//   r_1 = (1, v - c e_d, H - u c),  r_nv = (1, v + c e_d, H + u c),
+//   r_2 = (1, v, eps) with eps fixed by dp/dU . r_2 = 0 (no pressure jump
+//         across the entropy wave): eps = -(dp_rho + sum_j dp_mj v_j)/dp_rhoE,
+//   r_{2+k} = (0, e_t, v_t)  (dp/dU . r = -p_e v_t/rho + p_e v_t/rho = 0).
+template <class T> void right_eig_eos_d(const State<T>& s, int d, T* R, T* lam) {
+  const int D = s.D, nv = D + 2;
+  const T zero = lit<T>(0.0), one = lit<T>(1.0);
+  const T u = s.v[d], c = s.c;
+  for (int k = 0; k < nv * nv; ++k) R[k] = zero;
+  R[0 * nv + 0] = one;
+  for (int i = 0; i < D; ++i) R[(1 + i) * nv + 0] = (i == d) ? s.v[i] - c : s.v[i];
+  R[(nv - 1) * nv + 0] = s.H - u * c;
+  T num = s.dp[0];
+  for (int j = 0; j < D; ++j) num = num + s.dp[1 + j] * s.v[j];
+  R[0 * nv + 1] = one;
+  for (int i = 0; i < D; ++i) R[(1 + i) * nv + 1] = s.v[i];
+  R[(nv - 1) * nv + 1] = -(num / s.dp[nv - 1]);
+  for (int k = 0; k < D - 1; ++k) {
+    int t = tangential(D, d, k);
+    R[(1 + t) * nv + (2 + k)] = one;
+    R[(nv - 1) * nv + (2 + k)] = s.v[t];
+  }
+  R[0 * nv + (nv - 1)] = one;
+  for (int i = 0; i < D; ++i) R[(1 + i) * nv + (nv - 1)] = (i == d) ? s.v[i] + c : s.v[i];
+  R[(nv - 1) * nv + (nv - 1)] = s.H + u * c;
+  if (lam) {
+    lam[0] = u - c;
+    for (int k = 1; k < nv - 1; ++k) lam[k] = u;
+    lam[nv - 1] = u + c;
+  }
+}
+
+// Left eigenvectors (rows of L = R^{-1}) under a general EOS, with
+// beta = (dp/dU) / c^2 (a row vector):
+//   l_1  = 1/2 (beta + (u/c) e_0 - (1/c) e_{1+d})
+//   l_2  = e_0 - beta
+//   l_{2+k} = -v_t e_0 + e_{1+t}
+//   l_nv = 1/2 (beta - (u/c) e_0 + (1/c) e_{1+d})
+// (the acoustic rows pick out (dp +- rho c du_d)/(2 c^2), the entropy row
+// drho - dp/c^2).
+template <class T> void left_eig_eos_d(const State<T>& s, int d, T* L) {
+  const int D = s.D, nv = D + 2;
+  const T zero = lit<T>(0.0), one = lit<T>(1.0), half = lit<T>(0.5);
+  const T u = s.v[d], c = s.c;
+  const T c2 = c * c;
+  for (int k = 0; k < nv * nv; ++k) L[k] = zero;
+  T* l1 = L + 0 * nv;
+  T* l2 = L + 1 * nv;
+  T* ln = L + (nv - 1) * nv;
+  for (int k = 0; k < nv; ++k) {
+    const T beta = s.dp[k] / c2;
+    T a = beta, b = beta;
+    if (k == 0) {
+      a = a + u / c;
+      b = b - u / c;
+    } else if (k == 1 + d) {
+      a = a - one / c;
+      b = b + one / c;
+    }
+    l1[k] = half * a;
+    ln[k] = half * b;
+    l2[k] = (k == 0) ? one - beta : -beta;
+  }
+  for (int k = 0; k < D - 1; ++k) {
+    int t = tangential(D, d, k);
+    T* lk = L + (2 + k) * nv;
+    lk[0] = -s.v[t];
+    lk[1 + t] = one;
+  }
+}
+
+// Flux from primitive variables under a general EOS:
+//   F_d = (rho u, rho u v + p e_d, u (rho e(rho, p) + rho |v|^2 / 2 + p)).
+template <class T>
+void flux_prim_eos_d(int D, const EosModel& M, const double* const* V, int64_t i, int d, T* F) {
+  const T rho = lit<T>(V[0][i]), p = lit<T>(V[D + 1][i]);
+  T v[3];
+  for (int k = 0; k < D; ++k) v[k] = lit<T>(V[1 + k][i]);
+  T v2 = v[0] * v[0];
+  for (int k = 1; k < D; ++k) v2 = v2 + v[k] * v[k];
+  T z, z_rho, z_p;
+  eos_rhoe(M, rho, p, z, z_rho, z_p);
+  const T u = v[d];
+  F[0] = rho * u;
+  for (int k = 0; k < D; ++k) {
+    F[1 + k] = rho * u * v[k];
+    if (k == d) F[1 + k] = F[1 + k] + p;
+  }
+  F[D + 1] = u * (z + lit<T>(0.5) * rho * v2 + p);
+}
+
+// B_d = dF_d/dV under a general EOS (rows in U order, columns in V order):
+// rows 0..D as for the ideal gas; row nv-1 differentiates
+// u (z(rho, p) + rho |v|^2/2 + p):
+//   (u (z_rho + |v|^2/2), delta_jd (z + rho |v|^2/2 + p) + rho u v_j, u (z_p + 1)).
+template <class T>
+void jac_prim_eos_d(int D, const EosModel& M, const double* const* V, int64_t i, int d, T* B) {
+  const int nv = D + 2;
+  const T zero = lit<T>(0.0), one = lit<T>(1.0);
+  const T rho = lit<T>(V[0][i]), p = lit<T>(V[D + 1][i]);
+  T v[3];
+  for (int k = 0; k < D; ++k) v[k] = lit<T>(V[1 + k][i]);
+  T v2 = v[0] * v[0];
+  for (int k = 1; k < D; ++k) v2 = v2 + v[k] * v[k];
+  T z, z_rho, z_p;
+  eos_rhoe(M, rho, p, z, z_rho, z_p);
+  const T u = v[d];
+  for (int k = 0; k < nv * nv; ++k) B[k] = zero;
+  B[0] = u;
+  B[1 + d] = rho;
+  for (int r = 0; r < D; ++r) {
+    T* row = B + (1 + r) * nv;
+    row[0] = u * v[r];
+    for (int j = 0; j < D; ++j) {
+      T e = zero;
+      if (j == d) e = e + rho * v[r];
+      if (j == r) e = e + rho * u;
+      row[1 + j] = e;
+    }
+    row[nv - 1] = (r == d) ? one : zero;
+  }
+  T* last = B + (nv - 1) * nv;
+  last[0] = u * (z_rho + lit<T>(0.5) * v2);
+  for (int j = 0; j < D; ++j) {
+    T e = rho * u * v[j];
+    if (j == d) e = e + (z + lit<T>(0.5) * rho * v2 + p);
+    last[1 + j] = e;
+  }
+  last[nv - 1] = u * (z_p + one);
+}
+
+// Array drivers of the general-EOS blocks (same layouts as the ideal-gas ones).
+template <class T>
+void run_eos_prim_from_cons(int D, const EosModel& M, int64_t n, const double* const* U, double* const* V,
+                            double* const* sc) {
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons_eos<T>(D, M, U, i);
+    put(V, sc, 0, i, s.rho);
+    for (int k = 0; k < D; ++k) put(V, sc, 1 + k, i, s.v[k]);
+    put(V, sc, D + 1, i, s.p);
+  }
+}
+
+template <class T>
+void run_eos_cons_from_prim(int D, const EosModel& M, int64_t n, const double* const* V, double* const* U,
+                            double* const* sc) {
+  // m_i = rho v_i, rhoE = rho e(rho, p) + rho |v|^2 / 2.
+  for (int64_t i = 0; i < n; ++i) {
+    T rho = lit<T>(V[0][i]);
+    T v2 = lit<T>(0.0);
+    put(U, sc, 0, i, rho);
+    for (int k = 0; k < D; ++k) {
+      T vk = lit<T>(V[1 + k][i]);
+      put(U, sc, 1 + k, i, rho * vk);
+      v2 = (k == 0) ? vk * vk : v2 + vk * vk;
+    }
+    T z, z_rho, z_p;
+    eos_rhoe(M, rho, lit<T>(V[D + 1][i]), z, z_rho, z_p);
+    put(U, sc, D + 1, i, z + lit<T>(0.5) * rho * v2);
+  }
+}
+
+template <class T>
+void run_eos_pc(int D, const EosModel& M, int64_t n, const double* const* U, double* const* out,
+                double* const* sc) {
+  // out = {p, c}
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons_eos<T>(D, M, U, i);
+    put(out, sc, 0, i, s.p);
+    put(out, sc, 1, i, s.c);
+  }
+}
+
+template <class T>
+void run_eos_temperature(int D, const EosModel& M, int64_t n, const double* const* U, double* const* out,
+                         double* const* sc) {
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons_eos<T>(D, M, U, i);
+    put(out, sc, 0, i, eos_T(M, s.rho, s.e));
+  }
+}
+
+template <class T>
+void run_eos_flux(int D, int dir, const EosModel& M, int64_t n, const double* const* U, double* const* F,
+                  double* const* sc) {
+  const int nv = D + 2;
+  T f[5];
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons_eos<T>(D, M, U, i);
+    for (int d = 0; d < D; ++d) {
+      if (dir >= 0 && d != dir) continue;
+      flux_d(s, d, f);
+      const int base = (dir < 0) ? d * nv : 0;
+      for (int k = 0; k < nv; ++k) put(F, sc, base + k, i, f[k]);
+    }
+  }
+}
+
+template <class T>
+void run_eos_flux_jac(int D, int d, const EosModel& M, int64_t n, const double* const* U, double* const* A,
+                      double* const* sc) {
+  const int nv = D + 2;
+  T a[25];
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons_eos<T>(D, M, U, i);
+    jacobian_eos_d(s, d, a);
+    for (int k = 0; k < nv * nv; ++k) put(A, sc, k, i, a[k]);
+  }
+}
+
+template <class T>
+void run_eos_char(int D, int d, const EosModel& M, int inverse, int64_t n, const double* const* U,
+                  const double* const* W, double* const* Y, double* const* sc) {
+  const int nv = D + 2;
+  T Mx[25], w[5], y[5];
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons_eos<T>(D, M, U, i);
+    if (inverse)
+      right_eig_eos_d(s, d, Mx, (T*)nullptr);
+    else
+      left_eig_eos_d(s, d, Mx);
+    for (int k = 0; k < nv; ++k) w[k] = lit<T>(W[k][i]);
+    matvec(nv, Mx, w, y);
+    for (int k = 0; k < nv; ++k) put(Y, sc, k, i, y[k]);
+  }
+}
+
+template <class T>
+void run_eos_flux_vjp(int D, int d, const EosModel& M, int64_t n, const double* const* U,
+                      const double* const* G, double* const* gU, double* const* sc) {
+  const int nv = D + 2;
+  T a[25], gg[5], y[5];
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons_eos<T>(D, M, U, i);
+    jacobian_eos_d(s, d, a);
+    for (int k = 0; k < nv; ++k) gg[k] = lit<T>(G[k][i]);
+    matvec_t(nv, a, gg, y);
+    for (int k = 0; k < nv; ++k) put(gU, sc, k, i, y[k]);
+  }
+}
+
+template <class T>
+void run_eos_fused(int D, int dj, const EosModel& M, int64_t n, const double* const* U, const double* const* W,
+                   double* const* out, double* const* sc) {
+  // run_eos_flux(dir=-1), run_eos_flux_jac and run_eos_char(forward) in turn.
+  const int nv = D + 2;
+  const int off_A = D * nv, off_Y = D * nv + nv * nv;
+  T f[5], a[25], Mx[25], w[5], y[5];
+  for (int64_t i = 0; i < n; ++i) {
+    State<T> s = state_from_cons_eos<T>(D, M, U, i);
+    for (int d = 0; d < D; ++d) {
+      flux_d(s, d, f);
+      for (int k = 0; k < nv; ++k) put(out, sc, d * nv + k, i, f[k]);
+    }
+    jacobian_eos_d(s, dj, a);
+    for (int k = 0; k < nv * nv; ++k) put(out, sc, off_A + k, i, a[k]);
+    left_eig_eos_d(s, dj, Mx);
+    for (int k = 0; k < nv; ++k) w[k] = lit<T>(W[k][i]);
+    matvec(nv, Mx, w, y);
+    for (int k = 0; k < nv; ++k) put(out, sc, off_Y + k, i, y[k]);
+  }
+}
+
+template <class T>
+void run_eos_flux_prim(int D, int dir, const EosModel& M, int64_t n, const double* const* V, double* const* F,
+                       double* const* sc) {
+  const int nv = D + 2;
+  T f[5];
+  for (int64_t i = 0; i < n; ++i)
+    for (int d = 0; d < D; ++d) {
+      if (dir >= 0 && d != dir) continue;
+      flux_prim_eos_d<T>(D, M, V, i, d, f);
+      const int base = (dir < 0) ? d * nv : 0;
+      for (int k = 0; k < nv; ++k) put(F, sc, base + k, i, f[k]);
+    }
+}
+
+template <class T>
+void run_eos_jac_prim(int D, int d, const EosModel& M, int64_t n, const double* const* V, double* const* B,
+                      double* const* sc) {
+  const int nv = D + 2;
+  T b[25];
+  for (int64_t i = 0; i < n; ++i) {
+    jac_prim_eos_d<T>(D, M, V, i, d, b);
+    for (int k = 0; k < nv * nv; ++k) put(B, sc, k, i, b[k]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Explicit first-order finite-volume step with the Rusanov (local
 // Lax-Friedrichs) numerical flux on a periodic n^3 grid over [0,1]^3.
 // Cell (i,j,k) is point index (k*n + j)*n + i (x fastest).
@@ -866,6 +1328,156 @@ int oracle_eig(int D, int d, double g, int64_t n, const double* const* U, double
   }
   return 0;
 }
+
+// General-EOS blocks.  `eos` = {kind (1 NASG, 2 van der Waals), gamma,
+// p_inf, b, q, a, c_v}; outputs and layouts as for the ideal-gas blocks
+// (eos_pc: {p, c}).
+#define ORACLE_EOS_ARGS(cond)                      \
+  EosModel M;                                      \
+  if (bad_dim(D) || n < 0 || !eos_from_params(eos, M) || !(cond)) return 1;
+
+int oracle_eos_prim_from_cons(const double* eos, int D, int64_t n, const double* const* U, double* const* V,
+                              double* const* scale) {
+  ORACLE_EOS_ARGS(true)
+  run_eos_prim_from_cons<double>(D, M, n, U, V, nullptr);
+  if (scale) run_eos_prim_from_cons<Err>(D, M, n, U, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_cons_from_prim(const double* eos, int D, int64_t n, const double* const* V, double* const* U,
+                              double* const* scale) {
+  ORACLE_EOS_ARGS(true)
+  run_eos_cons_from_prim<double>(D, M, n, V, U, nullptr);
+  if (scale) run_eos_cons_from_prim<Err>(D, M, n, V, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_pc(const double* eos, int D, int64_t n, const double* const* U, double* const* out,
+                  double* const* scale) {
+  ORACLE_EOS_ARGS(true)
+  run_eos_pc<double>(D, M, n, U, out, nullptr);
+  if (scale) run_eos_pc<Err>(D, M, n, U, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_temperature(const double* eos, int D, int64_t n, const double* const* U, double* const* out,
+                           double* const* scale) {
+  ORACLE_EOS_ARGS(true)
+  run_eos_temperature<double>(D, M, n, U, out, nullptr);
+  if (scale) run_eos_temperature<Err>(D, M, n, U, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_flux(const double* eos, int D, int dir, int64_t n, const double* const* U, double* const* F,
+                    double* const* scale) {
+  ORACLE_EOS_ARGS(dir >= -1 && dir < D)
+  run_eos_flux<double>(D, dir, M, n, U, F, nullptr);
+  if (scale) run_eos_flux<Err>(D, dir, M, n, U, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_flux_jac(const double* eos, int D, int d, int64_t n, const double* const* U, double* const* A,
+                        double* const* scale) {
+  ORACLE_EOS_ARGS(d >= 0 && d < D)
+  run_eos_flux_jac<double>(D, d, M, n, U, A, nullptr);
+  if (scale) run_eos_flux_jac<Err>(D, d, M, n, U, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_char_transform(const double* eos, int D, int d, int inverse, int64_t n, const double* const* U,
+                              const double* const* W, double* const* Y, double* const* scale) {
+  ORACLE_EOS_ARGS(d >= 0 && d < D)
+  run_eos_char<double>(D, d, M, inverse, n, U, W, Y, nullptr);
+  if (scale) run_eos_char<Err>(D, d, M, inverse, n, U, W, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_flux_vjp(const double* eos, int D, int d, int64_t n, const double* const* U,
+                        const double* const* G, double* const* gU, double* const* scale) {
+  ORACLE_EOS_ARGS(d >= 0 && d < D)
+  run_eos_flux_vjp<double>(D, d, M, n, U, G, gU, nullptr);
+  if (scale) run_eos_flux_vjp<Err>(D, d, M, n, U, G, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_euler_fused(const double* eos, int D, int dj, int64_t n, const double* const* U,
+                           const double* const* W, double* const* out, double* const* scale) {
+  ORACLE_EOS_ARGS(dj >= 0 && dj < D)
+  run_eos_fused<double>(D, dj, M, n, U, W, out, nullptr);
+  if (scale) run_eos_fused<Err>(D, dj, M, n, U, W, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_flux_prim(const double* eos, int D, int dir, int64_t n, const double* const* V,
+                         double* const* F, double* const* scale) {
+  ORACLE_EOS_ARGS(dir >= -1 && dir < D)
+  run_eos_flux_prim<double>(D, dir, M, n, V, F, nullptr);
+  if (scale) run_eos_flux_prim<Err>(D, dir, M, n, V, nullptr, scale);
+  return 0;
+}
+
+int oracle_eos_flux_jac_prim(const double* eos, int D, int d, int64_t n, const double* const* V,
+                             double* const* B, double* const* scale) {
+  ORACLE_EOS_ARGS(d >= 0 && d < D)
+  run_eos_jac_prim<double>(D, d, M, n, V, B, nullptr);
+  if (scale) run_eos_jac_prim<Err>(D, d, M, n, V, nullptr, scale);
+  return 0;
+}
+
+// Eigen-decomposition under a general EOS (as oracle_eig), plus the raw EOS
+// values at each point: aux = {p, p_rho, p_e, T, e} (any entry may be NULL).
+int oracle_eos_eig(const double* eos, int D, int d, int64_t n, const double* const* U, double* const* R,
+                   double* const* L, double* const* lam, double* const* aux) {
+  ORACLE_EOS_ARGS(d >= 0 && d < D)
+  const int nv = D + 2;
+  double r[25], l[25], lm[5];
+  for (int64_t i = 0; i < n; ++i) {
+    State<double> s = state_from_cons_eos<double>(D, M, U, i);
+    right_eig_eos_d(s, d, r, lm);
+    left_eig_eos_d(s, d, l);
+    for (int k = 0; k < nv * nv; ++k) {
+      if (R && R[k]) R[k][i] = r[k];
+      if (L && L[k]) L[k][i] = l[k];
+    }
+    for (int k = 0; k < nv; ++k)
+      if (lam && lam[k]) lam[k][i] = lm[k];
+    if (aux) {
+      double p, p_rho, p_e;
+      eos_p(M, s.rho, s.e, p, p_rho, p_e);
+      const double vals[5] = {p, p_rho, p_e, eos_T(M, s.rho, s.e), s.e};
+      for (int k = 0; k < 5; ++k)
+        if (aux[k]) aux[k][i] = vals[k];
+    }
+  }
+  return 0;
+}
+
+// The EOS functions at given (rho, e) or (rho, p) pairs:
+//   out_pe = {p, p_rho, p_e, T} at (rho[i], e[i]);
+//   out_z  = {rho e, d(rho e)/drho|_p, d(rho e)/dp|_rho} at (rho[i], p[i] = e[i]).
+int oracle_eos_point(const double* eos, int64_t n, const double* rho, const double* e, double* const* out_pe,
+                     double* const* out_z) {
+  EosModel M;
+  if (n < 0 || !eos_from_params(eos, M)) return 1;
+  for (int64_t i = 0; i < n; ++i) {
+    if (out_pe) {
+      double p, p_rho, p_e;
+      eos_p(M, rho[i], e[i], p, p_rho, p_e);
+      const double v[4] = {p, p_rho, p_e, eos_T(M, rho[i], e[i])};
+      for (int k = 0; k < 4; ++k)
+        if (out_pe[k]) out_pe[k][i] = v[k];
+    }
+    if (out_z) {
+      double z, z_rho, z_p;
+      eos_rhoe(M, rho[i], e[i], z, z_rho, z_p);
+      const double v[3] = {z, z_rho, z_p};
+      for (int k = 0; k < 3; ++k)
+        if (out_z[k]) out_z[k][i] = v[k];
+    }
+  }
+  return 0;
+}
+#undef ORACLE_EOS_ARGS
 
 // Rusanov finite-volume scheme on one periodic n^3 grid (FP64).
 double oracle_rusanov_dt(int n, double g, double cfl, const double* const* U) {

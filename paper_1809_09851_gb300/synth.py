@@ -20,6 +20,10 @@ the benchmark configurations):
                     (rho, p ~ U[1e-4, 1e-3]) and 5% at Mach M ~ U[10, 50]
                     given as a Mach number and a unit direction per point
   * ``cotangent`` : G ~ N(0, 1), nv planes (upstream gradients of a VJP)
+  * ``euler_eos`` : D=1..3 under a general EOS: rho ~ U[0.2, 4], v_i ~ N(0, 1),
+                    p ~ U[0.1, 10], with the nondimensional EOS parameter sets
+                    ``EOS_NASG`` and ``EOS_VDW`` (1 - b rho >= 0.6 and c^2 > 0
+                    on the whole range)
   * ``serving``   : request stream and smooth periodic initial data for the
                     finite-volume serving loop
 """
@@ -62,6 +66,17 @@ def euler1d(n: int, seed: int = SEED):
 def euler3d(n: int, seed: int = SEED, D: int = 3):
     """3D (or 2D) Euler: rho ~ U[0.1,10], v_i ~ N(0, sd 2), p ~ U[0.1,10]."""
     return euler_primitive(n, D, (0.1, 10.0), 2.0, (0.1, 10.0), seed)
+
+
+# Nondimensional parameter sets of the general-EOS workload (section 2.2,
+# "Equations of state"): a Noble-Abel stiffened gas and a van der Waals gas.
+EOS_NASG = {"kind": "nasg", "gamma": 1.6, "p_inf": 1.0, "b": 0.1, "q": -0.3, "cv": 2.0}
+EOS_VDW = {"kind": "vdw", "gamma": 1.4, "a": 0.05, "b": 0.1, "cv": 2.5}
+
+
+def euler_eos(n: int, D: int = 3, seed: int = SEED):
+    """General-EOS states: rho ~ U[0.2, 4], v_i ~ N(0, 1), p ~ U[0.1, 10]."""
+    return euler_primitive(n, D, (0.2, 4.0), 1.0, (0.1, 10.0), seed)
 
 
 def char_weights(n: int, nv: int = 5, seed: int = SEED_W):
