@@ -189,6 +189,57 @@ def time_fused(U, W, out, steps, warmup, stream, dw=False):
     return per, total
 
 
+def time_launch(fn, steps, warmup, stream):
+    """Like time_fused, for any launch fn() enqueued on the current stream."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for i in range(steps):
+            fn()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)], ev[0].elapsed_time(ev[steps])
+
+
+def run_general_eos(args, n, W64, out64, stream, dev, world, hbm_peak):
+    """The fused 3D pass under the Noble-Abel stiffened-gas EOS (fdbb_euler_fused_eos)
+    on the general-EOS workload, FP64 and FP32 storage, same N and planes as the headline."""
+    import torch
+    from paper_1809_09851_gb300 import blocks, synth
+    eos = synth.EOS_NASG
+    V = [torch.from_numpy(v).to(dev) for v in synth.euler_eos(n, 3, seed=shard_seed(4242, dist_env()[1]))]
+    U = blocks.cons_from_prim_eos(V, eos)
+    del V
+    res = {"eos": "NASG gamma=1.6 p_inf=1 b=0.1 q=-0.3 c_v=2 (nondimensional)",
+           "workload": "rho~U[0.2,4], v~N(0,1), p~U[0.1,10]"}
+    for tag, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        if tag == "f64":
+            Ut, Wt, out = U, W64, out64
+        else:
+            Ut = [u.to(dt) for u in U]
+            Wt = [w.to(dt) for w in W64]
+            out = tuple([torch.empty(n, dtype=dt, device=dev) for _ in range(k)] for k in (D * NV, NV * NV, NV))
+        per, total = time_launch(lambda: blocks.euler_fused_eos(Ut, Wt, eos, 0, out=out), args.steps,
+                                 args.warmup, stream)
+        t = max_over_ranks(total / 1e3, world, dev)
+        avg = sum(per) / len(per) / 1e3
+        b = (PLANES_IN + PLANES_OUT) * BYTES[tag] * n
+        res[tag] = {"value": round(world * n * args.steps / t / 1e9, 3), "unit": UNIT,
+                    "ms_per_step": round(t * 1e3 / args.steps, 4), "p99_ms": round(pct(per, 99), 4),
+                    "hbm_gbs": round(b / avg / 1e9, 1), "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3),
+                    "stated_err": "|gpu - oracle| <= 1e-12 * S" if tag == "f64"
+                    else "|gpu - oracle| <= 2^-24 |o| + 64 * 2^-24 * S"}
+        if tag != "f64":
+            del Ut, Wt, out
+    del U
+    torch.cuda.empty_cache()
+    return res
+
+
 def pct(xs, q):
     xs = sorted(xs)
     k = max(0, min(len(xs) - 1, int(math.ceil(q / 100.0 * len(xs))) - 1))
@@ -280,6 +331,12 @@ def run_gpu(args):
         del U, W, out
         torch.cuda.empty_cache()
 
+    # ---- the same pass under a general equation of state -----------------------
+    general_eos = None
+    if args.only in ("all", "eos"):
+        barrier()
+        general_eos = run_general_eos(args, n, W64, out64, stream, dev, world, hbm_peak)
+
     # ---- end to end through host buffers ---------------------------------------
     e2e = None if args.no_e2e else run_e2e(args, U64, W64, out64, stream, dev, world)
     del out64
@@ -309,6 +366,7 @@ def run_gpu(args):
                          "peak_kind": peak_kind, "algorithmic_bytes_per_point": (PLANES_IN + PLANES_OUT) * 8},
             "f64_native": f64_native,
             "mixed": extra,
+            "general_eos": general_eos,
             "e2e": e2e,
             "serving": serving,
             "gpu_launches": args.steps,
@@ -511,7 +569,7 @@ def main(argv=None):
     ap.add_argument("--fv-n", type=int, default=128)
     ap.add_argument("--fv-grids", type=int, default=8)
     ap.add_argument("--fv-steps", type=int, default=20)
-    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16", "fv"], default="all",
+    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16", "eos", "fv"], default="all",
                     help="storage types to time besides the f64 headline (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -264,6 +264,93 @@ FDBB_API fdbb_status fdbb_roe_char_transform(int dim, int dir, double gamma, int
                                              void *const *Y, fdbb_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * General equations of state.
+ *
+ * The paper lets a user plug in an equation of state f(p, V, T) = 0 through a
+ * type with members p_rhoe(rho, e) and T_rhoe(rho, e) (section 2.2,
+ * "Equations of state", Fig. 10).  The entry points below evaluate the
+ * EOS-dependent blocks under such a model instead of the ideal gas:
+ *
+ *   FDBB_EOS_NASG  Noble-Abel stiffened gas (Le Metayer and Saurel 2016),
+ *                  p = (gamma - 1)(e - q) rho / (1 - b rho) - gamma p_inf,
+ *                  T = (e - q - p_inf (1/rho - b)) / c_v
+ *                  (the ideal gas for p_inf = b = q = 0; the stiffened gas for b = 0);
+ *   FDBB_EOS_VDW   van der Waals with caloric law e = c_v T - a rho,
+ *                  p = (gamma - 1)(rho e + a rho^2)/(1 - b rho) - a rho^2,
+ *                  T = (e + a rho) / c_v;
+ *   FDBB_EOS_IDEAL the ideal gas: the call runs the corresponding ideal-gas
+ *                  entry point above with gamma and cv (every storage type).
+ *
+ * With the pressure gradient dp/dU = (phi, -Gamma v, Gamma), Gamma =
+ * (1/rho) dp/de|_rho, phi = dp/drho|_e + Gamma (q - e), q = |v|^2/2, the
+ * blocks are the ideal-gas ones with these per-point values in place of
+ * gamma - 1 and (gamma - 1) q:
+ *   c^2 = dp/drho|_e + Gamma p / rho (isentropic derivative),
+ *   A_d: row 1+d = (phi - u^2, -Gamma v_j, (2 - Gamma) u, Gamma),
+ *        row nv-1 = (u (phi - H), -Gamma u v_j, H - Gamma u^2, (1 + Gamma) u),
+ *   eigenvectors as at fdbb_char_transform except the entropy wave
+ *        r_2 = (1, v, 2q - phi/Gamma), L = R^{-1},
+ *   rhoE = rho e(rho, p) + rho q in the primitive forms (whose Jacobian row
+ *        nv-1 is (u (q + d(rho e)/drho|_p), delta_jd (rhoE + p) + rho u v_j,
+ *        u (d(rho e)/dp|_rho + 1))).
+ * The kernels take the partial derivatives of p(rho, e) and rho e(rho, p)
+ * from one evaluation on dual numbers.
+ *
+ * Storage types: FDBB_F64 (IEEE double) and FDBB_F32 (float) for NASG and
+ * VDW; others return FDBB_ERR_DTYPE.  The Riemann invariants and the
+ * Roe-averaged forms have no counterpart here (no closed form for a general
+ * EOS).  Argument errors (FDBB_ERR_ARG): eos NULL, unknown kind, gamma <= 1,
+ * cv <= 0, b < 0, p_inf < 0 (NASG) or a < 0 (VDW).  States with
+ * 1 - b rho <= 0 or c^2 < 0 are not checked: they give inf or NaN.
+ * Every other convention (planes, alignment, NULL outputs, streams,
+ * ownership) is that of the ideal-gas entry point of the same block.
+ * ------------------------------------------------------------------------ */
+
+typedef enum { FDBB_EOS_IDEAL = 0, FDBB_EOS_NASG = 1, FDBB_EOS_VDW = 2 } fdbb_eos_kind;
+
+typedef struct fdbb_eos_model {
+  int32_t kind;    /* fdbb_eos_kind */
+  int32_t reserved; /* must be 0 */
+  double gamma;    /* ratio of specific heats, > 1 */
+  double p_inf;    /* NASG stiffening pressure, >= 0 */
+  double b;        /* co-volume (NASG, VDW), >= 0 */
+  double q;        /* NASG reference energy */
+  double a;        /* VDW attraction, >= 0 */
+  double cv;       /* specific heat at constant volume (temperature), > 0 */
+} fdbb_eos_model;
+
+/* Blocks under a general EOS: arguments as the ideal-gas entry point of the
+ * same name without the suffix (gamma and cv come from the model). */
+FDBB_API fdbb_status fdbb_prim_from_cons_eos(const fdbb_eos_model *eos, int dim, int64_t n, fdbb_dtype t,
+                                             const void *const *U, void *const *V, fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_cons_from_prim_eos(const fdbb_eos_model *eos, int dim, int64_t n, fdbb_dtype t,
+                                             const void *const *V, void *const *U, fdbb_stream_t stream);
+/* p and c (the block fdbb_eos computes for the ideal gas). */
+FDBB_API fdbb_status fdbb_pressure_eos(const fdbb_eos_model *eos, int dim, int64_t n, fdbb_dtype t,
+                                       const void *const *U, void *p, void *c, fdbb_stream_t stream);
+/* T = T_rhoe(rho, e) of the model. */
+FDBB_API fdbb_status fdbb_temperature_eos(const fdbb_eos_model *eos, int dim, int64_t n, fdbb_dtype t,
+                                          const void *const *U, void *T, fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_flux_eos(const fdbb_eos_model *eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                                   const void *const *U, void *const *F, fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_flux_jac_eos(const fdbb_eos_model *eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                                       const void *const *U, void *const *A, fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_char_transform_eos(const fdbb_eos_model *eos, int dim, int dir, int64_t n,
+                                             fdbb_dtype t, int inverse, const void *const *U,
+                                             const void *const *W, void *const *Y, fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_euler_fused_eos(const fdbb_eos_model *eos, int dim, int dir_jac, int64_t n,
+                                          fdbb_dtype t, const void *const *U, const void *const *W,
+                                          void *const *F, void *const *A, void *const *Y, fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_flux_vjp_eos(const fdbb_eos_model *eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                                       const void *const *U, const void *const *G, void *const *gU,
+                                       fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_flux_prim_eos(const fdbb_eos_model *eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                                        const void *const *V, void *const *F, fdbb_stream_t stream);
+FDBB_API fdbb_status fdbb_flux_jac_prim_eos(const fdbb_eos_model *eos, int dim, int dir, int64_t n,
+                                            fdbb_dtype t, const void *const *V, void *const *B,
+                                            fdbb_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Batched finite-volume steps (the serving workload).
  *
  * An explicit first-order finite-volume scheme with the Rusanov (local

@@ -14,6 +14,7 @@ outside its range.
 """
 from __future__ import annotations
 
+import ctypes
 from typing import Optional, Sequence
 
 import torch
@@ -301,3 +302,125 @@ def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: i
     for s in (s_h2d, s_cmp, s_d2h):
         cur.wait_stream(s)
     return work
+
+
+# ---------------------------------------------------------------------------
+# General equations of state (fdbb_*_eos).  ``eos`` is a dict
+# {"kind": "ideal" | "nasg" | "vdw", "gamma", "p_inf", "b", "q", "a", "cv"}
+# (missing parameters 0, cv 1) or a capi.EosModel.  NASG and VDW take float64
+# or float32 planes; "ideal" runs the ideal-gas kernels (any dtype).
+# ---------------------------------------------------------------------------
+
+def _eos_ref(eos):
+    m = capi.eos_model(eos)
+    return m, ctypes.byref(m)
+
+
+def prim_from_cons_eos(U, eos, out=None, stream=None):
+    D = _dim(U)
+    n, dt, dev = _info(U)
+    V = out if out is not None else _alloc(D + 2, n, dt, dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_prim_from_cons_eos", pm, D, n, DTYPES[dt], _ptrs(U), _ptrs(V), _stream(dev, stream))
+    return V
+
+
+def cons_from_prim_eos(V, eos, out=None, stream=None):
+    D = _dim(V)
+    n, dt, dev = _info(V)
+    U = out if out is not None else _alloc(D + 2, n, dt, dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_cons_from_prim_eos", pm, D, n, DTYPES[dt], _ptrs(V), _ptrs(U), _stream(dev, stream))
+    return U
+
+
+def pressure_eos(U, eos, want_p: bool = True, want_c: bool = True, stream=None):
+    """(p, c) under the EOS; an output not wanted is None."""
+    D = _dim(U)
+    n, dt, dev = _info(U)
+    p = torch.empty(n, dtype=dt, device=dev) if want_p else None
+    c = torch.empty(n, dtype=dt, device=dev) if want_c else None
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_pressure_eos", pm, D, n, DTYPES[dt], _ptrs(U), p.data_ptr() if p is not None else None,
+              c.data_ptr() if c is not None else None, _stream(dev, stream))
+    return p, c
+
+
+def temperature_eos(U, eos, out=None, stream=None):
+    D = _dim(U)
+    n, dt, dev = _info(U)
+    T = out if out is not None else torch.empty(n, dtype=dt, device=dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_temperature_eos", pm, D, n, DTYPES[dt], _ptrs(U), T.data_ptr(), _stream(dev, stream))
+    return T
+
+
+def flux_eos(U, eos, dir: int = -1, out=None, stream=None):
+    D = _dim(U)
+    n, dt, dev = _info(U)
+    F = out if out is not None else _alloc((D + 2) * (D if dir < 0 else 1), n, dt, dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_flux_eos", pm, D, dir, n, DTYPES[dt], _ptrs(U), _ptrs(F), _stream(dev, stream))
+    return F
+
+
+def flux_jac_eos(U, eos, dir: int, out=None, stream=None):
+    D = _dim(U)
+    n, dt, dev = _info(U)
+    A = out if out is not None else _alloc((D + 2) ** 2, n, dt, dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_flux_jac_eos", pm, D, dir, n, DTYPES[dt], _ptrs(U), _ptrs(A), _stream(dev, stream))
+    return A
+
+
+def char_transform_eos(U, W, eos, dir: int, inverse: bool = False, out=None, stream=None):
+    D = _dim(U)
+    n, dt, dev = _info(list(U) + list(W))
+    Y = out if out is not None else _alloc(D + 2, n, dt, dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_char_transform_eos", pm, D, dir, n, DTYPES[dt], int(bool(inverse)), _ptrs(U), _ptrs(W),
+              _ptrs(Y), _stream(dev, stream))
+    return Y
+
+
+def euler_fused_eos(U, W, eos, dir_jac: int = 0, out=None, stream=None):
+    D = _dim(U)
+    nv = D + 2
+    n, dt, dev = _info(list(U) + (list(W) if W is not None else []))
+    if out is None:
+        out = (_alloc(D * nv, n, dt, dev), _alloc(nv * nv, n, dt, dev),
+               _alloc(nv, n, dt, dev) if W is not None else None)
+    F, A, Y = out
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_euler_fused_eos", pm, D, dir_jac, n, DTYPES[dt], _ptrs(U),
+              _ptrs(W) if W is not None else None,
+              _ptrs(F) if F is not None else None, _ptrs(A) if A is not None else None,
+              _ptrs(Y) if Y is not None else None, _stream(dev, stream))
+    return F, A, Y
+
+
+def flux_vjp_eos(U, G, eos, dir: int, out=None, stream=None):
+    D = _dim(U)
+    n, dt, dev = _info(list(U) + list(G))
+    gU = out if out is not None else _alloc(D + 2, n, dt, dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_flux_vjp_eos", pm, D, dir, n, DTYPES[dt], _ptrs(U), _ptrs(G), _ptrs(gU), _stream(dev, stream))
+    return gU
+
+
+def flux_prim_eos(V, eos, dir: int = -1, out=None, stream=None):
+    D = _dim(V)
+    n, dt, dev = _info(V)
+    F = out if out is not None else _alloc((D + 2) * (D if dir < 0 else 1), n, dt, dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_flux_prim_eos", pm, D, dir, n, DTYPES[dt], _ptrs(V), _ptrs(F), _stream(dev, stream))
+    return F
+
+
+def flux_jac_prim_eos(V, eos, dir: int, out=None, stream=None):
+    D = _dim(V)
+    n, dt, dev = _info(V)
+    B = out if out is not None else _alloc((D + 2) ** 2, n, dt, dev)
+    m, pm = _eos_ref(eos)
+    capi.call("fdbb_flux_jac_prim_eos", pm, D, dir, n, DTYPES[dt], _ptrs(V), _ptrs(B), _stream(dev, stream))
+    return B

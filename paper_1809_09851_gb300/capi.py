@@ -59,6 +59,44 @@ SIGNATURES.update({
     "fdbb_fv_rusanov_step_noalloc": [_i, _FVP, _i64, _d, _d, _i, _vp],
 })
 
+
+
+class EosModel(ctypes.Structure):
+    """struct fdbb_eos_model (include/fdbb.h)."""
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("p_inf", ctypes.c_double), ("b", ctypes.c_double), ("q", ctypes.c_double),
+                ("a", ctypes.c_double), ("cv", ctypes.c_double)]
+
+
+FDBB_EOS_IDEAL, FDBB_EOS_NASG, FDBB_EOS_VDW = 0, 1, 2
+EOS_KINDS = {"ideal": FDBB_EOS_IDEAL, "nasg": FDBB_EOS_NASG, "vdw": FDBB_EOS_VDW}
+
+
+def eos_model(eos) -> EosModel:
+    """EosModel from a dict {"kind": "ideal"|"nasg"|"vdw", "gamma", "p_inf", "b",
+    "q", "a", "cv"} (missing parameters 0, cv 1) or an EosModel."""
+    if isinstance(eos, EosModel):
+        return eos
+    return EosModel(EOS_KINDS[eos["kind"]], 0, float(eos["gamma"]), float(eos.get("p_inf", 0.0)),
+                    float(eos.get("b", 0.0)), float(eos.get("q", 0.0)), float(eos.get("a", 0.0)),
+                    float(eos.get("cv", 1.0)))
+
+
+_EP = ctypes.POINTER(EosModel)
+SIGNATURES.update({
+    "fdbb_prim_from_cons_eos": [_EP, _i, _i64, _i, _PP, _PP, _vp],
+    "fdbb_cons_from_prim_eos": [_EP, _i, _i64, _i, _PP, _PP, _vp],
+    "fdbb_pressure_eos": [_EP, _i, _i64, _i, _PP, _vp, _vp, _vp],
+    "fdbb_temperature_eos": [_EP, _i, _i64, _i, _PP, _vp, _vp],
+    "fdbb_flux_eos": [_EP, _i, _i, _i64, _i, _PP, _PP, _vp],
+    "fdbb_flux_jac_eos": [_EP, _i, _i, _i64, _i, _PP, _PP, _vp],
+    "fdbb_char_transform_eos": [_EP, _i, _i, _i64, _i, _i, _PP, _PP, _PP, _vp],
+    "fdbb_euler_fused_eos": [_EP, _i, _i, _i64, _i, _PP, _PP, _PP, _PP, _PP, _vp],
+    "fdbb_flux_vjp_eos": [_EP, _i, _i, _i64, _i, _PP, _PP, _PP, _vp],
+    "fdbb_flux_prim_eos": [_EP, _i, _i, _i64, _i, _PP, _PP, _vp],
+    "fdbb_flux_jac_prim_eos": [_EP, _i, _i, _i64, _i, _PP, _PP, _vp],
+})
+
 _lib = None
 
 

@@ -93,27 +93,141 @@ KArgs make_args(int64_t n, double gamma, double cv = 0.0) {
   return a;
 }
 
-fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, KArgs& a, fdbb_stream_t stream) {
+// General EOS parameters into the kernel's EOS slots (double, and rounded
+// once to float).  The model has been validated.
+void set_eos_args(KArgs& a, const fdbb_eos_model& m) {
+  const double a1 = m.gamma - 1.0;
+  const double ke[8] = {a1, 1.0 / a1, m.b, 1.0 / m.cv, m.p_inf, m.q, m.gamma * m.p_inf, m.a};
+  for (int i = 0; i < 8; ++i) {
+    a.ke[i] = ke[i];
+    a.kef[i] = static_cast<float>(ke[i]);
+  }
+}
+
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+fdbb_status check_eos(const fdbb_eos_model* m) {
+  if (m == nullptr) return FDBB_ERR_ARG;
+  if (m->kind != FDBB_EOS_IDEAL && m->kind != FDBB_EOS_NASG && m->kind != FDBB_EOS_VDW) return FDBB_ERR_ARG;
+  if (m->reserved != 0) return FDBB_ERR_ARG;
+  if (!(m->gamma > 1.0) || !std::isfinite(m->gamma)) return FDBB_ERR_ARG;
+  if (!(m->cv > 0.0) || !std::isfinite(m->cv)) return FDBB_ERR_ARG;
+  if (!finite_nonneg(m->b) || !std::isfinite(m->q)) return FDBB_ERR_ARG;
+  if (m->kind == FDBB_EOS_NASG && !finite_nonneg(m->p_inf)) return FDBB_ERR_ARG;
+  if (m->kind == FDBB_EOS_VDW && !finite_nonneg(m->a)) return FDBB_ERR_ARG;
+  return FDBB_OK;
+}
+
+// Launch op for storage type t under the equation of state `eos`.
+fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, KArgs& a, fdbb_stream_t stream,
+                   fdbb::EosKind eos = fdbb::EosKind::Ideal) {
   if (a.n == 0) return FDBB_OK;
   a.nin = 0;
   while (a.nin < fdbb::kMaxIn && a.in[a.nin] != nullptr) ++a.nin;
-  const LaunchReq r{op, dim, dir, reinterpret_cast<cudaStream_t>(stream)};
+  LaunchReq r{op, dim, dir, reinterpret_cast<cudaStream_t>(stream)};
+  r.eos = eos;
   cudaError_t e = cudaErrorInvalidValue;
-  switch (t) {
-    case FDBB_F64: e = fdbb::dispatch_f64(r, a); break;
-    case FDBB_F32: e = fdbb::dispatch_f32(r, a); break;
-    case FDBB_F16: e = fdbb::dispatch_f16(r, a); break;
-    case FDBB_BF16: e = fdbb::dispatch_bf16(r, a); break;
-    case FDBB_F64_DW: e = fdbb::dispatch_f64dw(r, a); break;
+  if (eos != fdbb::EosKind::Ideal) {
+    switch (t) {
+      case FDBB_F64: e = fdbb::dispatch_eos_f64(r, a); break;
+      case FDBB_F32: e = fdbb::dispatch_eos_f32(r, a); break;
+      default: return FDBB_ERR_DTYPE;
+    }
+  } else {
+    switch (t) {
+      case FDBB_F64: e = fdbb::dispatch_f64(r, a); break;
+      case FDBB_F32: e = fdbb::dispatch_f32(r, a); break;
+      case FDBB_F16: e = fdbb::dispatch_f16(r, a); break;
+      case FDBB_BF16: e = fdbb::dispatch_bf16(r, a); break;
+      case FDBB_F64_DW: e = fdbb::dispatch_f64dw(r, a); break;
+    }
   }
   return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
 }
+
 
 #define FDBB_TRY(expr)                   \
   do {                                   \
     const fdbb_status s_ = (expr);       \
     if (s_ != FDBB_OK) return s_;        \
   } while (0)
+
+// Plane bookkeeping of each block, shared by the ideal-gas and general-EOS
+// entry points: fills a.in / a.out from the caller's plane arrays.
+fdbb_status fill_prim(KArgs& a, int dim, const void* const* U, void* const* V) {
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_out(a, 0, V, nv, false));
+  if (a.out[0] == a.in[0]) a.out[0] = nullptr;  // rho onto itself: no copy
+  return FDBB_OK;
+}
+
+fdbb_status fill_pc(KArgs& a, int dim, const void* const* U, void* p, void* c) {
+  FDBB_TRY(take_in(a, 0, U, dim + 2));
+  FDBB_TRY(take_out1(a, 0, p));
+  return take_out1(a, 1, c);
+}
+
+fdbb_status fill_flux(KArgs& a, int dim, int dir, const void* const* U, void* const* F) {
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  return take_out(a, 0, F, dir < 0 ? dim * nv : nv, false);
+}
+
+fdbb_status fill_jac(KArgs& a, int dim, const void* const* U, void* const* A) {
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  return take_out(a, 0, A, nv * nv, false);
+}
+
+// Two nv-plane inputs (U and W, G or U_R), one nv-plane output.
+fdbb_status fill_two(KArgs& a, int dim, const void* const* U, const void* const* W, void* const* Y) {
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_in(a, nv, W, nv));
+  return take_out(a, 0, Y, nv, false);
+}
+
+fdbb_status fill_fused(KArgs& a, int dim, const void* const* U, const void* const* W, void* const* F,
+                       void* const* A, void* const* Y) {
+  const int nv = dim + 2;
+  FDBB_TRY(take_in(a, 0, U, nv));
+  FDBB_TRY(take_out(a, 0, F, dim * nv, true));
+  FDBB_TRY(take_out(a, dim * nv, A, nv * nv, true));
+  FDBB_TRY(take_out(a, dim * nv + nv * nv, Y, nv, true));
+  bool want_y = false;
+  for (int i = 0; i < nv; ++i) want_y = want_y || a.out[dim * nv + nv * nv + i] != nullptr;
+  // W is read only when Y is wanted; otherwise in[nv] stays NULL.
+  if (want_y) FDBB_TRY(take_in(a, nv, W, nv));
+  return FDBB_OK;
+}
+
+fdbb_status fill_temp(KArgs& a, int dim, const void* const* U, void* T) {
+  FDBB_TRY(take_in(a, 0, U, dim + 2));
+  if (T == nullptr) return FDBB_ERR_NULLPTR;
+  return take_out1(a, 0, T);
+}
+
+bool dir_ok(int dim, int dir, bool all_allowed) { return dir >= (all_allowed ? -1 : 0) && dir < dim; }
+
+// Common checks and parameter block of a general-EOS entry point.  Sets
+// `ideal` when the model is the ideal gas (the caller then forwards to the
+// ideal-gas entry point, which checks the rest).
+fdbb_status eos_prologue(const fdbb_eos_model* eos, int dim, int64_t n, fdbb_dtype t, KArgs& a, bool& ideal) {
+  FDBB_TRY(check_dims(dim, n));
+  FDBB_TRY(check_eos(eos));
+  FDBB_TRY(check_dtype(t));
+  ideal = eos->kind == FDBB_EOS_IDEAL;
+  if (ideal) return FDBB_OK;
+  if (t != FDBB_F64 && t != FDBB_F32) return FDBB_ERR_DTYPE;
+  a = make_args(n, eos->gamma, eos->cv);
+  set_eos_args(a, *eos);
+  return FDBB_OK;
+}
+
+fdbb::EosKind eos_kind(const fdbb_eos_model* eos) {
+  return eos->kind == FDBB_EOS_NASG ? fdbb::EosKind::Nasg : fdbb::EosKind::Vdw;
+}
 
 }  // namespace
 
@@ -122,10 +236,10 @@ extern "C" {
 const char* fdbb_status_string(fdbb_status s) {
   switch (s) {
     case FDBB_OK: return "ok";
-    case FDBB_ERR_ARG: return "invalid argument (dim, dir, n or gamma)";
+    case FDBB_ERR_ARG: return "invalid argument (dim, dir, n, gamma or EOS model)";
     case FDBB_ERR_NULLPTR: return "required plane pointer is NULL";
     case FDBB_ERR_ALIGN: return "plane pointer is not 16-byte aligned";
-    case FDBB_ERR_DTYPE: return "unknown storage type";
+    case FDBB_ERR_DTYPE: return "unknown storage type, or one the block does not support";
     case FDBB_ERR_CUDA: return "CUDA launch failed";
     case FDBB_ERR_TIMEOUT: return "timed out waiting for the device";
     case FDBB_ERR_NOMEM: return "buffer or memory budget too small";
@@ -137,7 +251,8 @@ int fdbb_version(void) { return 100; }
 
 fdbb_status fdbb_device_status(void) {
   const unsigned int n = fdbb::wait_timeouts_f64() + fdbb::wait_timeouts_f32() + fdbb::wait_timeouts_f16() +
-                         fdbb::wait_timeouts_bf16() + fdbb::wait_timeouts_f64dw();
+                         fdbb::wait_timeouts_bf16() + fdbb::wait_timeouts_f64dw() +
+                         fdbb::wait_timeouts_eos_f64() + fdbb::wait_timeouts_eos_f32();
   return n ? FDBB_ERR_TIMEOUT : FDBB_OK;
 }
 
@@ -157,10 +272,7 @@ fdbb_status fdbb_prim_from_cons(int dim, double gamma, int64_t n, fdbb_dtype t, 
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, U, nv));
-  FDBB_TRY(take_out(a, 0, V, nv, false));
-  if (a.out[0] == a.in[0]) a.out[0] = nullptr;  // rho onto itself: no copy
+  FDBB_TRY(fill_prim(a, dim, U, V));
   return launch(t, OpKind::Prim, dim, 0, a, stream);
 }
 
@@ -170,10 +282,7 @@ fdbb_status fdbb_cons_from_prim(int dim, double gamma, int64_t n, fdbb_dtype t, 
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, V, nv));
-  FDBB_TRY(take_out(a, 0, U, nv, false));
-  if (a.out[0] == a.in[0]) a.out[0] = nullptr;
+  FDBB_TRY(fill_prim(a, dim, V, U));
   return launch(t, OpKind::Cons, dim, 0, a, stream);
 }
 
@@ -183,9 +292,7 @@ fdbb_status fdbb_eos(int dim, double gamma, int64_t n, fdbb_dtype t, const void*
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  FDBB_TRY(take_in(a, 0, U, dim + 2));
-  FDBB_TRY(take_out1(a, 0, p));
-  FDBB_TRY(take_out1(a, 1, c));
+  FDBB_TRY(fill_pc(a, dim, U, p, c));
   if (p == nullptr && c == nullptr) return FDBB_OK;
   return launch(t, OpKind::Eos, dim, 0, a, stream);
 }
@@ -193,7 +300,7 @@ fdbb_status fdbb_eos(int dim, double gamma, int64_t n, fdbb_dtype t, const void*
 fdbb_status fdbb_riemann_inv(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
                              void* wm, void* wp, void* s, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
@@ -208,26 +315,22 @@ fdbb_status fdbb_riemann_inv(int dim, int dir, double gamma, int64_t n, fdbb_dty
 fdbb_status fdbb_flux(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
                       void* const* F, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < -1 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, true)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, U, nv));
-  FDBB_TRY(take_out(a, 0, F, dir < 0 ? dim * nv : nv, false));
+  FDBB_TRY(fill_flux(a, dim, dir, U, F));
   return launch(t, dir < 0 ? OpKind::FluxAll : OpKind::Flux, dim, dir, a, stream);
 }
 
 fdbb_status fdbb_flux_jac(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
                           void* const* A, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, U, nv));
-  FDBB_TRY(take_out(a, 0, A, nv * nv, false));
+  FDBB_TRY(fill_jac(a, dim, U, A));
   return launch(t, OpKind::Jac, dim, dir, a, stream);
 }
 
@@ -235,14 +338,11 @@ fdbb_status fdbb_char_transform(int dim, int dir, double gamma, int64_t n, fdbb_
                                 const void* const* U, const void* const* W, void* const* Y,
                                 fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, U, nv));
-  FDBB_TRY(take_in(a, nv, W, nv));
-  FDBB_TRY(take_out(a, 0, Y, nv, false));
+  FDBB_TRY(fill_two(a, dim, U, W, Y));
   return launch(t, inverse ? OpKind::CharInv : OpKind::CharFwd, dim, dir, a, stream);
 }
 
@@ -250,48 +350,33 @@ fdbb_status fdbb_euler_fused(int dim, int dir_jac, double gamma, int64_t n, fdbb
                              const void* const* W, void* const* F, void* const* A, void* const* Y,
                              fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir_jac < 0 || dir_jac >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir_jac, false)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, U, nv));
-  FDBB_TRY(take_out(a, 0, F, dim * nv, true));
-  FDBB_TRY(take_out(a, dim * nv, A, nv * nv, true));
-  FDBB_TRY(take_out(a, dim * nv + nv * nv, Y, nv, true));
-  bool want_y = false;
-  for (int i = 0; i < nv; ++i) want_y = want_y || a.out[dim * nv + nv * nv + i] != nullptr;
-  if (want_y) {
-    FDBB_TRY(take_in(a, nv, W, nv));
-  } else if (W != nullptr) {
-    // W is not needed: leave in[nv] NULL so the kernel does not read it.
-  }
+  FDBB_TRY(fill_fused(a, dim, U, W, F, A, Y));
   return launch(t, OpKind::Fused, dim, dir_jac, a, stream);
 }
 
 fdbb_status fdbb_flux_prim(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* V,
                            void* const* F, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < -1 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, true)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, V, nv));
-  FDBB_TRY(take_out(a, 0, F, dir < 0 ? dim * nv : nv, false));
+  FDBB_TRY(fill_flux(a, dim, dir, V, F));
   return launch(t, dir < 0 ? OpKind::FluxPrimAll : OpKind::FluxPrim, dim, dir, a, stream);
 }
 
 fdbb_status fdbb_flux_jac_prim(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* V,
                                void* const* B, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, V, nv));
-  FDBB_TRY(take_out(a, 0, B, nv * nv, false));
+  FDBB_TRY(fill_jac(a, dim, V, B));
   return launch(t, OpKind::JacPrim, dim, dir, a, stream);
 }
 
@@ -302,23 +387,18 @@ fdbb_status fdbb_temperature(int dim, double gamma, double cv, int64_t n, fdbb_d
   if (!(cv > 0.0) || !std::isfinite(cv)) return FDBB_ERR_ARG;
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma, cv);
-  FDBB_TRY(take_in(a, 0, U, dim + 2));
-  if (T == nullptr) return FDBB_ERR_NULLPTR;
-  FDBB_TRY(take_out1(a, 0, T));
+  FDBB_TRY(fill_temp(a, dim, U, T));
   return launch(t, OpKind::Temp, dim, 0, a, stream);
 }
 
 fdbb_status fdbb_roe_flux(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* UL,
                           const void* const* UR, void* const* F, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, UL, nv));
-  FDBB_TRY(take_in(a, nv, UR, nv));
-  FDBB_TRY(take_out(a, 0, F, nv, false));
+  FDBB_TRY(fill_two(a, dim, UL, UR, F));
   return launch(t, OpKind::RoeFlux, dim, dir, a, stream);
 }
 
@@ -326,7 +406,7 @@ fdbb_status fdbb_roe_char_transform(int dim, int dir, double gamma, int64_t n, f
                                     const void* const* UL, const void* const* UR, const void* const* W,
                                     void* const* Y, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
@@ -341,15 +421,136 @@ fdbb_status fdbb_roe_char_transform(int dim, int dir, double gamma, int64_t n, f
 fdbb_status fdbb_flux_vjp(int dim, int dir, double gamma, int64_t n, fdbb_dtype t, const void* const* U,
                           const void* const* G, void* const* gU, fdbb_stream_t stream) {
   FDBB_TRY(check_dims(dim, n));
-  if (dir < 0 || dir >= dim) return FDBB_ERR_ARG;
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
   FDBB_TRY(check_gamma(gamma));
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
-  const int nv = dim + 2;
-  FDBB_TRY(take_in(a, 0, U, nv));
-  FDBB_TRY(take_in(a, nv, G, nv));
-  FDBB_TRY(take_out(a, 0, gU, nv, false));
+  FDBB_TRY(fill_two(a, dim, U, G, gU));
   return launch(t, OpKind::Vjp, dim, dir, a, stream);
+}
+
+// ---------------------------------------------------------------------------
+// General equations of state
+// ---------------------------------------------------------------------------
+
+fdbb_status fdbb_prim_from_cons_eos(const fdbb_eos_model* eos, int dim, int64_t n, fdbb_dtype t,
+                                    const void* const* U, void* const* V, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (ideal) return fdbb_prim_from_cons(dim, eos->gamma, n, t, U, V, stream);
+  FDBB_TRY(fill_prim(a, dim, U, V));
+  return launch(t, OpKind::Prim, dim, 0, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_cons_from_prim_eos(const fdbb_eos_model* eos, int dim, int64_t n, fdbb_dtype t,
+                                    const void* const* V, void* const* U, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (ideal) return fdbb_cons_from_prim(dim, eos->gamma, n, t, V, U, stream);
+  FDBB_TRY(fill_prim(a, dim, V, U));
+  return launch(t, OpKind::Cons, dim, 0, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_pressure_eos(const fdbb_eos_model* eos, int dim, int64_t n, fdbb_dtype t, const void* const* U,
+                              void* p, void* c, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (ideal) return fdbb_eos(dim, eos->gamma, n, t, U, p, c, stream);
+  FDBB_TRY(fill_pc(a, dim, U, p, c));
+  if (p == nullptr && c == nullptr) return FDBB_OK;
+  return launch(t, OpKind::Eos, dim, 0, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_temperature_eos(const fdbb_eos_model* eos, int dim, int64_t n, fdbb_dtype t,
+                                 const void* const* U, void* T, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (ideal) return fdbb_temperature(dim, eos->gamma, eos->cv, n, t, U, T, stream);
+  FDBB_TRY(fill_temp(a, dim, U, T));
+  return launch(t, OpKind::Temp, dim, 0, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_flux_eos(const fdbb_eos_model* eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                          const void* const* U, void* const* F, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (!dir_ok(dim, dir, true)) return FDBB_ERR_ARG;
+  if (ideal) return fdbb_flux(dim, dir, eos->gamma, n, t, U, F, stream);
+  FDBB_TRY(fill_flux(a, dim, dir, U, F));
+  return launch(t, dir < 0 ? OpKind::FluxAll : OpKind::Flux, dim, dir, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_flux_jac_eos(const fdbb_eos_model* eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                              const void* const* U, void* const* A, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
+  if (ideal) return fdbb_flux_jac(dim, dir, eos->gamma, n, t, U, A, stream);
+  FDBB_TRY(fill_jac(a, dim, U, A));
+  return launch(t, OpKind::Jac, dim, dir, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_char_transform_eos(const fdbb_eos_model* eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                                    int inverse, const void* const* U, const void* const* W, void* const* Y,
+                                    fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
+  if (ideal) return fdbb_char_transform(dim, dir, eos->gamma, n, t, inverse, U, W, Y, stream);
+  FDBB_TRY(fill_two(a, dim, U, W, Y));
+  return launch(t, inverse ? OpKind::CharInv : OpKind::CharFwd, dim, dir, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_euler_fused_eos(const fdbb_eos_model* eos, int dim, int dir_jac, int64_t n, fdbb_dtype t,
+                                 const void* const* U, const void* const* W, void* const* F, void* const* A,
+                                 void* const* Y, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (!dir_ok(dim, dir_jac, false)) return FDBB_ERR_ARG;
+  if (ideal) return fdbb_euler_fused(dim, dir_jac, eos->gamma, n, t, U, W, F, A, Y, stream);
+  FDBB_TRY(fill_fused(a, dim, U, W, F, A, Y));
+  return launch(t, OpKind::Fused, dim, dir_jac, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_flux_vjp_eos(const fdbb_eos_model* eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                              const void* const* U, const void* const* G, void* const* gU, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
+  if (ideal) return fdbb_flux_vjp(dim, dir, eos->gamma, n, t, U, G, gU, stream);
+  FDBB_TRY(fill_two(a, dim, U, G, gU));
+  return launch(t, OpKind::Vjp, dim, dir, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_flux_prim_eos(const fdbb_eos_model* eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                               const void* const* V, void* const* F, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (!dir_ok(dim, dir, true)) return FDBB_ERR_ARG;
+  if (ideal) return fdbb_flux_prim(dim, dir, eos->gamma, n, t, V, F, stream);
+  FDBB_TRY(fill_flux(a, dim, dir, V, F));
+  return launch(t, dir < 0 ? OpKind::FluxPrimAll : OpKind::FluxPrim, dim, dir, a, stream, eos_kind(eos));
+}
+
+fdbb_status fdbb_flux_jac_prim_eos(const fdbb_eos_model* eos, int dim, int dir, int64_t n, fdbb_dtype t,
+                                   const void* const* V, void* const* B, fdbb_stream_t stream) {
+  KArgs a = {};
+  bool ideal = false;
+  FDBB_TRY(eos_prologue(eos, dim, n, t, a, ideal));
+  if (!dir_ok(dim, dir, false)) return FDBB_ERR_ARG;
+  if (ideal) return fdbb_flux_jac_prim(dim, dir, eos->gamma, n, t, V, B, stream);
+  FDBB_TRY(fill_jac(a, dim, V, B));
+  return launch(t, OpKind::JacPrim, dim, dir, a, stream, eos_kind(eos));
 }
 
 }  // extern "C"

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "fdbb_dw.cuh"
+#include "fdbb_eos.cuh"
 
 namespace fdbb {
 
@@ -230,8 +231,11 @@ __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
 __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
 
-// Constants derived from gamma on the host in double, rounded once to R.
+// Constants derived from gamma on the host in double, rounded once to R: the
+// ideal-gas model of the per-point formulas (general EOS models, whose
+// kIdeal is false, live in fdbb_eos.cuh).
 template <class R> struct Consts {
+  static constexpr bool kIdeal = true;
   R g;      // gamma
   R a1;     // gamma - 1
   R g3;     // 3 - gamma
@@ -263,7 +267,28 @@ template <class R, int D> struct Pt {
   R p;              // pressure
   R H;              // total specific enthalpy (rhoE + p) / rho
   R c2;             // squared speed of sound gamma p / rho
+  // General EOS only (the ideal-gas formulas use constants instead):
+  R G;              // Grueneisen coefficient (1/rho) dp/de|_rho   (ideal: gamma - 1)
+  R ph;             // dp/drho at constant m, rhoE                  (ideal: (gamma - 1) q)
+  R ie;             // specific internal energy e
+  R zr, zp;         // d(rho e)/drho|_p and d(rho e)/dp|_rho of the inverse rho e(rho, p)
 };
+
+// EOS-dependent coefficients of the Euler algebra: constants of the ideal
+// gas, per-point values of a general EOS.
+//   Gamma = (1/rho) dp/de, phi = dp/drho|_(m, rhoE) = dp/drho|_e + Gamma (q - e)
+template <class R, int D, class K> __device__ __forceinline__ R eos_G(const Pt<R, D>& s, const K& k) {
+  if constexpr (K::kIdeal) return k.a1; else return s.G;
+}
+template <class R, int D, class K> __device__ __forceinline__ R eos_phi(const Pt<R, D>& s, const K& k) {
+  if constexpr (K::kIdeal) return k.a1 * s.q; else return s.ph;
+}
+template <class R, int D, class K> __device__ __forceinline__ R eos_1pG(const Pt<R, D>& s, const K& k) {
+  if constexpr (K::kIdeal) return k.g; else return R(1) + s.G;  // 1 + Gamma
+}
+template <class R, int D, class K> __device__ __forceinline__ R eos_2mG(const Pt<R, D>& s, const K& k) {
+  if constexpr (K::kIdeal) return k.g3; else return R(2) - s.G;  // 2 - Gamma
+}
 
 // Error-free transforms (Knuth TwoSum, FMA-based TwoProduct), written with
 // round-to-nearest intrinsics so that no contraction or reassociation applies.
@@ -317,17 +342,32 @@ __device__ __forceinline__ void internal_energy(Pt<float, D>& s, float& rhoe) {
 // Conservative -> derived state.  One reciprocal per point.  The guard sees
 // every derived quantity that later enters a product (1/rho is covered by
 // rho, 1/c and (gamma-1)/c^2 by c^2).
-template <class R, int D, class G>
-__device__ __forceinline__ void derive(Pt<R, D>& s, const Consts<R>& k, G& g) {
+//
+// A general EOS evaluates p(rho, e) once on dual numbers, which also gives
+// dp/drho|_e and dp/de|_rho; then Gamma = (1/rho) dp/de,
+// c^2 = dp/drho|_e + Gamma p / rho (the isentropic derivative, de = p/rho^2 drho)
+// and phi = dp/drho|_e + Gamma (q - e).
+template <class R, int D, class K, class G>
+__device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
   s.r = rcp_(s.rho);
 #pragma unroll
   for (int i = 0; i < D; ++i) s.v[i] = s.m[i] * s.r;
   R rhoe;
   internal_energy(s, rhoe);
   s.q = s.rq * s.r;
-  s.p = k.a1 * rhoe;
-  s.H = (s.rE + s.p) * s.r;
-  s.c2 = k.g * s.p * s.r;
+  if constexpr (K::kIdeal) {
+    s.p = k.a1 * rhoe;
+    s.H = (s.rE + s.p) * s.r;
+    s.c2 = k.g * s.p * s.r;
+  } else {
+    s.ie = rhoe * s.r;
+    const D2<R> P = k.p_rhoe(arg1(s.rho), arg2(s.ie));
+    s.p = P.v;
+    s.G = P.de * s.r;
+    s.H = (s.rE + s.p) * s.r;
+    s.c2 = fma_(s.G * s.p, s.r, P.dr);
+    s.ph = fma_(s.G, s.q - s.ie, P.dr);
+  }
 #pragma unroll
   for (int i = 0; i < D; ++i) g.check(s.v[i]);
   g.check(s.q);
@@ -349,17 +389,18 @@ __device__ __forceinline__ R flux_comp(const Pt<R, D>& s, int k) {
   return (i == d) ? fma_(s.m[d], s.v[d], s.p) : s.m[d] * s.v[i];
 }
 
-// Jacobian entry A_d[row][col] (row-major), u = v_d, phi = (gamma-1) q.
-template <int D, int d, class R>
-__device__ __forceinline__ R jac_entry(const Pt<R, D>& s, const Consts<R>& k, int row, int col) {
+// Jacobian entry A_d[row][col] (row-major), u = v_d, with dp/dU =
+// (phi, -Gamma v, Gamma) (ideal gas: phi = (gamma-1) q, Gamma = gamma - 1).
+template <int D, int d, class R, class K>
+__device__ __forceinline__ R jac_entry(const Pt<R, D>& s, const K& k, int row, int col) {
   constexpr int nv = D + 2;
   const R u = s.v[d];
   if (row == 0) return (col == 1 + d) ? R(1) : R(0);
   if (row == nv - 1) {
-    if (col == 0) return u * (k.a1 * s.q - s.H);
-    if (col == nv - 1) return k.g * u;
-    if (col == 1 + d) return fma_(-(k.a1 * u), u, s.H);
-    return -(k.a1 * u) * s.v[col - 1];
+    if (col == 0) return u * (eos_phi(s, k) - s.H);
+    if (col == nv - 1) return eos_1pG(s, k) * u;
+    if (col == 1 + d) return fma_(-(eos_G(s, k) * u), u, s.H);
+    return -(eos_G(s, k) * u) * s.v[col - 1];
   }
   const int i = row - 1;
   if (i != d) {
@@ -369,10 +410,10 @@ __device__ __forceinline__ R jac_entry(const Pt<R, D>& s, const Consts<R>& k, in
     return R(0);
   }
   // row 1 + d
-  if (col == 0) return fma_(-u, u, k.a1 * s.q);
-  if (col == nv - 1) return k.a1;
-  if (col == 1 + d) return k.g3 * u;
-  return -(k.a1 * s.v[col - 1]);
+  if (col == 0) return fma_(-u, u, eos_phi(s, k));
+  if (col == nv - 1) return eos_G(s, k);
+  if (col == 1 + d) return eos_2mG(s, k) * u;
+  return -(eos_G(s, k) * s.v[col - 1]);
 }
 
 // Tangential direction t_k of d (ascending), compile-time.
@@ -383,15 +424,21 @@ template <int D, int d> __device__ __forceinline__ constexpr int tang(int k) {
 // Forward characteristic transform Y = L_d W at one point (see fdbb.h):
 //   t = b1 (q w0 - v.w + w_e), a = (u w0 - w_d) / c, b1 = (gamma-1)/c^2
 //   Y0 = (t + a)/2, Y1 = w0 - t, Y_{1+k} = w_{t_k} - v_{t_k} w0, Y_{nv-1} = (t - a)/2
-template <int D, int d, class R>
-__device__ __forceinline__ void char_fwd(const Pt<R, D>& s, const Consts<R>& k, const R* w, R* y) {
+// For a general EOS t = (dp/dU . w) / c^2 = (phi w0 + Gamma (w_e - v.w)) / c^2.
+template <int D, int d, class R, class K>
+__device__ __forceinline__ void char_fwd(const Pt<R, D>& s, const K& k, const R* w, R* y) {
   constexpr int nv = D + 2;
   const R ic = rsqrt_(s.c2);
-  const R b1 = k.a1 * ic * ic;
   R dot = s.v[0] * w[1];
 #pragma unroll
   for (int i = 1; i < D; ++i) dot = fma_(s.v[i], w[1 + i], dot);
-  const R t = b1 * (fma_(s.q, w[0], w[nv - 1]) - dot);
+  R t;
+  if constexpr (K::kIdeal) {
+    const R b1 = k.a1 * ic * ic;
+    t = b1 * (fma_(s.q, w[0], w[nv - 1]) - dot);
+  } else {
+    t = fma_(s.ph, w[0], s.G * (w[nv - 1] - dot)) * (ic * ic);
+  }
   const R a = fma_(s.v[d], w[0], -w[1 + d]) * ic;
   y[0] = R(0.5f) * (t + a);
   y[1] = w[0] - t;
@@ -403,9 +450,11 @@ __device__ __forceinline__ void char_fwd(const Pt<R, D>& s, const Consts<R>& k, 
   y[nv - 1] = R(0.5f) * (t - a);
 }
 
-// Inverse characteristic transform Y = R_d W at one point.
-template <int D, int d, class R>
-__device__ __forceinline__ void char_inv(const Pt<R, D>& s, const Consts<R>& k, const R* w, R* y) {
+// Inverse characteristic transform Y = R_d W at one point.  The entropy wave's
+// energy component is q for the ideal gas and 2q - phi/Gamma for a general EOS
+// (the value that leaves the pressure unchanged across the wave).
+template <int D, int d, class R, class K>
+__device__ __forceinline__ void char_inv(const Pt<R, D>& s, const K& k, const R* w, R* y) {
   constexpr int nv = D + 2;
   const R c = sqrt_(s.c2);
   const R a1 = w[0], a2 = w[1], an = w[nv - 1];
@@ -416,7 +465,10 @@ __device__ __forceinline__ void char_inv(const Pt<R, D>& s, const Consts<R>& k, 
   for (int i = 0; i < D; ++i) y[1 + i] = s.v[i] * sum;
   y[1 + d] = y[1 + d] + dif;
   R e = fma_(s.H, a1 + an, s.v[d] * dif);
-  e = fma_(s.q, a2, e);
+  if constexpr (K::kIdeal)
+    e = fma_(s.q, a2, e);
+  else
+    e = fma_(fma_(R(2), s.q, -(s.ph / s.G)), a2, e);
 #pragma unroll
   for (int kk = 0; kk < D - 1; ++kk) {
     const int tk = tang<D, d>(kk);
@@ -431,8 +483,9 @@ __device__ __forceinline__ void char_inv(const Pt<R, D>& s, const Consts<R>& k, 
 //   gU[1+j]   = u g_j - (gamma-1) v_j z             (j != d)
 //   gU[1+d]   = g_0 + sigma + 2 u g_d + H g_e - (gamma-1) u z
 //   gU[nv-1]  = (gamma-1) g_d + gamma u g_e
-template <int D, int d, class R>
-__device__ __forceinline__ void flux_vjp_pt(const Pt<R, D>& s, const Consts<R>& k, const R* g, R* y) {
+// (general EOS: gamma - 1 -> Gamma, gamma -> 1 + Gamma, phi per point).
+template <int D, int d, class R, class K>
+__device__ __forceinline__ void flux_vjp_pt(const Pt<R, D>& s, const K& k, const R* g, R* y) {
   constexpr int nv = D + 2;
   const R u = s.v[d];
   const R gd = g[1 + d], ge = g[nv - 1];
@@ -441,19 +494,21 @@ __device__ __forceinline__ void flux_vjp_pt(const Pt<R, D>& s, const Consts<R>& 
 #pragma unroll
   for (int i = 0; i < D; ++i)
     if (i != d) sigma = fma_(s.v[i], g[1 + i], sigma);
-  const R phi = k.a1 * s.q;
+  const R phi = eos_phi(s, k), a1 = eos_G(s, k);
   y[0] = fma_(phi, z, -fma_(u, sigma, u * fma_(u, gd, s.H * ge)));
 #pragma unroll
   for (int j = 0; j < D; ++j)
-    if (j != d) y[1 + j] = fma_(u, g[1 + j], -(k.a1 * s.v[j] * z));
-  y[1 + d] = g[0] + sigma + fma_(R(2) * u, gd, fma_(s.H, ge, -(k.a1 * u * z)));
-  y[nv - 1] = fma_(k.a1, gd, k.g * u * ge);
+    if (j != d) y[1 + j] = fma_(u, g[1 + j], -(a1 * s.v[j] * z));
+  y[1 + d] = g[0] + sigma + fma_(R(2) * u, gd, fma_(s.H, ge, -(a1 * u * z)));
+  y[nv - 1] = fma_(a1, gd, eos_1pG(s, k) * u * ge);
 }
 
 // State from primitive variables (rho, v, p set): m = rho v, q = |v|^2/2,
-// rhoE = p/(gamma-1) + rho q (paper section 2.2, Fig. 9, the primitive form).
-template <class R, int D, class G>
-__device__ __forceinline__ void derive_prim(Pt<R, D>& s, const Consts<R>& k, G& g) {
+// rhoE = p/(gamma-1) + rho q (paper section 2.2, Fig. 9, the primitive form);
+// for a general EOS rhoE = rho e(rho, p) + rho q, with the partial derivatives
+// of rho e(rho, p) from one dual-number evaluation.
+template <class R, int D, class K, class G>
+__device__ __forceinline__ void derive_prim(Pt<R, D>& s, const K& k, G& g) {
   R v2 = s.v[0] * s.v[0];
 #pragma unroll
   for (int i = 1; i < D; ++i) v2 = fma_(s.v[i], s.v[i], v2);
@@ -464,7 +519,14 @@ __device__ __forceinline__ void derive_prim(Pt<R, D>& s, const Consts<R>& k, G& 
   }
   s.q = R(0.5f) * v2;
   s.rq = s.rho * s.q;
-  s.rE = fma_(s.p, k.ia1, s.rq);
+  if constexpr (K::kIdeal) {
+    s.rE = fma_(s.p, k.ia1, s.rq);
+  } else {
+    const D2<R> Z = k.rhoe_rhop(arg1(s.rho), arg2(s.p));
+    s.rE = Z.v + s.rq;
+    s.zr = Z.dr;
+    s.zp = Z.de;
+  }
   g.check(s.q);
   g.check(s.rE);
 }
@@ -472,17 +534,25 @@ __device__ __forceinline__ void derive_prim(Pt<R, D>& s, const Consts<R>& k, G& 
 // Entry of B_d = dF_d/dV (rows in U order, columns in V order), u = v_d:
 //   row 0: (u, rho at col 1+d, 0); row 1+i: (u v_i, rho (delta_jd v_i +
 //   delta_ij u), delta_id); row nv-1: (u q, delta_jd (gamma/(gamma-1) p +
-//   rho q) + rho u v_j, gamma/(gamma-1) u).
-template <int D, int d, class R>
-__device__ __forceinline__ R jacp_entry(const Pt<R, D>& s, const Consts<R>& k, int row, int col) {
+//   rho q) + rho u v_j, gamma/(gamma-1) u).  General EOS, with z = rho e(rho, p):
+//   row nv-1: (u (q + dz/drho), delta_jd (rhoE + p) + rho u v_j, u (dz/dp + 1)).
+template <int D, int d, class R, class K>
+__device__ __forceinline__ R jacp_entry(const Pt<R, D>& s, const K& k, int row, int col) {
   constexpr int nv = D + 2;
   const R u = s.v[d];
   if (row == 0) return col == 0 ? u : (col == 1 + d ? s.rho : R(0));
   if (row == nv - 1) {
-    if (col == 0) return u * s.q;
-    if (col == nv - 1) return k.gia1 * u;
-    const R e = s.m[col - 1] * u;  // rho v_j u
-    return col == 1 + d ? e + fma_(k.gia1, s.p, s.rq) : e;
+    if constexpr (K::kIdeal) {
+      if (col == 0) return u * s.q;
+      if (col == nv - 1) return k.gia1 * u;
+      const R e = s.m[col - 1] * u;  // rho v_j u
+      return col == 1 + d ? e + fma_(k.gia1, s.p, s.rq) : e;
+    } else {
+      if (col == 0) return u * (s.q + s.zr);
+      if (col == nv - 1) return fma_(u, s.zp, u);
+      const R e = s.m[col - 1] * u;
+      return col == 1 + d ? e + (s.rE + s.p) : e;
+    }
   }
   const int i = row - 1;
   if (col == 0) return u * s.v[i];

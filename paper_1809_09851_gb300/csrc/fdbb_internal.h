@@ -23,13 +23,21 @@ struct KArgs {
                  // gamma/(gamma-1), 1/((gamma-1) c_v)
   float kf[8];   // the same, rounded once to float
   float kl[8];   // kd - kf rounded to float: (kf, kl) is the double-word constant
+  double ke[8];  // general EOS parameters (slots: gamma-1, 1/(gamma-1), b, 1/c_v,
+                 // p_inf, q, gamma p_inf, a); unused by the ideal-gas kernels
+  float kef[8];  // the same, rounded once to float
 };
+
+// Equation of state of a launch: the ideal gas (gamma in kd/kf/kl) or one of
+// the general models (parameters in ke/kef).
+enum class EosKind { Ideal = 0, Nasg = 1, Vdw = 2 };
 
 struct LaunchReq {
   OpKind op;
   int dim;
   int dir;
   cudaStream_t stream;
+  EosKind eos = EosKind::Ideal;
 };
 
 // Streaming multiprocessors of the current device (cached per device).
@@ -41,6 +49,9 @@ cudaError_t dispatch_f32(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_bf16(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f64dw(const LaunchReq& r, const KArgs& a);
+// General-EOS blocks (r.eos != Ideal), double and float storage.
+cudaError_t dispatch_eos_f64(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_eos_f32(const LaunchReq& r, const KArgs& a);
 
 // Bounded device waits that ran out since the last call, per translation unit
 // (read and cleared; synchronous).
@@ -49,5 +60,7 @@ unsigned int wait_timeouts_f32();
 unsigned int wait_timeouts_f16();
 unsigned int wait_timeouts_bf16();
 unsigned int wait_timeouts_f64dw();
+unsigned int wait_timeouts_eos_f64();
+unsigned int wait_timeouts_eos_f32();
 
 }  // namespace fdbb

@@ -52,6 +52,11 @@ template <> __device__ __forceinline__ Consts<dw> consts<dw>(const KArgs& a) {
           dw(a.kf[4], a.kl[4]), dw(a.kf[5], a.kl[5]), dw(a.kf[6], a.kl[6]), dw(a.kf[7], a.kl[7])};
 }
 
+// Model tag of the ideal gas (the general-EOS tags are in fdbb_eos.cuh).
+struct IdealModel {
+  template <class R> static __device__ __forceinline__ Consts<R> make(const KArgs& a) { return consts<R>(a); }
+};
+
 // ---------------------------------------------------------------------------
 // Input sources: plane k of the current VW points, in the storage's load type.
 // ---------------------------------------------------------------------------
@@ -136,8 +141,8 @@ __device__ __forceinline__ void store_field(const KArgs& a, int base, int64_t i0
   }
 }
 
-template <int VW, int D, class R, class G>
-__device__ __forceinline__ void derive_all(Pt<R, D> (&s)[VW], const Consts<R>& k, G& g) {
+template <int VW, int D, class R, class K, class G>
+__device__ __forceinline__ void derive_all(Pt<R, D> (&s)[VW], const K& k, G& g) {
 #pragma unroll
   for (int j = 0; j < VW; ++j) derive(s[j], k, g);
 }
@@ -167,9 +172,9 @@ __device__ __forceinline__ void emit_flux(const KArgs& a, int base, int64_t i0, 
 }
 
 // Jacobian A_d into output planes base..base+nv*nv-1 (row-major).
-template <class T, int VW, int D, int d, class R>
+template <class T, int VW, int D, int d, class R, class K>
 __device__ __forceinline__ void emit_jac(const KArgs& a, int base, int64_t i0, int cnt, const Pt<R, D> (&s)[VW],
-                                         const Consts<R>& k) {
+                                         const K& k) {
   constexpr int nv = D + 2;
 #pragma unroll
   for (int row = 0; row < nv; ++row) {
@@ -192,8 +197,8 @@ __device__ __forceinline__ void emit_jac(const KArgs& a, int base, int64_t i0, i
 // |v|^2 = (sum m_i^2) / (rho rho)  (paper section 3, Eq. (2)).
 template <int D> struct OpVMag2 {
   static constexpr int kIn = D + 1;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>&, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K&, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     R rho[VW], m[VW], num[VW];
@@ -218,8 +223,8 @@ template <int D> struct OpVMag2 {
 // V = (rho, v, p) from U.
 template <int D> struct OpPrim {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -250,11 +255,12 @@ template <int D> struct OpPrim {
   }
 };
 
-// U = (rho, rho v, p/(gamma-1) + rho |v|^2 / 2) from V.
+// U = (rho, rho v, p/(gamma-1) + rho |v|^2 / 2) from V; for a general EOS
+// rhoE = rho e(rho, p) + rho |v|^2 / 2.
 template <int D> struct OpCons {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     R rho[VW], v[D][VW], p[VW], x[VW];
@@ -278,7 +284,12 @@ template <int D> struct OpCons {
       store<T, VW, R>(outp<T>(a, 1 + i), i0, cnt, x);
     }
 #pragma unroll
-    for (int j = 0; j < VW; ++j) x[j] = fma_(p[j], k.ia1, R(0.5f) * rho[j] * v2[j]);
+    for (int j = 0; j < VW; ++j) {
+      if constexpr (K::kIdeal)
+        x[j] = fma_(p[j], k.ia1, R(0.5f) * rho[j] * v2[j]);
+      else
+        x[j] = k.rhoe_rhop(rho[j], p[j]) + R(0.5f) * rho[j] * v2[j];
+    }
     store<T, VW, R>(outp<T>(a, D + 1), i0, cnt, x);
     return true;
   }
@@ -287,8 +298,8 @@ template <int D> struct OpCons {
 // p and c.
 template <int D> struct OpEos {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -313,8 +324,8 @@ template <int D> struct OpEos {
 // w- = u - 2c/(gamma-1), w+ = u + 2c/(gamma-1), s = p rho^-gamma.
 template <int D, int d> struct OpRiemann {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -342,8 +353,8 @@ template <int D, int d> struct OpRiemann {
 // Flux column d, or all columns when d == -1.
 template <int D, int d> struct OpFlux {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -363,8 +374,8 @@ template <int D, int d> struct OpFlux {
 
 template <int D, int d> struct OpJac {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -378,8 +389,8 @@ template <int D, int d> struct OpJac {
 
 template <int D, int d, bool INV> struct OpChar {
   static constexpr int kIn = 2 * (D + 2);
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
@@ -401,12 +412,15 @@ template <int D, int d, bool INV> struct OpChar {
   }
 };
 
+template <int D, int d> using OpCharFwd = OpChar<D, d, false>;
+template <int D, int d> using OpCharInv = OpChar<D, d, true>;
+
 // All flux columns (planes 0..D*nv-1), A_dj (D*nv .. D*nv+nv^2-1) and
 // L_dj W (last nv planes) in one pass; inputs U (planes 0..nv-1), W (nv..2nv-1).
 template <int D, int dj> struct OpFused {
   static constexpr int kIn = 2 * (D + 2);
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
@@ -433,8 +447,8 @@ template <int D, int dj> struct OpFused {
 
 template <int D, int d> struct OpVjp {
   static constexpr int kIn = 2 * (D + 2);
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
@@ -454,8 +468,8 @@ template <int D, int d> struct OpVjp {
 // Roe flux between U_L (planes 0..nv-1) and U_R (nv..2nv-1) in direction d.
 template <int D, int d> struct OpRoeFlux {
   static constexpr int kIn = 2 * (D + 2);
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
@@ -479,8 +493,8 @@ template <int D, int d> struct OpRoeFlux {
 // and U_R (nv..2nv-1) applied to W (2nv..3nv-1).
 template <int D, int d, bool INV> struct OpRoeChar {
   static constexpr int kIn = 3 * (D + 2);
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
@@ -536,8 +550,8 @@ __device__ __forceinline__ void load_V(const Src& src, int base, Pt<R, D> (&s)[V
 // all columns when d == -1 (paper section 2.2, Figs. 9 and 11).
 template <int D, int d> struct OpFluxPrim {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -570,8 +584,8 @@ template <int D, int d> struct OpFluxPrim {
 // B_d = dF_d/dV, nv*nv planes row-major.
 template <int D, int d> struct OpJacPrim {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
@@ -606,11 +620,12 @@ template <int D, int d> struct OpJacPrim {
 };
 
 // Temperature T = e / c_v = p / rho / ((gamma - 1) c_v) (paper section 2.2,
-// "Equations of state", T_rhoe of the EOS prototype, Fig. 10).
+// "Equations of state", T_rhoe of the EOS prototype, Fig. 10); a general EOS
+// evaluates its own T_rhoe(rho, e).
 template <int D> struct OpTemp {
   static constexpr int kIn = D + 2;
-  template <class T, int VW, class R, class Src>
-  static __device__ __forceinline__ bool apply(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0,
+  template <class T, int VW, class R, class K, class Src>
+  static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -619,7 +634,12 @@ template <int D> struct OpTemp {
     if (!g.ok) return false;
     R x[VW];
 #pragma unroll
-    for (int j = 0; j < VW; ++j) x[j] = s[j].p * s[j].r * k.tcv;
+    for (int j = 0; j < VW; ++j) {
+      if constexpr (K::kIdeal)
+        x[j] = s[j].p * s[j].r * k.tcv;
+      else
+        x[j] = k.T_rhoe(s[j].rho, s[j].ie);
+    }
     store<T, VW, R>(outp<T>(a, 0), i0, cnt, x);
     return true;
   }
@@ -677,8 +697,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // Kernels
 // ---------------------------------------------------------------------------
 
-template <class Op, class T, class R, class Src>
-__device__ __forceinline__ void apply_chunk(const KArgs& a, const Consts<R>& k, const Src& src, int64_t i0, int cnt) {
+template <class Op, class T, class R, class K, class Src>
+__device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Src& src, int64_t i0, int cnt) {
   constexpr int VW = Width<T, R>::VW;
   if constexpr (std::is_same<R, dw>::value) {
     // double-word fast path; chunks outside its range run in native FP64
@@ -690,8 +710,8 @@ __device__ __forceinline__ void apply_chunk(const KArgs& a, const Consts<R>& k, 
 }
 
 // Chunks [ch0, nchunk) of VW points read straight from global memory.
-template <class Op, class T, class R>
-__device__ __forceinline__ void global_chunks(const KArgs& a, const Consts<R>& k, int64_t ch0) {
+template <class Op, class T, class R, class K>
+__device__ __forceinline__ void global_chunks(const KArgs& a, const K& k, int64_t ch0) {
   constexpr int VW = Width<T, R>::VW;
   const int64_t nchunk = (a.n + VW - 1) / VW;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -703,12 +723,12 @@ __device__ __forceinline__ void global_chunks(const KArgs& a, const Consts<R>& k
   }
 }
 
-template <class Op, class T, class R>
+template <class Op, class T, class R, class Mdl>
 __global__ void __launch_bounds__(kThreads) k_pointwise(const __grid_constant__ KArgs a) {
-  global_chunks<Op, T, R>(a, consts<R>(a), 0);
+  global_chunks<Op, T, R>(a, Mdl::template make<R>(a), 0);
 }
 
-template <class Op, class T, class R>
+template <class Op, class T, class R, class Mdl>
 __global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KArgs a) {
   constexpr int VW = Width<T, R>::VW;
   constexpr int TILE = kThreads * VW;
@@ -719,7 +739,7 @@ __global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KAr
   const int tid = threadIdx.x;
   const int64_t ntiles = a.n / TILE;
   const uint32_t plane_bytes = TILE * sizeof(T);
-  const Consts<R> k = consts<R>(a);
+  const auto k = Mdl::template make<R>(a);
   // The j-th tile of this block is tile blockIdx.x + j * gridDim.x, streamed
   // into stage j % kStages; its copy completes phase j / kStages of that
   // stage's mbarrier.
@@ -785,10 +805,10 @@ inline unsigned int take_wait_timeouts_tu() {
 
 // Persistent grid of the direct kernel: enough blocks to fill every SM at its
 // occupancy, no more than there are chunks.
-template <class Op, class T, class R> cudaError_t launch_direct(const KArgs& a, cudaStream_t stream) {
+template <class Op, class T, class R, class Mdl> cudaError_t launch_direct(const KArgs& a, cudaStream_t stream) {
   static const int blocks_per_sm = [] {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pointwise<Op, T, R>, kThreads, 0) != cudaSuccess) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pointwise<Op, T, R, Mdl>, kThreads, 0) != cudaSuccess) b = 1;
     return b > 0 ? b : 1;
   }();
   constexpr int VW = Width<T, R>::VW;
@@ -796,41 +816,42 @@ template <class Op, class T, class R> cudaError_t launch_direct(const KArgs& a, 
   const int64_t need = (nchunk + kThreads - 1) / kThreads;
   const int64_t cap = (int64_t)device_sm_count() * blocks_per_sm;
   const int grid = (int)(need < cap ? need : cap);
-  k_pointwise<Op, T, R><<<grid, kThreads, 0, stream>>>(a);
+  k_pointwise<Op, T, R, Mdl><<<grid, kThreads, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
 // Staged kernel: kStages * nin planes of one tile in dynamic shared memory.
-template <class Op, class T, class R> cudaError_t launch_staged(const KArgs& a, cudaStream_t stream) {
+template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const KArgs& a, cudaStream_t stream) {
   constexpr int VW = Width<T, R>::VW;
   constexpr int TILE = kThreads * VW;
   constexpr size_t kMaxSmem = (size_t)kStages * Op::kIn * TILE * sizeof(T);
   static const cudaError_t attr =
-      cudaFuncSetAttribute(k_staged<Op, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+      cudaFuncSetAttribute(k_staged<Op, T, R, Mdl>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   if (attr != cudaSuccess) return attr;
   const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T);
   static int bps_cache[Op::kIn + 1] = {};  // blocks per SM for each nin
   int& bps = bps_cache[a.nin];
   if (bps == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_staged<Op, T, R>, kThreads, smem) != cudaSuccess) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_staged<Op, T, R, Mdl>, kThreads, smem) != cudaSuccess) b = 1;
     bps = b > 0 ? b : 1;
   }
   const int64_t ntiles = a.n / TILE;
   const int64_t cap = (int64_t)device_sm_count() * bps;
   const int grid = (int)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
-  k_staged<Op, T, R><<<grid, kThreads, smem, stream>>>(a);
+  k_staged<Op, T, R, Mdl><<<grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
 // The staged kernel pays off once every SM has a few tiles to stream, and
 // while its two-stage ring leaves room for more than one block per SM.
-template <class Op, class T, class R> cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
+template <class Op, class T, class R, class Mdl = IdealModel>
+cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
   constexpr int TILE = kThreads * Width<T, R>::VW;
   const size_t ring = (size_t)kStages * a.nin * TILE * sizeof(T);
   if (a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn && ring <= (100u << 10))
-    return launch_staged<Op, T, R>(a, stream);
-  return launch_direct<Op, T, R>(a, stream);
+    return launch_staged<Op, T, R, Mdl>(a, stream);
+  return launch_direct<Op, T, R, Mdl>(a, stream);
 }
 
 // Dispatch on (op, dim, dir) for storage type T and compute type R.
@@ -907,6 +928,61 @@ template <class T, class R> cudaError_t dispatch(const LaunchReq& r, const KArgs
     case 1: return dispatch_dim<1, T, R>(r, a);
     case 2: return dispatch_dim<2, T, R>(r, a);
     case 3: return dispatch_dim<3, T, R>(r, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// General-EOS blocks for EOS model Mdl, storage T computed in T's own IEEE
+// type: every block whose formulas the EOS enters, except the Riemann
+// invariants and the Roe-averaged forms, which have no closed form for a
+// general EOS.
+template <int D, class T, class R, class Mdl> cudaError_t dispatch_eos_dim(const LaunchReq& r, const KArgs& a) {
+  const int d = r.dir;
+  switch (r.op) {
+    case OpKind::Prim: return launch_op<OpPrim<D>, T, R, Mdl>(a, r.stream);
+    case OpKind::Cons: return launch_op<OpCons<D>, T, R, Mdl>(a, r.stream);
+    case OpKind::Eos: return launch_op<OpEos<D>, T, R, Mdl>(a, r.stream);
+    case OpKind::FluxAll: return launch_op<OpFlux<D, -1>, T, R, Mdl>(a, r.stream);
+    case OpKind::FluxPrimAll: return launch_op<OpFluxPrim<D, -1>, T, R, Mdl>(a, r.stream);
+    case OpKind::Temp: return launch_op<OpTemp<D>, T, R, Mdl>(a, r.stream);
+    default: break;
+  }
+#define FDBB_EOS_DIR_CASES(OPK, ...)                                                              \
+  case OPK:                                                                                       \
+    if (d == 0) return launch_op<__VA_ARGS__<D, 0>, T, R, Mdl>(a, r.stream);                      \
+    if constexpr (D > 1)                                                                          \
+      if (d == 1) return launch_op<__VA_ARGS__<D, (D > 1 ? 1 : 0)>, T, R, Mdl>(a, r.stream);      \
+    if constexpr (D > 2)                                                                          \
+      if (d == 2) return launch_op<__VA_ARGS__<D, (D > 2 ? 2 : 0)>, T, R, Mdl>(a, r.stream);      \
+    return cudaErrorInvalidValue;
+  switch (r.op) {
+    FDBB_EOS_DIR_CASES(OpKind::Flux, OpFlux)
+    FDBB_EOS_DIR_CASES(OpKind::Jac, OpJac)
+    FDBB_EOS_DIR_CASES(OpKind::Fused, OpFused)
+    FDBB_EOS_DIR_CASES(OpKind::Vjp, OpVjp)
+    FDBB_EOS_DIR_CASES(OpKind::FluxPrim, OpFluxPrim)
+    FDBB_EOS_DIR_CASES(OpKind::JacPrim, OpJacPrim)
+    FDBB_EOS_DIR_CASES(OpKind::CharFwd, OpCharFwd)
+    FDBB_EOS_DIR_CASES(OpKind::CharInv, OpCharInv)
+    default: break;
+  }
+#undef FDBB_EOS_DIR_CASES
+  return cudaErrorInvalidValue;
+}
+
+template <class T, class R, class Mdl> cudaError_t dispatch_eos_model(const LaunchReq& r, const KArgs& a) {
+  switch (r.dim) {
+    case 1: return dispatch_eos_dim<1, T, R, Mdl>(r, a);
+    case 2: return dispatch_eos_dim<2, T, R, Mdl>(r, a);
+    case 3: return dispatch_eos_dim<3, T, R, Mdl>(r, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T, class R> cudaError_t dispatch_eos(const LaunchReq& r, const KArgs& a) {
+  switch (r.eos) {
+    case EosKind::Nasg: return dispatch_eos_model<T, R, NasgModel>(r, a);
+    case EosKind::Vdw: return dispatch_eos_model<T, R, VdwModel>(r, a);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -2,6 +2,7 @@
 exports every entry point declared in include/fdbb.h, and rejects bad
 arguments before any launch (fake device pointers are never dereferenced
 because every call here fails validation or has n == 0)."""
+import ctypes
 import os
 import re
 import subprocess
@@ -84,3 +85,48 @@ def test_empty_input_is_a_no_op(L):
     # n == 0 validates the arguments and returns without touching the device
     assert L.fdbb_flux(3, -1, 1.4, 0, capi.FDBB_F32, _U(5), _U(15), None) == 0
     assert L.fdbb_euler_fused(3, 0, 1.4, 0, capi.FDBB_F64, _U(5), _U(5), _U(15), _U(25), _U(5), None) == 0
+
+
+def _eos(**kw):
+    d = {"kind": "nasg", "gamma": 1.6, "p_inf": 1.0, "b": 0.1, "q": -0.3, "cv": 2.0}
+    d.update(kw)
+    return ctypes.byref(capi.eos_model(d))
+
+
+def test_general_eos_argument_errors(L):
+    F64, F32 = capi.FDBB_F64, capi.FDBB_F32
+    # NULL model, bad parameters, reserved field
+    assert L.fdbb_flux_eos(None, 3, 0, 10, F64, _U(5), _U(5), None) == 1
+    for bad in ({"gamma": 1.0}, {"cv": 0.0}, {"b": -0.1}, {"p_inf": -1.0}, {"kind": "vdw", "a": -1.0}):
+        assert L.fdbb_pressure_eos(_eos(**bad), 3, 10, F64, _U(5), A, A, None) == 1, bad
+    m = capi.eos_model({"kind": "nasg", "gamma": 1.4})
+    m.reserved = 1
+    assert L.fdbb_flux_eos(ctypes.byref(m), 3, 0, 10, F64, _U(5), _U(5), None) == 1
+    m = capi.eos_model({"kind": "nasg", "gamma": 1.4})
+    m.kind = 7
+    assert L.fdbb_flux_eos(ctypes.byref(m), 3, 0, 10, F64, _U(5), _U(5), None) == 1
+    # dim / dir / n
+    assert L.fdbb_flux_eos(_eos(), 4, 0, 10, F64, _U(6), _U(6), None) == 1
+    assert L.fdbb_flux_jac_eos(_eos(), 2, -1, 10, F64, _U(4), _U(16), None) == 1
+    assert L.fdbb_prim_from_cons_eos(_eos(), 3, -1, F64, _U(5), _U(5), None) == 1
+    # the general models take float64 and float32 planes only
+    for t in (capi.FDBB_F16, capi.FDBB_BF16, capi.FDBB_F64_DW):
+        assert L.fdbb_flux_eos(_eos(), 3, 0, 10, t, _U(5), _U(5), None) == 4
+    assert L.fdbb_flux_eos(_eos(), 3, 0, 10, 9, _U(5), _U(5), None) == 4
+    # NULL / misaligned planes, W required for Y in the fused pass
+    assert L.fdbb_flux_eos(_eos(), 3, 0, 10, F32, None, _U(5), None) == 2
+    assert L.fdbb_temperature_eos(_eos(), 3, 10, F64, _U(5), None, None) == 2
+    assert L.fdbb_flux_vjp_eos(_eos(), 3, 0, 10, F64, _U(5, MIS), _U(5), _U(5), None) == 3
+    assert L.fdbb_euler_fused_eos(_eos(), 3, 0, 10, F64, _U(5), None, None, None, _U(5), None) == 2
+    # the ideal kind forwards to the ideal-gas entry points and their checks
+    ideal = _eos(kind="ideal", gamma=1.4)
+    assert L.fdbb_flux_eos(ideal, 3, 3, 10, F64, _U(5), _U(5), None) == 1
+    assert L.fdbb_flux_eos(ideal, 3, 0, 10, capi.FDBB_BF16, _U(5, MIS), _U(5), None) == 3
+
+
+def test_general_eos_empty_input_is_a_no_op(L):
+    for kind in ("nasg", "vdw", "ideal"):
+        m = _eos(kind=kind, a=0.05)
+        assert L.fdbb_euler_fused_eos(m, 3, 1, 0, capi.FDBB_F64, _U(5), _U(5), _U(15), _U(25), _U(5), None) == 0
+        assert L.fdbb_cons_from_prim_eos(m, 2, 0, capi.FDBB_F32, _U(4), _U(4), None) == 0
+        assert L.fdbb_flux_jac_prim_eos(m, 1, 0, 0, capi.FDBB_F64, _U(3), _U(9), None) == 0
