@@ -52,7 +52,8 @@ L2_BYTES = 129 * 2 ** 20
 NCU_TRAFFIC = {"source_hash": "5e59be38340d9c84", "bytes_per_point": 425.5}
 
 
-FUSED_KERNEL_SOURCES = ("fdbb_device.cuh", "fdbb_dw.cuh", "fdbb_kernels.cuh", "fdbb_internal.h", "kern_f64dw.cu")
+FUSED_KERNEL_SOURCES = ("fdbb_device.cuh", "fdbb_dw.cuh", "fdbb_eos.cuh", "fdbb_kernels.cuh", "fdbb_internal.h",
+                        "kern_f64dw3.cu")
 
 
 def kernel_source_hash() -> str:
@@ -216,24 +217,24 @@ def run_general_eos(args, n, W64, out64, stream, dev, world, hbm_peak):
     del V
     res = {"eos": "NASG gamma=1.6 p_inf=1 b=0.1 q=-0.3 c_v=2 (nondimensional)",
            "workload": "rho~U[0.2,4], v~N(0,1), p~U[0.1,10]"}
-    for tag, dt in (("f64", torch.float64), ("f32", torch.float32)):
-        if tag == "f64":
+    for tag, dt, dw in (("f64dw", torch.float64, True), ("f64", torch.float64, False), ("f32", torch.float32, False)):
+        if dt == torch.float64:
             Ut, Wt, out = U, W64, out64
         else:
             Ut = [u.to(dt) for u in U]
             Wt = [w.to(dt) for w in W64]
             out = tuple([torch.empty(n, dtype=dt, device=dev) for _ in range(k)] for k in (D * NV, NV * NV, NV))
-        per, total = time_launch(lambda: blocks.euler_fused_eos(Ut, Wt, eos, 0, out=out), args.steps,
+        per, total = time_launch(lambda: blocks.euler_fused_eos(Ut, Wt, eos, 0, out=out, dw=dw), args.steps,
                                  args.warmup, stream)
         t = max_over_ranks(total / 1e3, world, dev)
         avg = sum(per) / len(per) / 1e3
-        b = (PLANES_IN + PLANES_OUT) * BYTES[tag] * n
+        b = (PLANES_IN + PLANES_OUT) * BYTES["f32" if dt == torch.float32 else "f64"] * n
         res[tag] = {"value": round(world * n * args.steps / t / 1e9, 3), "unit": UNIT,
                     "ms_per_step": round(t * 1e3 / args.steps, 4), "p99_ms": round(pct(per, 99), 4),
                     "hbm_gbs": round(b / avg / 1e9, 1), "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3),
-                    "stated_err": "|gpu - oracle| <= 1e-12 * S" if tag == "f64"
+                    "stated_err": "|gpu - oracle| <= 1e-12 * S" if dt == torch.float64
                     else "|gpu - oracle| <= 2^-24 |o| + 64 * 2^-24 * S"}
-        if tag != "f64":
+        if dt != torch.float64:
             del Ut, Wt, out
     del U
     torch.cuda.empty_cache()
@@ -447,9 +448,11 @@ def run_fv_batch(args, dev, hbm_peak):
 
 def run_e2e(args, U, W, out, stream, dev, world):
     """Same metric through the public API with pinned host buffers: every step
-    copies U and W host->device, runs the fused pass and copies all 45 output
-    planes device->host (blocks.euler_fused_host: chunks of 2^22 points whose
-    copies and kernels overlap on three streams)."""
+    moves U and W host->device, runs the fused pass and moves all 45 output
+    planes device->host (blocks.euler_fused_host; default mode "mapped_out":
+    chunked host->device copies of the inputs overlapped with kernels that
+    write their outputs straight into the pinned host planes over the
+    CPU-GPU link)."""
     import torch
     from paper_1809_09851_gb300 import blocks
     n = U[0].shape[0]
@@ -466,21 +469,22 @@ def run_e2e(args, U, W, out, stream, dev, world):
     d2h = hOut.numel() * hOut.element_size()
     with torch.cuda.stream(stream):
         work = blocks.euler_fused_host(hU, hW, (hF, hA, hY), 0, GAMMA, chunk=args.e2e_chunk, device=dev,
-                                       dw=True)
+                                       dw=True, mode=args.e2e_mode)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             work = blocks.euler_fused_host(hU, hW, (hF, hA, hY), 0, GAMMA, chunk=args.e2e_chunk, device=dev,
-                                           work=work, dw=True)
+                                           work=work, dw=True, mode=args.e2e_mode)
         e1.record(stream)
         torch.cuda.synchronize()
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
     del hU, hW, hF, hA, hY, rows_in, rows_out, hIn, hOut, work
     return {"value": round(world * n * steps / t / 1e9, 4), "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": round(t * 1e3 / steps, 3), "chunk_points": args.e2e_chunk,
-            "gpu_launches_per_step": -(-n // args.e2e_chunk)}
+            "ms_per_step": round(t * 1e3 / steps, 3), "mode": args.e2e_mode,
+            "chunk_points": args.e2e_chunk if args.e2e_mode != "mapped" else n,
+            "gpu_launches_per_step": -(-n // args.e2e_chunk) if args.e2e_mode != "mapped" else 1}
 
 
 # ---------------------------------------------------------------------------
@@ -558,6 +562,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=N_POINTS, help="points per GPU (default 2^26)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-chunk", type=int, default=1 << 23)
+    ap.add_argument("--e2e-mode", choices=["mapped_out", "mapped", "copy"], default="mapped_out",
+                    help="how the end-to-end leg moves host data (blocks.euler_fused_host)")
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=1 << 16)

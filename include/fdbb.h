@@ -110,6 +110,22 @@ FDBB_API int fdbb_version(void);
 FDBB_API fdbb_status fdbb_device_status(void);
 
 /*
+ * Where a plane pointer lives, for callers that hand the blocks host memory:
+ *   FDBB_PTR_DEVICE  memory of the current CUDA device (cudaMalloc, stream-ordered
+ *                    pools; another device's memory is FDBB_PTR_OTHER);
+ *   FDBB_PTR_HOST    page-locked host memory (cudaHostAlloc, cudaMallocHost,
+ *                    cudaHostRegister) that the device reads and writes at the
+ *                    same address (unified addressing): the kernels accept it
+ *                    as plane memory and move it over the CPU-GPU link;
+ *   FDBB_PTR_MANAGED managed memory (cudaMallocManaged);
+ *   FDBB_PTR_OTHER   anything else (pageable host memory, invalid pointers).
+ * Synchronous with respect to the host, enqueues nothing; the CUDA error of a
+ * failed query is consumed.
+ */
+typedef enum { FDBB_PTR_OTHER = 0, FDBB_PTR_DEVICE = 1, FDBB_PTR_HOST = 2, FDBB_PTR_MANAGED = 3 } fdbb_ptr_kind;
+FDBB_API fdbb_ptr_kind fdbb_pointer_kind(const void *p);
+
+/*
  * |v|^2 = (m_1^2 + .. + m_D^2) / rho^2, the kinetic-energy sub-expression
  * used as micro-benchmark in the paper (section 3, Eq. (2)).
  * U: the first D+1 planes of a conservative field (rho, m_1..m_D); y: 1 plane.
@@ -197,6 +213,22 @@ FDBB_API fdbb_status fdbb_char_transform(int dim, int dir, double gamma, int64_t
 FDBB_API fdbb_status fdbb_euler_fused(int dim, int dir_jac, double gamma, int64_t n, fdbb_dtype t,
                              const void *const *U, const void *const *W, void *const *F,
                              void *const *A, void *const *Y, fdbb_stream_t stream);
+
+/*
+ * fdbb_euler_fused over planes that may live in page-locked host memory
+ * (FDBB_PTR_HOST, see fdbb_pointer_kind) as well as in device memory: the
+ * kernel reads and writes host planes directly over the CPU-GPU link
+ * (NVLink-C2C on Grace-Blackwell), so a field resident in host memory needs
+ * no staging copies and no device memory.  Every non-NULL plane is checked
+ * with fdbb_pointer_kind before the launch: a plane that is neither device
+ * memory nor page-locked host memory returns FDBB_ERR_ARG and nothing is
+ * enqueued.  When an input plane is host (or managed) memory the direct
+ * kernel (plain global loads) runs, since the bulk-copy staging reads device
+ * memory only.  Arguments, layout and results are those of fdbb_euler_fused.
+ */
+FDBB_API fdbb_status fdbb_euler_fused_host(int dim, int dir_jac, double gamma, int64_t n, fdbb_dtype t,
+                                           const void *const *U, const void *const *W, void *const *F,
+                                           void *const *A, void *const *Y, fdbb_stream_t stream);
 
 /*
  * Vector-Jacobian product of the direction-dir flux: gU = A_dir(U)^T G
@@ -296,8 +328,11 @@ FDBB_API fdbb_status fdbb_roe_char_transform(int dim, int dir, double gamma, int
  * The kernels take the partial derivatives of p(rho, e) and rho e(rho, p)
  * from one evaluation on dual numbers.
  *
- * Storage types: FDBB_F64 (IEEE double) and FDBB_F32 (float) for NASG and
- * VDW; others return FDBB_ERR_DTYPE.  The Riemann invariants and the
+ * Storage types: FDBB_F64 (IEEE double), FDBB_F64_DW (double-word, with the
+ * same range rule and IEEE fallback as for the ideal gas; if an EOS
+ * parameter (gamma - 1, its reciprocal, b, 1/c_v, p_inf, q, gamma p_inf, a)
+ * is non-zero and outside [2^-24, 2^24] the call runs in IEEE double) and
+ * FDBB_F32 (float) for NASG and VDW; others return FDBB_ERR_DTYPE.  The Riemann invariants and the
  * Roe-averaged forms have no counterpart here (no closed form for a general
  * EOS).  Argument errors (FDBB_ERR_ARG): eos NULL, unknown kind, gamma <= 1,
  * cv <= 0, b < 0, p_inf < 0 (NASG) or a < 0 (VDW).  States with

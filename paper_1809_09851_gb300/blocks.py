@@ -232,21 +232,73 @@ def roe_char_transform(UL, UR, W, dir: int, gamma: float = GAMMA, inverse: bool 
     return Y
 
 
+def _info_host(planes: Sequence[torch.Tensor]):
+    """Like _info, for planes that are CUDA tensors or pinned CPU tensors."""
+    if not planes:
+        raise ValueError("empty field")
+    t0 = planes[0]
+    for t in planes:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("planes must be torch tensors")
+        if not (t.is_cuda or t.is_pinned()):
+            raise ValueError("planes must be CUDA tensors or pinned CPU tensors")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError("planes must be contiguous 1-D tensors")
+        if t.dtype != t0.dtype or t.shape[0] != t0.shape[0]:
+            raise ValueError("planes must share dtype and length")
+    if t0.dtype not in DTYPES:
+        raise TypeError(f"unsupported dtype {t0.dtype}")
+    return t0.shape[0], t0.dtype
+
+
+def euler_fused_mapped(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, device=None, stream=None,
+                       dw: bool = False):
+    """fdbb_euler_fused_host: one launch over planes in pinned host memory
+    and/or device memory; the kernel reads and writes host planes directly
+    over the CPU-GPU link.  ``out`` is the (F, A, Y) triple of plane lists
+    (any may be None); W may be None when Y is None."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    D = _dim(U)
+    F, A, Y = out
+    n, dt = _info_host(list(U) + (list(W) if W is not None else []) + [p for grp in out if grp for p in grp])
+    capi.call("fdbb_euler_fused_host", D, dir_jac, gamma, n, _code(dt, dw), _ptrs(U),
+              _ptrs(W) if W is not None else None,
+              _ptrs(F) if F is not None else None, _ptrs(A) if A is not None else None,
+              _ptrs(Y) if Y is not None else None, _stream(dev, stream))
+    return out
+
+
 def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: int = 1 << 22,
-                     device=None, dw: bool = False, work=None):
+                     device=None, dw: bool = False, work=None, mode: str = "mapped_out"):
     """fdbb_euler_fused over fields in pinned HOST memory.
 
     U (nv planes) and W (nv planes) are pinned CPU tensors and ``out`` the
     (F, A, Y) plane lists, also pinned CPU tensors (rows of one pinned
-    (planes, n) tensor copy fastest).  The points are processed
-    in chunks of ``chunk`` through device staging buffers on three streams, so
-    that the host-to-device copy of chunk i+1, the kernel on chunk i and the
-    device-to-host copy of chunk i-1 overlap.  ``work`` may hold the staging
-    buffers of a previous call (returned) to avoid reallocating them.
-    Returns ``work``; the results are complete when the current stream has
-    caught up (the call makes the current stream wait for its streams).
+    (planes, n) tensor copy fastest).  Modes:
+
+    * ``"mapped_out"`` (default): chunks of ``chunk`` points; the inputs of
+      each chunk are copied host-to-device into a device staging buffer (copy
+      engine, one stream) while the kernel on the previous chunk, on a second
+      stream, reads its staged inputs and writes its outputs straight into the
+      host planes over the CPU-GPU link (fdbb_euler_fused_host): the outputs,
+      4.5x the inputs' bytes, need no device buffer and no copy.
+    * ``"mapped"``: one fdbb_euler_fused_host launch that reads the inputs from
+      host memory as well.
+    * ``"copy"``: copy engines both ways: host-to-device copy of chunk i+1,
+      the kernel on chunk i and the device-to-host copy of chunk i-1 overlap
+      on three streams.
+
+    ``work`` may hold the staging buffers of a previous call (returned) to
+    avoid reallocating them.  Returns ``work``; the results are complete when
+    the current stream has caught up (the call makes the current stream wait
+    for its streams).
     """
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if mode == "mapped":
+        euler_fused_mapped(U, W, out, dir_jac, gamma, device=dev, dw=dw)
+        return work
+    if mode not in ("mapped_out", "copy"):
+        raise ValueError(f"unknown mode {mode!r}")
     D = _dim(U)
     nv = D + 2
     n = U[0].shape[0]
@@ -255,11 +307,13 @@ def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: i
     host_out = [*F, *A, *Y]
     n_out = len(host_out)
     nbuf = 2
-    if work is None or work["chunk"] != chunk or work["dtype"] != dt:
+    copy_out = mode == "copy"
+    if work is None or work["chunk"] != chunk or work["dtype"] != dt or work["mode"] != mode:
         work = {
-            "chunk": chunk, "dtype": dt,
+            "chunk": chunk, "dtype": dt, "mode": mode,
             "in": [[torch.empty(chunk, dtype=dt, device=dev) for _ in range(2 * nv)] for _ in range(nbuf)],
-            "out": [[torch.empty(chunk, dtype=dt, device=dev) for _ in range(n_out)] for _ in range(nbuf)],
+            "out": [[torch.empty(chunk, dtype=dt, device=dev) for _ in range(n_out)] for _ in range(nbuf)]
+            if copy_out else None,
             "s_h2d": torch.cuda.Stream(dev), "s_cmp": torch.cuda.Stream(dev), "s_d2h": torch.cuda.Stream(dev),
         }
     s_h2d, s_cmp, s_d2h = work["s_h2d"], work["s_cmp"], work["s_d2h"]
@@ -270,13 +324,13 @@ def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: i
     ev_done = [torch.cuda.Event() for _ in range(nbuf)]  # kernel on buffer b finished
     ev_out = [torch.cuda.Event() for _ in range(nbuf)]   # outputs of buffer b copied out
     used = [False] * nbuf
+    code = _code(dt, dw)
     nchunks = (n + chunk - 1) // chunk
     for c in range(nchunks):
         b = c % nbuf
         lo, hi = c * chunk, min(n, (c + 1) * chunk)
         m = hi - lo
         din = work["in"][b]
-        dout = work["out"][b]
         with torch.cuda.stream(s_h2d):
             if used[b]:
                 s_h2d.wait_event(ev_done[b])  # the kernel no longer reads din
@@ -285,19 +339,23 @@ def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: i
             ev_in[b].record(s_h2d)
         with torch.cuda.stream(s_cmp):
             s_cmp.wait_event(ev_in[b])
-            if used[b]:
-                s_cmp.wait_event(ev_out[b])  # dout has been copied out
             ins = [t[:m] for t in din]
-            outs = [t[:m] for t in dout]
-            euler_fused(ins[:nv], ins[nv:], dir_jac, gamma,
-                        out=(outs[:D * nv], outs[D * nv:D * nv + nv * nv], outs[D * nv + nv * nv:]),
-                        stream=s_cmp, dw=dw)
+            if copy_out:
+                if used[b]:
+                    s_cmp.wait_event(ev_out[b])  # dout has been copied out
+                outs = [t[:m] for t in work["out"][b]]
+            else:
+                outs = [h[lo:hi] for h in host_out]
+            capi.call("fdbb_euler_fused_host", D, dir_jac, gamma, m, code, _ptrs(ins[:nv]), _ptrs(ins[nv:]),
+                      _ptrs(outs[:D * nv]), _ptrs(outs[D * nv:D * nv + nv * nv]), _ptrs(outs[D * nv + nv * nv:]),
+                      s_cmp.cuda_stream)
             ev_done[b].record(s_cmp)
-        with torch.cuda.stream(s_d2h):
-            s_d2h.wait_event(ev_done[b])
-            for h, d in zip(host_out, dout):
-                h[lo:hi].copy_(d[:m], non_blocking=True)
-            ev_out[b].record(s_d2h)
+        if copy_out:
+            with torch.cuda.stream(s_d2h):
+                s_d2h.wait_event(ev_done[b])
+                for h, d in zip(host_out, work["out"][b]):
+                    h[lo:hi].copy_(d[:m], non_blocking=True)
+                ev_out[b].record(s_d2h)
         used[b] = True
     for s in (s_h2d, s_cmp, s_d2h):
         cur.wait_stream(s)
@@ -308,7 +366,8 @@ def euler_fused_host(U, W, out, dir_jac: int = 0, gamma: float = GAMMA, chunk: i
 # General equations of state (fdbb_*_eos).  ``eos`` is a dict
 # {"kind": "ideal" | "nasg" | "vdw", "gamma", "p_inf", "b", "q", "a", "cv"}
 # (missing parameters 0, cv 1) or a capi.EosModel.  NASG and VDW take float64
-# or float32 planes; "ideal" runs the ideal-gas kernels (any dtype).
+# planes (IEEE double, or double-word with dw=True) or float32 planes;
+# "ideal" runs the ideal-gas kernels (any dtype).
 # ---------------------------------------------------------------------------
 
 def _eos_ref(eos):
@@ -316,74 +375,74 @@ def _eos_ref(eos):
     return m, ctypes.byref(m)
 
 
-def prim_from_cons_eos(U, eos, out=None, stream=None):
+def prim_from_cons_eos(U, eos, out=None, stream=None, dw: bool = False):
     D = _dim(U)
     n, dt, dev = _info(U)
     V = out if out is not None else _alloc(D + 2, n, dt, dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_prim_from_cons_eos", pm, D, n, DTYPES[dt], _ptrs(U), _ptrs(V), _stream(dev, stream))
+    capi.call("fdbb_prim_from_cons_eos", pm, D, n, _code(dt, dw), _ptrs(U), _ptrs(V), _stream(dev, stream))
     return V
 
 
-def cons_from_prim_eos(V, eos, out=None, stream=None):
+def cons_from_prim_eos(V, eos, out=None, stream=None, dw: bool = False):
     D = _dim(V)
     n, dt, dev = _info(V)
     U = out if out is not None else _alloc(D + 2, n, dt, dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_cons_from_prim_eos", pm, D, n, DTYPES[dt], _ptrs(V), _ptrs(U), _stream(dev, stream))
+    capi.call("fdbb_cons_from_prim_eos", pm, D, n, _code(dt, dw), _ptrs(V), _ptrs(U), _stream(dev, stream))
     return U
 
 
-def pressure_eos(U, eos, want_p: bool = True, want_c: bool = True, stream=None):
+def pressure_eos(U, eos, want_p: bool = True, want_c: bool = True, stream=None, dw: bool = False):
     """(p, c) under the EOS; an output not wanted is None."""
     D = _dim(U)
     n, dt, dev = _info(U)
     p = torch.empty(n, dtype=dt, device=dev) if want_p else None
     c = torch.empty(n, dtype=dt, device=dev) if want_c else None
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_pressure_eos", pm, D, n, DTYPES[dt], _ptrs(U), p.data_ptr() if p is not None else None,
+    capi.call("fdbb_pressure_eos", pm, D, n, _code(dt, dw), _ptrs(U), p.data_ptr() if p is not None else None,
               c.data_ptr() if c is not None else None, _stream(dev, stream))
     return p, c
 
 
-def temperature_eos(U, eos, out=None, stream=None):
+def temperature_eos(U, eos, out=None, stream=None, dw: bool = False):
     D = _dim(U)
     n, dt, dev = _info(U)
     T = out if out is not None else torch.empty(n, dtype=dt, device=dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_temperature_eos", pm, D, n, DTYPES[dt], _ptrs(U), T.data_ptr(), _stream(dev, stream))
+    capi.call("fdbb_temperature_eos", pm, D, n, _code(dt, dw), _ptrs(U), T.data_ptr(), _stream(dev, stream))
     return T
 
 
-def flux_eos(U, eos, dir: int = -1, out=None, stream=None):
+def flux_eos(U, eos, dir: int = -1, out=None, stream=None, dw: bool = False):
     D = _dim(U)
     n, dt, dev = _info(U)
     F = out if out is not None else _alloc((D + 2) * (D if dir < 0 else 1), n, dt, dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_flux_eos", pm, D, dir, n, DTYPES[dt], _ptrs(U), _ptrs(F), _stream(dev, stream))
+    capi.call("fdbb_flux_eos", pm, D, dir, n, _code(dt, dw), _ptrs(U), _ptrs(F), _stream(dev, stream))
     return F
 
 
-def flux_jac_eos(U, eos, dir: int, out=None, stream=None):
+def flux_jac_eos(U, eos, dir: int, out=None, stream=None, dw: bool = False):
     D = _dim(U)
     n, dt, dev = _info(U)
     A = out if out is not None else _alloc((D + 2) ** 2, n, dt, dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_flux_jac_eos", pm, D, dir, n, DTYPES[dt], _ptrs(U), _ptrs(A), _stream(dev, stream))
+    capi.call("fdbb_flux_jac_eos", pm, D, dir, n, _code(dt, dw), _ptrs(U), _ptrs(A), _stream(dev, stream))
     return A
 
 
-def char_transform_eos(U, W, eos, dir: int, inverse: bool = False, out=None, stream=None):
+def char_transform_eos(U, W, eos, dir: int, inverse: bool = False, out=None, stream=None, dw: bool = False):
     D = _dim(U)
     n, dt, dev = _info(list(U) + list(W))
     Y = out if out is not None else _alloc(D + 2, n, dt, dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_char_transform_eos", pm, D, dir, n, DTYPES[dt], int(bool(inverse)), _ptrs(U), _ptrs(W),
+    capi.call("fdbb_char_transform_eos", pm, D, dir, n, _code(dt, dw), int(bool(inverse)), _ptrs(U), _ptrs(W),
               _ptrs(Y), _stream(dev, stream))
     return Y
 
 
-def euler_fused_eos(U, W, eos, dir_jac: int = 0, out=None, stream=None):
+def euler_fused_eos(U, W, eos, dir_jac: int = 0, out=None, stream=None, dw: bool = False):
     D = _dim(U)
     nv = D + 2
     n, dt, dev = _info(list(U) + (list(W) if W is not None else []))
@@ -392,35 +451,35 @@ def euler_fused_eos(U, W, eos, dir_jac: int = 0, out=None, stream=None):
                _alloc(nv, n, dt, dev) if W is not None else None)
     F, A, Y = out
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_euler_fused_eos", pm, D, dir_jac, n, DTYPES[dt], _ptrs(U),
+    capi.call("fdbb_euler_fused_eos", pm, D, dir_jac, n, _code(dt, dw), _ptrs(U),
               _ptrs(W) if W is not None else None,
               _ptrs(F) if F is not None else None, _ptrs(A) if A is not None else None,
               _ptrs(Y) if Y is not None else None, _stream(dev, stream))
     return F, A, Y
 
 
-def flux_vjp_eos(U, G, eos, dir: int, out=None, stream=None):
+def flux_vjp_eos(U, G, eos, dir: int, out=None, stream=None, dw: bool = False):
     D = _dim(U)
     n, dt, dev = _info(list(U) + list(G))
     gU = out if out is not None else _alloc(D + 2, n, dt, dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_flux_vjp_eos", pm, D, dir, n, DTYPES[dt], _ptrs(U), _ptrs(G), _ptrs(gU), _stream(dev, stream))
+    capi.call("fdbb_flux_vjp_eos", pm, D, dir, n, _code(dt, dw), _ptrs(U), _ptrs(G), _ptrs(gU), _stream(dev, stream))
     return gU
 
 
-def flux_prim_eos(V, eos, dir: int = -1, out=None, stream=None):
+def flux_prim_eos(V, eos, dir: int = -1, out=None, stream=None, dw: bool = False):
     D = _dim(V)
     n, dt, dev = _info(V)
     F = out if out is not None else _alloc((D + 2) * (D if dir < 0 else 1), n, dt, dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_flux_prim_eos", pm, D, dir, n, DTYPES[dt], _ptrs(V), _ptrs(F), _stream(dev, stream))
+    capi.call("fdbb_flux_prim_eos", pm, D, dir, n, _code(dt, dw), _ptrs(V), _ptrs(F), _stream(dev, stream))
     return F
 
 
-def flux_jac_prim_eos(V, eos, dir: int, out=None, stream=None):
+def flux_jac_prim_eos(V, eos, dir: int, out=None, stream=None, dw: bool = False):
     D = _dim(V)
     n, dt, dev = _info(V)
     B = out if out is not None else _alloc((D + 2) ** 2, n, dt, dev)
     m, pm = _eos_ref(eos)
-    capi.call("fdbb_flux_jac_prim_eos", pm, D, dir, n, DTYPES[dt], _ptrs(V), _ptrs(B), _stream(dev, stream))
+    capi.call("fdbb_flux_jac_prim_eos", pm, D, dir, n, _code(dt, dw), _ptrs(V), _ptrs(B), _stream(dev, stream))
     return B

@@ -18,6 +18,7 @@ STATUS = {
     4: "FDBB_ERR_DTYPE", 5: "FDBB_ERR_CUDA", 6: "FDBB_ERR_TIMEOUT", 7: "FDBB_ERR_NOMEM",
 }
 FDBB_F64, FDBB_F32, FDBB_F16, FDBB_BF16, FDBB_F64_DW = 0, 1, 2, 3, 4
+FDBB_PTR_OTHER, FDBB_PTR_DEVICE, FDBB_PTR_HOST, FDBB_PTR_MANAGED = 0, 1, 2, 3
 
 _i, _i64, _d, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)
@@ -33,6 +34,7 @@ SIGNATURES = {
     "fdbb_flux_jac": [_i, _i, _d, _i64, _i, _PP, _PP, _vp],
     "fdbb_char_transform": [_i, _i, _d, _i64, _i, _i, _PP, _PP, _PP, _vp],
     "fdbb_euler_fused": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _PP, _PP, _vp],
+    "fdbb_euler_fused_host": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _PP, _PP, _vp],
     "fdbb_flux_vjp": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _vp],
     "fdbb_roe_flux": [_i, _i, _d, _i64, _i, _PP, _PP, _PP, _vp],
     "fdbb_flux_prim": [_i, _i, _d, _i64, _i, _PP, _PP, _vp],
@@ -125,6 +127,8 @@ def lib():
         L.fdbb_version.restype = _i
         L.fdbb_device_status.argtypes = []
         L.fdbb_device_status.restype = _i
+        L.fdbb_pointer_kind.argtypes = [_vp]
+        L.fdbb_pointer_kind.restype = _i
         _lib = L
     return _lib
 
@@ -148,4 +152,4 @@ def status_string(status: int) -> str:
 
 
 def exported_symbols():
-    return ["fdbb_status_string", "fdbb_version", "fdbb_device_status", *SIGNATURES.keys()]
+    return ["fdbb_status_string", "fdbb_version", "fdbb_device_status", "fdbb_pointer_kind", *SIGNATURES.keys()]

@@ -101,7 +101,18 @@ void set_eos_args(KArgs& a, const fdbb_eos_model& m) {
   for (int i = 0; i < 8; ++i) {
     a.ke[i] = ke[i];
     a.kef[i] = static_cast<float>(ke[i]);
+    a.kel[i] = static_cast<float>(ke[i] - static_cast<double>(a.kef[i]));
   }
+}
+
+// The double-word form needs every EOS parameter 0 or of magnitude in
+// [2^-24, 2^24] (the range of its fast path); otherwise IEEE double is used.
+bool eos_args_dw_range(const KArgs& a) {
+  for (int i = 0; i < 8; ++i) {
+    const double x = std::fabs(a.ke[i]);
+    if (x != 0.0 && !(x >= 0x1p-24 && x <= 0x1p24)) return false;
+  }
+  return true;
 }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
@@ -118,6 +129,19 @@ fdbb_status check_eos(const fdbb_eos_model* m) {
   return FDBB_OK;
 }
 
+// Double-word general-EOS kernels, by model and dim.
+cudaError_t dispatch_eos_f64dw(const LaunchReq& r, const KArgs& a) {
+  using fdbb::EosKind;
+  const bool nasg = r.eos == EosKind::Nasg;
+  if (r.eos != EosKind::Nasg && r.eos != EosKind::Vdw) return cudaErrorInvalidValue;
+  switch (r.dim) {
+    case 1: return nasg ? fdbb::dispatch_eos_f64dw_nasg1(r, a) : fdbb::dispatch_eos_f64dw_vdw1(r, a);
+    case 2: return nasg ? fdbb::dispatch_eos_f64dw_nasg2(r, a) : fdbb::dispatch_eos_f64dw_vdw2(r, a);
+    case 3: return nasg ? fdbb::dispatch_eos_f64dw_nasg3(r, a) : fdbb::dispatch_eos_f64dw_vdw3(r, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Launch op for storage type t under the equation of state `eos`.
 fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, KArgs& a, fdbb_stream_t stream,
                    fdbb::EosKind eos = fdbb::EosKind::Ideal) {
@@ -130,6 +154,7 @@ fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, KArgs& a, fdbb_str
   if (eos != fdbb::EosKind::Ideal) {
     switch (t) {
       case FDBB_F64: e = fdbb::dispatch_eos_f64(r, a); break;
+      case FDBB_F64_DW: e = eos_args_dw_range(a) ? dispatch_eos_f64dw(r, a) : fdbb::dispatch_eos_f64(r, a); break;
       case FDBB_F32: e = fdbb::dispatch_eos_f32(r, a); break;
       default: return FDBB_ERR_DTYPE;
     }
@@ -139,7 +164,11 @@ fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, KArgs& a, fdbb_str
       case FDBB_F32: e = fdbb::dispatch_f32(r, a); break;
       case FDBB_F16: e = fdbb::dispatch_f16(r, a); break;
       case FDBB_BF16: e = fdbb::dispatch_bf16(r, a); break;
-      case FDBB_F64_DW: e = fdbb::dispatch_f64dw(r, a); break;
+      case FDBB_F64_DW:
+        e = r.dim == 1 ? fdbb::dispatch_f64dw_d1(r, a)
+            : r.dim == 2 ? fdbb::dispatch_f64dw_d2(r, a)
+                         : fdbb::dispatch_f64dw_d3(r, a);
+        break;
     }
   }
   return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
@@ -219,7 +248,7 @@ fdbb_status eos_prologue(const fdbb_eos_model* eos, int dim, int64_t n, fdbb_dty
   FDBB_TRY(check_dtype(t));
   ideal = eos->kind == FDBB_EOS_IDEAL;
   if (ideal) return FDBB_OK;
-  if (t != FDBB_F64 && t != FDBB_F32) return FDBB_ERR_DTYPE;
+  if (t != FDBB_F64 && t != FDBB_F32 && t != FDBB_F64_DW) return FDBB_ERR_DTYPE;
   a = make_args(n, eos->gamma, eos->cv);
   set_eos_args(a, *eos);
   return FDBB_OK;
@@ -249,10 +278,34 @@ const char* fdbb_status_string(fdbb_status s) {
 
 int fdbb_version(void) { return 100; }
 
+fdbb_ptr_kind fdbb_pointer_kind(const void* p) {
+  if (p == nullptr) return FDBB_PTR_OTHER;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return FDBB_PTR_OTHER;
+  }
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return FDBB_PTR_OTHER;
+  }
+  switch (at.type) {
+    case cudaMemoryTypeDevice: return at.device == cur ? FDBB_PTR_DEVICE : FDBB_PTR_OTHER;
+    case cudaMemoryTypeManaged: return FDBB_PTR_MANAGED;
+    case cudaMemoryTypeHost: return at.devicePointer == p ? FDBB_PTR_HOST : FDBB_PTR_OTHER;
+    default: return FDBB_PTR_OTHER;
+  }
+}
+
 fdbb_status fdbb_device_status(void) {
   const unsigned int n = fdbb::wait_timeouts_f64() + fdbb::wait_timeouts_f32() + fdbb::wait_timeouts_f16() +
-                         fdbb::wait_timeouts_bf16() + fdbb::wait_timeouts_f64dw() +
-                         fdbb::wait_timeouts_eos_f64() + fdbb::wait_timeouts_eos_f32();
+                         fdbb::wait_timeouts_bf16() + fdbb::wait_timeouts_f64dw_d1() +
+                         fdbb::wait_timeouts_f64dw_d2() + fdbb::wait_timeouts_f64dw_d3() +
+                         fdbb::wait_timeouts_eos_f64() + fdbb::wait_timeouts_eos_f32() +
+                         fdbb::wait_timeouts_eos_f64dw_nasg1() + fdbb::wait_timeouts_eos_f64dw_nasg2() +
+                         fdbb::wait_timeouts_eos_f64dw_nasg3() + fdbb::wait_timeouts_eos_f64dw_vdw1() +
+                         fdbb::wait_timeouts_eos_f64dw_vdw2() + fdbb::wait_timeouts_eos_f64dw_vdw3();
   return n ? FDBB_ERR_TIMEOUT : FDBB_OK;
 }
 
@@ -355,6 +408,27 @@ fdbb_status fdbb_euler_fused(int dim, int dir_jac, double gamma, int64_t n, fdbb
   FDBB_TRY(check_dtype(t));
   KArgs a = make_args(n, gamma);
   FDBB_TRY(fill_fused(a, dim, U, W, F, A, Y));
+  return launch(t, OpKind::Fused, dim, dir_jac, a, stream);
+}
+
+fdbb_status fdbb_euler_fused_host(int dim, int dir_jac, double gamma, int64_t n, fdbb_dtype t,
+                                  const void* const* U, const void* const* W, void* const* F, void* const* A,
+                                  void* const* Y, fdbb_stream_t stream) {
+  FDBB_TRY(check_dims(dim, n));
+  if (!dir_ok(dim, dir_jac, false)) return FDBB_ERR_ARG;
+  FDBB_TRY(check_gamma(gamma));
+  FDBB_TRY(check_dtype(t));
+  KArgs a = make_args(n, gamma);
+  FDBB_TRY(fill_fused(a, dim, U, W, F, A, Y));
+  if (n == 0) return FDBB_OK;
+  for (int i = 0; i < fdbb::kMaxIn; ++i) {
+    if (a.in[i] == nullptr) continue;
+    const fdbb_ptr_kind k = fdbb_pointer_kind(a.in[i]);
+    if (k == FDBB_PTR_OTHER) return FDBB_ERR_ARG;
+    if (k != FDBB_PTR_DEVICE) a.flags |= fdbb::kDirectOnly;
+  }
+  for (int i = 0; i < fdbb::kMaxOut; ++i)
+    if (a.out[i] != nullptr && fdbb_pointer_kind(a.out[i]) == FDBB_PTR_OTHER) return FDBB_ERR_ARG;
   return launch(t, OpKind::Fused, dim, dir_jac, a, stream);
 }
 

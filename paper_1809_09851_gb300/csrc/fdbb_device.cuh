@@ -367,6 +367,9 @@ __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
     s.H = (s.rE + s.p) * s.r;
     s.c2 = fma_(s.G * s.p, s.r, P.dr);
     s.ph = fma_(s.G, s.q - s.ie, P.dr);
+    g.check(s.ie);
+    g.check(s.G);
+    g.check(s.ph);
   }
 #pragma unroll
   for (int i = 0; i < D; ++i) g.check(s.v[i]);
@@ -526,6 +529,8 @@ __device__ __forceinline__ void derive_prim(Pt<R, D>& s, const K& k, G& g) {
     s.rE = Z.v + s.rq;
     s.zr = Z.dr;
     s.zp = Z.de;
+    g.check(s.zr);
+    g.check(s.zp);
   }
   g.check(s.q);
   g.check(s.rE);

@@ -21,6 +21,7 @@
 // with `make`, and list it in the EOS dispatcher (kern_eos_*.cu).
 #pragma once
 
+#include "fdbb_dw.cuh"
 #include "fdbb_internal.h"
 
 namespace fdbb {
@@ -101,6 +102,7 @@ template <class R> struct EosVdw {
 template <class R> __device__ __forceinline__ R eos_param(const KArgs& a, int k);
 template <> __device__ __forceinline__ double eos_param<double>(const KArgs& a, int k) { return a.ke[k]; }
 template <> __device__ __forceinline__ float eos_param<float>(const KArgs& a, int k) { return a.kef[k]; }
+template <> __device__ __forceinline__ dw eos_param<dw>(const KArgs& a, int k) { return dw(a.kef[k], a.kel[k]); }
 
 // Model tags: the per-point model type for compute type R and its
 // construction from the kernel's parameter block.

@@ -13,12 +13,18 @@ constexpr int kMaxOut = 45;  // fused 3D: 15 flux + 25 Jacobian + 5 characterist
 enum class OpKind { VMag2, Prim, Cons, Eos, Riemann, Flux, FluxAll, Jac, CharFwd, CharInv, Fused, Vjp, RoeFlux,
                     RoeCharFwd, RoeCharInv, FluxPrim, FluxPrimAll, JacPrim, Temp };
 
+// KArgs::flags: run the direct kernel (plain global loads) even where the
+// staged one (bulk copies into shared memory) would be chosen -- for inputs in
+// host memory, which the kernels read over the CPU-GPU link.
+constexpr int kDirectOnly = 1;
+
 // Kernel parameter block (passed by value as a __grid_constant__).
 struct KArgs {
   const void* in[kMaxIn];
   void* out[kMaxOut];
   int64_t n;
   int nin;       // input planes in use (the leading non-NULL entries of in[])
+  int flags;     // launch options (kDirectOnly); not read by the kernels
   double kd[8];  // gamma, gamma-1, 3-gamma, 2/(gamma-1), 1/(gamma-1), -gamma,
                  // gamma/(gamma-1), 1/((gamma-1) c_v)
   float kf[8];   // the same, rounded once to float
@@ -26,6 +32,7 @@ struct KArgs {
   double ke[8];  // general EOS parameters (slots: gamma-1, 1/(gamma-1), b, 1/c_v,
                  // p_inf, q, gamma p_inf, a); unused by the ideal-gas kernels
   float kef[8];  // the same, rounded once to float
+  float kel[8];  // ke - kef rounded to float: (kef, kel) is the double-word parameter
 };
 
 // Equation of state of a launch: the ideal gas (gamma in kd/kf/kl) or one of
@@ -48,9 +55,20 @@ cudaError_t dispatch_f64(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f32(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f16(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_bf16(const LaunchReq& r, const KArgs& a);
-cudaError_t dispatch_f64dw(const LaunchReq& r, const KArgs& a);
-// General-EOS blocks (r.eos != Ideal), double and float storage.
+// (double-word: one translation unit per dim)
+cudaError_t dispatch_f64dw_d1(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_f64dw_d2(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_f64dw_d3(const LaunchReq& r, const KArgs& a);
+// General-EOS blocks (r.eos != Ideal): double storage in IEEE double and in
+// double-word arithmetic, float storage.
 cudaError_t dispatch_eos_f64(const LaunchReq& r, const KArgs& a);
+// (double-word: one translation unit per model and dim)
+cudaError_t dispatch_eos_f64dw_nasg1(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_eos_f64dw_nasg2(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_eos_f64dw_nasg3(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_eos_f64dw_vdw1(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_eos_f64dw_vdw2(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_eos_f64dw_vdw3(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_eos_f32(const LaunchReq& r, const KArgs& a);
 
 // Bounded device waits that ran out since the last call, per translation unit
@@ -59,8 +77,16 @@ unsigned int wait_timeouts_f64();
 unsigned int wait_timeouts_f32();
 unsigned int wait_timeouts_f16();
 unsigned int wait_timeouts_bf16();
-unsigned int wait_timeouts_f64dw();
+unsigned int wait_timeouts_f64dw_d1();
+unsigned int wait_timeouts_f64dw_d2();
+unsigned int wait_timeouts_f64dw_d3();
 unsigned int wait_timeouts_eos_f64();
+unsigned int wait_timeouts_eos_f64dw_nasg1();
+unsigned int wait_timeouts_eos_f64dw_nasg2();
+unsigned int wait_timeouts_eos_f64dw_nasg3();
+unsigned int wait_timeouts_eos_f64dw_vdw1();
+unsigned int wait_timeouts_eos_f64dw_vdw2();
+unsigned int wait_timeouts_eos_f64dw_vdw3();
 unsigned int wait_timeouts_eos_f32();
 
 }  // namespace fdbb

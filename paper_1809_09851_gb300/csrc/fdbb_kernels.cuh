@@ -697,20 +697,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // Kernels
 // ---------------------------------------------------------------------------
 
-template <class Op, class T, class R, class K, class Src>
+template <class Op, class T, class R, class Mdl, class K, class Src>
 __device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Src& src, int64_t i0, int cnt) {
   constexpr int VW = Width<T, R>::VW;
   if constexpr (std::is_same<R, dw>::value) {
     // double-word fast path; chunks outside its range run in native FP64
     if (!Op::template apply<T, VW, dw>(a, k, src, i0, cnt))
-      Op::template apply<T, VW, double>(a, consts<double>(a), src, i0, cnt);
+      Op::template apply<T, VW, double>(a, Mdl::template make<double>(a), src, i0, cnt);
   } else {
     Op::template apply<T, VW, R>(a, k, src, i0, cnt);
   }
 }
 
 // Chunks [ch0, nchunk) of VW points read straight from global memory.
-template <class Op, class T, class R, class K>
+template <class Op, class T, class R, class Mdl, class K>
 __device__ __forceinline__ void global_chunks(const KArgs& a, const K& k, int64_t ch0) {
   constexpr int VW = Width<T, R>::VW;
   const int64_t nchunk = (a.n + VW - 1) / VW;
@@ -719,13 +719,13 @@ __device__ __forceinline__ void global_chunks(const KArgs& a, const K& k, int64_
     const int64_t i0 = ch * VW;
     const int cnt = (a.n - i0 < VW) ? (int)(a.n - i0) : VW;
     const GlobalSrc<T, VW> src{a, i0, cnt};
-    apply_chunk<Op, T, R>(a, k, src, i0, cnt);
+    apply_chunk<Op, T, R, Mdl>(a, k, src, i0, cnt);
   }
 }
 
 template <class Op, class T, class R, class Mdl>
 __global__ void __launch_bounds__(kThreads) k_pointwise(const __grid_constant__ KArgs a) {
-  global_chunks<Op, T, R>(a, Mdl::template make<R>(a), 0);
+  global_chunks<Op, T, R, Mdl>(a, Mdl::template make<R>(a), 0);
 }
 
 template <class Op, class T, class R, class Mdl>
@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KAr
     if (__syncthreads_or(!ok)) break;
     const SmemSrc<T, VW, TILE> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW};
     const int64_t i0 = (blockIdx.x + (int64_t)j * gridDim.x) * TILE + (int64_t)tid * VW;
-    apply_chunk<Op, T, R>(a, k, src, i0, VW);
+    apply_chunk<Op, T, R, Mdl>(a, k, src, i0, VW);
     __syncthreads();  // the whole block is done with stage s: refill it
     if (tid == 0 && has_tile(j + kStages)) {
       fence_proxy_async();
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KAr
     return;
   }
   // the ragged tail (fewer than TILE points) straight from global memory
-  global_chunks<Op, T, R>(a, k, ntiles * kThreads);
+  global_chunks<Op, T, R, Mdl>(a, k, ntiles * kThreads);
 }
 
 // Host: read and clear the timeout count of this translation unit.
@@ -844,12 +844,15 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
 }
 
 // The staged kernel pays off once every SM has a few tiles to stream, and
-// while its two-stage ring leaves room for more than one block per SM.
+// while its two-stage ring leaves room for more than one block per SM; its
+// bulk copies read device memory only (inputs in host memory take the direct
+// kernel, kDirectOnly).
 template <class Op, class T, class R, class Mdl = IdealModel>
 cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
   constexpr int TILE = kThreads * Width<T, R>::VW;
   const size_t ring = (size_t)kStages * a.nin * TILE * sizeof(T);
-  if (a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn && ring <= (100u << 10))
+  if (!(a.flags & kDirectOnly) && a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn &&
+      ring <= (100u << 10))
     return launch_staged<Op, T, R, Mdl>(a, stream);
   return launch_direct<Op, T, R, Mdl>(a, stream);
 }
@@ -932,8 +935,8 @@ template <class T, class R> cudaError_t dispatch(const LaunchReq& r, const KArgs
   }
 }
 
-// General-EOS blocks for EOS model Mdl, storage T computed in T's own IEEE
-// type: every block whose formulas the EOS enters, except the Riemann
+// General-EOS blocks for EOS model Mdl, storage T computed in R (T's own IEEE
+// type, or double-word for double): every block whose formulas the EOS enters, except the Riemann
 // invariants and the Roe-averaged forms, which have no closed form for a
 // general EOS.
 template <int D, class T, class R, class Mdl> cudaError_t dispatch_eos_dim(const LaunchReq& r, const KArgs& a) {
@@ -963,10 +966,19 @@ template <int D, class T, class R, class Mdl> cudaError_t dispatch_eos_dim(const
     FDBB_EOS_DIR_CASES(OpKind::FluxPrim, OpFluxPrim)
     FDBB_EOS_DIR_CASES(OpKind::JacPrim, OpJacPrim)
     FDBB_EOS_DIR_CASES(OpKind::CharFwd, OpCharFwd)
-    FDBB_EOS_DIR_CASES(OpKind::CharInv, OpCharInv)
     default: break;
   }
 #undef FDBB_EOS_DIR_CASES
+  // the inverse transform adds input components directly: IEEE arithmetic
+  // for double-word, as for the ideal gas
+  using RI = typename std::conditional<std::is_same<R, dw>::value, double, R>::type;
+  if (r.op == OpKind::CharInv) {
+    if (d == 0) return launch_op<OpCharInv<D, 0>, T, RI, Mdl>(a, r.stream);
+    if constexpr (D > 1)
+      if (d == 1) return launch_op<OpCharInv<D, (D > 1 ? 1 : 0)>, T, RI, Mdl>(a, r.stream);
+    if constexpr (D > 2)
+      if (d == 2) return launch_op<OpCharInv<D, (D > 2 ? 2 : 0)>, T, RI, Mdl>(a, r.stream);
+  }
   return cudaErrorInvalidValue;
 }
 

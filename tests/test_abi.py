@@ -109,8 +109,8 @@ def test_general_eos_argument_errors(L):
     assert L.fdbb_flux_eos(_eos(), 4, 0, 10, F64, _U(6), _U(6), None) == 1
     assert L.fdbb_flux_jac_eos(_eos(), 2, -1, 10, F64, _U(4), _U(16), None) == 1
     assert L.fdbb_prim_from_cons_eos(_eos(), 3, -1, F64, _U(5), _U(5), None) == 1
-    # the general models take float64 and float32 planes only
-    for t in (capi.FDBB_F16, capi.FDBB_BF16, capi.FDBB_F64_DW):
+    # the general models take float64 (IEEE or double-word) and float32 planes only
+    for t in (capi.FDBB_F16, capi.FDBB_BF16):
         assert L.fdbb_flux_eos(_eos(), 3, 0, 10, t, _U(5), _U(5), None) == 4
     assert L.fdbb_flux_eos(_eos(), 3, 0, 10, 9, _U(5), _U(5), None) == 4
     # NULL / misaligned planes, W required for Y in the fused pass
@@ -130,3 +130,11 @@ def test_general_eos_empty_input_is_a_no_op(L):
         assert L.fdbb_euler_fused_eos(m, 3, 1, 0, capi.FDBB_F64, _U(5), _U(5), _U(15), _U(25), _U(5), None) == 0
         assert L.fdbb_cons_from_prim_eos(m, 2, 0, capi.FDBB_F32, _U(4), _U(4), None) == 0
         assert L.fdbb_flux_jac_prim_eos(m, 1, 0, 0, capi.FDBB_F64, _U(3), _U(9), None) == 0
+
+
+def test_pointer_kind_of_host_memory(L):
+    """NULL and pageable host memory are never plane memory the device can use
+    (on a machine without a GPU every query answers FDBB_PTR_OTHER)."""
+    buf = ctypes.create_string_buffer(64)
+    assert L.fdbb_pointer_kind(None) == capi.FDBB_PTR_OTHER
+    assert L.fdbb_pointer_kind(ctypes.addressof(buf)) == capi.FDBB_PTR_OTHER

@@ -4,8 +4,9 @@ Two equations of state stand in for a user EOS (paper section 2.2,
 "Equations of state"): the Noble-Abel stiffened gas and the van der Waals
 gas, on the workload ``synth.euler_eos``.  FP64 storage: |gpu - oracle| <=
 1e-12 * S (S the oracle's running-error scale; S == 0 only for exact copies,
-which must be bit-equal).  FP32 storage (float arithmetic): the oracle runs on
-the dequantised inputs and |gpu - oracle| <= 2^-24 |oracle| + 64 * 2^-24 * S.
+which must be bit-equal).  FP64 storage in double-word arithmetic
+meets the same FP64 bound.  FP32 storage (float arithmetic): the oracle runs
+on the dequantised inputs and |gpu - oracle| <= 2^-24 |oracle| + 64 * 2^-24 * S.
 """
 import ctypes
 
@@ -22,6 +23,8 @@ DEV = "cuda:0"
 MODELS = [synth.EOS_NASG, synth.EOS_VDW]
 IDS = ["nasg", "vdw"]
 SIZES = [1, 7, 513, 65539]
+# storage / arithmetic forms: (dtype, double-word)
+FORMS = {"f64": (torch.float64, False), "f64dw": (torch.float64, True), "f32": (torch.float32, False)}
 U_STORE = {torch.float64: 0.0, torch.float32: 2.0 ** -24}
 TOL = {torch.float64: 1e-12, torch.float32: 64 * 2.0 ** -24}
 
@@ -66,62 +69,84 @@ def case(eos, n, D, dtype, seed=1809):
     return (U, V, W, G), (Ud, Vd, Wd, Gd)
 
 
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("eos", MODELS, ids=IDS)
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("D", [1, 2, 3])
-def test_pointwise_state_blocks(D, n, eos, dtype):
+def test_pointwise_state_blocks(D, n, eos, form):
+    dtype, dw = FORMS[form]
     (U, V, W, G), (Ud, Vd, Wd, Gd) = case(eos, n, D, dtype)
     ref, S = oracle.eos_prim_from_cons(eos, D, U, scale=True)
-    check(host(blocks.prim_from_cons_eos(Ud, eos)), ref, S, dtype, "prim_from_cons")
+    check(host(blocks.prim_from_cons_eos(Ud, eos, dw=dw)), ref, S, dtype, "prim_from_cons")
     ref, S = oracle.eos_cons_from_prim(eos, D, V, scale=True)
-    check(host(blocks.cons_from_prim_eos(Vd, eos)), ref, S, dtype, "cons_from_prim")
+    check(host(blocks.cons_from_prim_eos(Vd, eos, dw=dw)), ref, S, dtype, "cons_from_prim")
     ref, S = oracle.eos_pc(eos, D, U, scale=True)
-    check(host(blocks.pressure_eos(Ud, eos)), ref, S, dtype, "p, c")
+    check(host(blocks.pressure_eos(Ud, eos, dw=dw)), ref, S, dtype, "p, c")
     ref, S = oracle.eos_temperature(eos, D, U, scale=True)
-    check(host([blocks.temperature_eos(Ud, eos)]), ref, S, dtype, "T")
+    check(host([blocks.temperature_eos(Ud, eos, dw=dw)]), ref, S, dtype, "T")
     ref, S = oracle.eos_flux(eos, D, -1, U, scale=True)
-    check(host(blocks.flux_eos(Ud, eos, -1)), ref, S, dtype, "flux all")
+    check(host(blocks.flux_eos(Ud, eos, -1, dw=dw)), ref, S, dtype, "flux all")
     ref, S = oracle.eos_flux_prim(eos, D, -1, V, scale=True)
-    check(host(blocks.flux_prim_eos(Vd, eos, -1)), ref, S, dtype, "flux_prim all")
+    check(host(blocks.flux_prim_eos(Vd, eos, -1, dw=dw)), ref, S, dtype, "flux_prim all")
 
 
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("eos", MODELS, ids=IDS)
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("D", [1, 2, 3])
-def test_directional_blocks(D, n, eos, dtype):
+def test_directional_blocks(D, n, eos, form):
+    dtype, dw = FORMS[form]
     (U, V, W, G), (Ud, Vd, Wd, Gd) = case(eos, n, D, dtype)
     for d in range(D):
         ref, S = oracle.eos_flux(eos, D, d, U, scale=True)
-        check(host(blocks.flux_eos(Ud, eos, d)), ref, S, dtype, f"flux {d}")
+        check(host(blocks.flux_eos(Ud, eos, d, dw=dw)), ref, S, dtype, f"flux {d}")
         ref, S = oracle.eos_flux_jac(eos, D, d, U, scale=True)
-        check(host(blocks.flux_jac_eos(Ud, eos, d)), ref, S, dtype, f"flux_jac {d}")
+        check(host(blocks.flux_jac_eos(Ud, eos, d, dw=dw)), ref, S, dtype, f"flux_jac {d}")
         for inv in (False, True):
             ref, S = oracle.eos_char_transform(eos, D, d, U, W, inverse=inv, scale=True)
-            check(host(blocks.char_transform_eos(Ud, Wd, eos, d, inverse=inv)), ref, S, dtype,
+            check(host(blocks.char_transform_eos(Ud, Wd, eos, d, inverse=inv, dw=dw)), ref, S, dtype,
                   f"char {'inv' if inv else 'fwd'} {d}")
         ref, S = oracle.eos_flux_vjp(eos, D, d, U, G, scale=True)
-        check(host(blocks.flux_vjp_eos(Ud, Gd, eos, d)), ref, S, dtype, f"vjp {d}")
+        check(host(blocks.flux_vjp_eos(Ud, Gd, eos, d, dw=dw)), ref, S, dtype, f"vjp {d}")
         ref, S = oracle.eos_euler_fused(eos, D, d, U, W, scale=True)
-        F, A, Y = blocks.euler_fused_eos(Ud, Wd, eos, d)
+        F, A, Y = blocks.euler_fused_eos(Ud, Wd, eos, d, dw=dw)
         check(host(F + A + Y), ref, S, dtype, f"fused {d}")
         ref, S = oracle.eos_flux_prim(eos, D, d, V, scale=True)
-        check(host(blocks.flux_prim_eos(Vd, eos, d)), ref, S, dtype, f"flux_prim {d}")
+        check(host(blocks.flux_prim_eos(Vd, eos, d, dw=dw)), ref, S, dtype, f"flux_prim {d}")
         ref, S = oracle.eos_flux_jac_prim(eos, D, d, V, scale=True)
-        check(host(blocks.flux_jac_prim_eos(Vd, eos, d)), ref, S, dtype, f"flux_jac_prim {d}")
+        check(host(blocks.flux_jac_prim_eos(Vd, eos, d, dw=dw)), ref, S, dtype, f"flux_jac_prim {d}")
 
 
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("eos", MODELS, ids=IDS)
-def test_fused_staged_path(eos, dtype):
+def test_fused_staged_path(eos, form):
     """Large enough for the staged (bulk-copy) kernel: >= 4 tiles per SM, plus a ragged tail."""
+    dtype, dw = FORMS[form]
     n = (1 << 20) + 5
     (U, V, W, G), (Ud, Vd, Wd, Gd) = case(eos, n, 3, dtype, seed=77)
     ref, S = oracle.eos_euler_fused(eos, 3, 0, U, W, scale=True)
-    F, A, Y = blocks.euler_fused_eos(Ud, Wd, eos, 0)
+    F, A, Y = blocks.euler_fused_eos(Ud, Wd, eos, 0, dw=dw)
     check(host(F + A + Y), ref, S, dtype, "fused staged")
     assert capi.lib().fdbb_device_status() == 0
+
+
+def test_double_word_out_of_range_points_and_parameters():
+    """Points outside the double-word range (tiny densities and pressures) are
+    recomputed in IEEE double; parameters outside it make the whole call IEEE
+    double.  Both meet the FP64 bound."""
+    n = 20000
+    for eos in (synth.EOS_NASG, dict(synth.EOS_NASG, p_inf=1e-9), dict(synth.EOS_VDW, a=3e-8)):
+        V = synth.euler_eos(n, 3, seed=91)
+        V[0][::7] *= 1e-9  # rho ~ 1e-9: outside [2^-24, 2^24]
+        if eos["kind"] == "nasg":
+            V[4][::5] *= 1e-9  # p ~ 1e-9 (p + p_inf stays positive)
+        U = oracle.eos_cons_from_prim(eos, 3, V)
+        W = synth.char_weights(n, 5, seed=92)
+        Ud, U = dev(U, torch.float64)
+        Wd, W = dev(W, torch.float64)
+        ref, S = oracle.eos_euler_fused(eos, 3, 1, U, W, scale=True)
+        F, A, Y = blocks.euler_fused_eos(Ud, Wd, eos, 1, dw=True)
+        check(host(F + A + Y), ref, S, torch.float64, f"fused dw {eos}")
 
 
 def test_exact_copies_and_skipped_outputs():
@@ -181,7 +206,8 @@ def test_empty_and_rejected_dtypes():
                                   capi.planes([t.data_ptr() for t in F]), None)
     torch.cuda.synchronize()
     assert st == 0 and all(bool((f == 7.0).all()) for f in F)
-    Uh = [torch.ones(8, dtype=torch.float16, device=DEV) for _ in range(5)]
-    with pytest.raises(capi.FdbbError) as e:
-        blocks.flux_eos(Uh, eos, 0)
-    assert e.value.status == 4
+    for dt in (torch.float16, torch.bfloat16):
+        Uh = [torch.ones(8, dtype=dt, device=DEV) for _ in range(5)]
+        with pytest.raises(capi.FdbbError) as e:
+            blocks.flux_eos(Uh, eos, 0)
+        assert e.value.status == 4
