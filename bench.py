@@ -49,7 +49,7 @@ L2_BYTES = 129 * 2 ** 20
 # for the kernel sources whose hash is recorded beside it.
 # Measured with ncu on N = 2^22 (profiles/fused3d_f64dw_staged_n2e22_full.md):
 # (335.7 MB read + 1448.2 MB written) / 2^22 points; scaled to the launch size.
-NCU_TRAFFIC = {"source_hash": "5e59be38340d9c84", "bytes_per_point": 425.5}
+NCU_TRAFFIC = {"source_hash": "58cf595e016cf164", "bytes_per_point": 425.4}
 
 
 FUSED_KERNEL_SOURCES = ("fdbb_device.cuh", "fdbb_dw.cuh", "fdbb_eos.cuh", "fdbb_kernels.cuh", "fdbb_internal.h",
@@ -241,6 +241,172 @@ def run_general_eos(args, n, W64, out64, stream, dev, world, hbm_peak):
     return res
 
 
+def time_flushed(fn, steps, warmup, stream, flush):
+    """Per-launch CUDA-event times (ms) of fn(); before every timed launch a
+    buffer of twice the L2 size is written, so no launch finds its inputs in L2."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        ev = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_configs(args, dev, stream, hbm_peak):
+    """The other measurement configurations of the blocks:
+    1D N = 65,536 FP64 (19 output planes: V, p, c, w+-, F_x, A_x; L2-resident,
+    latency-bound: per-call device time, eager and as one CUDA graph), the
+    fused 3D pass swept over N = 2^16 .. 2^24 (L2 flushed before each
+    launch), the precision workload at N = 2^25 (5% near vacuum, 5% at
+    Mach 10-50) in every storage form, and the flux VJP at N = 2^24."""
+    import torch
+    from paper_1809_09851_gb300 import blocks, capi, synth
+    L = capi.lib()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    res = {}
+
+    # ---- 1D, N = 65,536 FP64 ------------------------------------------------
+    n1 = 65536
+    V1 = [torch.from_numpy(v).to(dev) for v in synth.euler1d(n1)]
+    U1 = blocks.cons_from_prim(V1, GAMMA)
+    # V (3), p, c, w-, w+, F_x (3), A_x (9): 19 planes
+    outs = [torch.empty(n1, dtype=torch.float64, device=dev) for _ in range(19)]
+    P = lambda ts: capi.planes([t.data_ptr() for t in ts])
+    pU, pV, pF, pA = P(U1), P(outs[0:3]), P(outs[7:10]), P(outs[10:19])
+    assert len(U1) == 3 and len(outs[10:19]) == 9
+    p_, c_, wm, wp = (outs[k].data_ptr() for k in (3, 4, 5, 6))
+    calls = {
+        "prim_from_cons": lambda st: L.fdbb_prim_from_cons(1, GAMMA, n1, capi.FDBB_F64, pU, pV, st),
+        "eos": lambda st: L.fdbb_eos(1, GAMMA, n1, capi.FDBB_F64, pU, p_, c_, st),
+        "riemann_inv": lambda st: L.fdbb_riemann_inv(1, 0, GAMMA, n1, capi.FDBB_F64, pU, wm, wp, None, st),
+        "flux": lambda st: L.fdbb_flux(1, 0, GAMMA, n1, capi.FDBB_F64, pU, pF, st),
+        "flux_jac": lambda st: L.fdbb_flux_jac(1, 0, GAMMA, n1, capi.FDBB_F64, pU, pA, st),
+    }
+    per_call = {}
+    reps = 1000
+    with torch.cuda.stream(stream):
+        st = stream.cuda_stream
+        for name, fn in calls.items():
+            for _ in range(10):
+                assert fn(st) == 0
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for i in range(reps):
+                fn(st)
+                ev[i + 1].record(stream)
+            torch.cuda.synchronize()
+            t = [ev[i].elapsed_time(ev[i + 1]) * 1e3 for i in range(reps)]
+            per_call[name] = {"p50_us": round(pct(t, 50), 2), "p99_us": round(pct(t, 99), 2)}
+        # the five calls back to back, eager and replayed as one CUDA graph
+        step = lambda st: [fn(st) for fn in calls.values()]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            step(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eager_us = e0.elapsed_time(e1) * 1e3 / reps
+    graph_us = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step(torch.cuda.current_stream().cuda_stream)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_us = round(e0.elapsed_time(e1) * 1e3 / reps, 2)
+    except Exception as exc:  # capture unsupported: report the eager numbers only
+        graph_us = f"unavailable: {type(exc).__name__}"
+    res["1d_n65536_f64"] = {"per_call": per_call, "step_eager_us": round(eager_us, 2), "step_graph_us": graph_us,
+                            "gpoints_per_s_eager": round(n1 / eager_us / 1e3, 3),
+                            "gpoints_per_s_graph": round(n1 / graph_us / 1e3, 3) if isinstance(graph_us, float)
+                            else None,
+                            "bytes": "24 B in + 152 B out per point; 11.5 MB in all: L2-resident, launch-bound"}
+    del V1, U1, outs
+
+    # ---- fused 3D pass, N swept ---------------------------------------------
+    sweep = {}
+    for lg in (16, 18, 20, 22, 24):
+        n = 1 << lg
+        U, W = make_fields(n, 1809, dev)
+        for tag, dt, dw in (("f64dw", torch.float64, True), ("f32", torch.float32, False)):
+            Ut = U if dt == torch.float64 else [u.to(dt) for u in U]
+            Wt = W if dt == torch.float64 else [w.to(dt) for w in W]
+            out = tuple([torch.empty(n, dtype=dt, device=dev) for _ in range(k)] for k in (D * NV, NV * NV, NV))
+            t = time_flushed(lambda: blocks.euler_fused(Ut, Wt, 0, GAMMA, out=out, dw=dw), 20, 3, stream, flush)
+            avg = sum(t) / len(t) / 1e3
+            b = (PLANES_IN + PLANES_OUT) * (8 if dt == torch.float64 else 4) * n
+            sweep[f"2^{lg} {tag}"] = {"gpoints_per_s": round(n / avg / 1e9, 3), "us": round(avg * 1e6, 1),
+                                      "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3)}
+            del Ut, Wt, out
+        del U, W
+    torch.cuda.empty_cache()
+    res["fused3d_sweep"] = sweep
+
+    # ---- precision workload, N = 2^25 ---------------------------------------
+    n = 1 << 25
+    case = synth.precision(n)
+    V = [torch.from_numpy(v).to(dev) for v in case.V]
+    c = blocks.eos(blocks.cons_from_prim(V, GAMMA), GAMMA, want_p=False)[1]  # v = 0 at the fast points
+    fast = torch.from_numpy(case.mach > 0).to(dev)
+    mach = torch.from_numpy(case.mach).to(dev)
+    for k in range(3):
+        V[1 + k] = torch.where(fast, mach * c * torch.from_numpy(case.direction[k]).to(dev), V[1 + k])
+    U = blocks.cons_from_prim(V, GAMMA)
+    W = [torch.from_numpy(w).to(dev) for w in synth.char_weights(n, NV, seed=1810)]
+    del V, c, fast, mach, case
+    prec = {}
+    for tag, dt, dw in (("f64dw", torch.float64, True), ("f32", torch.float32, False),
+                        ("f16", torch.float16, False), ("bf16", torch.bfloat16, False)):
+        Ut = U if dt == torch.float64 else [u.to(dt) for u in U]
+        Wt = W if dt == torch.float64 else [w.to(dt) for w in W]
+        out = tuple([torch.empty(n, dtype=dt, device=dev) for _ in range(k)] for k in (D * NV, NV * NV, NV))
+        t = time_flushed(lambda: blocks.euler_fused(Ut, Wt, 0, GAMMA, out=out, dw=dw), 20, 3, stream, flush)
+        avg = sum(t) / len(t) / 1e3
+        b = (PLANES_IN + PLANES_OUT) * torch.empty(0, dtype=dt).element_size() * n
+        prec[tag] = {"gpoints_per_s": round(n / avg / 1e9, 3), "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3)}
+        del Ut, Wt, out
+    prec["workload"] = "2^25 points, 5% near vacuum (rho, p ~ U[1e-4, 1e-3]), 5% at Mach 10-50"
+    prec["stated_err"] = "tests/test_gpu_precision.py (arithmetic and end-to-end error per output)"
+    res["precision_n2e25"] = prec
+    del U, W
+    torch.cuda.empty_cache()
+
+    # ---- flux VJP, N = 2^24 --------------------------------------------------
+    n = 1 << 24
+    U, W = make_fields(n, 1809, dev)
+    G = [torch.from_numpy(g).to(dev) for g in synth.cotangent(n, NV)]
+    vjp = {}
+    for tag, dt, dw in (("f64dw", torch.float64, True), ("f64", torch.float64, False), ("f32", torch.float32, False)):
+        Ut = U if dt == torch.float64 else [u.to(dt) for u in U]
+        Gt = G if dt == torch.float64 else [g.to(dt) for g in G]
+        gU = [torch.empty(n, dtype=dt, device=dev) for _ in range(NV)]
+        t = time_flushed(lambda: blocks.flux_vjp(Ut, Gt, 0, GAMMA, out=gU, dw=dw), 20, 3, stream, flush)
+        avg = sum(t) / len(t) / 1e3
+        b = 15 * (8 if dt == torch.float64 else 4) * n
+        vjp[tag] = {"gpoints_per_s": round(n / avg / 1e9, 3), "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3)}
+        del Ut, Gt, gU
+    res["flux_vjp_n2e24"] = vjp
+    del U, W, G, flush
+    torch.cuda.empty_cache()
+    return res
+
+
 def pct(xs, q):
     xs = sorted(xs)
     k = max(0, min(len(xs) - 1, int(math.ceil(q / 100.0 * len(xs))) - 1))
@@ -340,6 +506,12 @@ def run_gpu(args):
 
     # ---- end to end through host buffers ---------------------------------------
     e2e = None if args.no_e2e else run_e2e(args, U64, W64, out64, stream, dev, world)
+    configs = None
+    if args.only in ("all", "configs") and world == 1:
+        del out64
+        torch.cuda.empty_cache()
+        out64 = None
+        configs = run_configs(args, dev, stream, hbm_peak)
     del out64
     torch.cuda.empty_cache()
     serving = run_serving(args, dev) if (args.serve_requests > 0 and world == 1) else None
@@ -368,6 +540,7 @@ def run_gpu(args):
             "f64_native": f64_native,
             "mixed": extra,
             "general_eos": general_eos,
+            "configs": configs,
             "e2e": e2e,
             "serving": serving,
             "gpu_launches": args.steps,
@@ -575,7 +748,7 @@ def main(argv=None):
     ap.add_argument("--fv-n", type=int, default=128)
     ap.add_argument("--fv-grids", type=int, default=8)
     ap.add_argument("--fv-steps", type=int, default=20)
-    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16", "eos", "fv"], default="all",
+    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16", "eos", "configs", "fv"], default="all",
                     help="storage types to time besides the f64 headline (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
