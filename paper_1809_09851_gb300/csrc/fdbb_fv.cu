@@ -30,7 +30,7 @@ constexpr int kFvThreads = FDBB_FV_TILE;
 // Tiles of the step kernel: a 32 x 8 (x, y) column segment of up to 32 planes.
 constexpr int kBX = 32, kBY = 8, kZSeg = 32;
 constexpr int kSX = kBX + 2, kSY = kBY + 2, kSlots = kSX * kSY;  // plane tile with a one-cell halo
-constexpr int kSlotVals = 23;  // U[5], F_x[5], F_y[5], F_z[5], |v_x|+c, |v_y|+c, |v_z|+c
+constexpr int kSlotVals = 8;  // U[5], p, 1/rho, c
 
 struct FvArgs {
   int ngrids;
@@ -177,8 +177,10 @@ template <class T> struct PlaneTile {
   T v[kSlotVals][kSlots];
 };
 
-// State, the three flux columns and the three wave speeds |v_d| + c of a cell
-// given its conservative values u, into slot `slot` of plane tile P.
+// State, pressure, 1/rho and speed of sound of a cell given its conservative
+// values u, into slot `slot` of plane tile P (each computed once per cell;
+// the faces form the flux columns from them, which keeps the shared-memory
+// traffic per cell at 8 values written and about 6 x 8 read).
 template <class T>
 __device__ __forceinline__ void put_slot(const T (&u)[5], const Consts<T>& k, PlaneTile<T>& P, int slot) {
   Pt<T, 3> s;
@@ -188,17 +190,11 @@ __device__ __forceinline__ void put_slot(const T (&u)[5], const Consts<T>& k, Pl
   s.m[2] = u[3];
   s.rE = u[4];
   fv_derive(s, k);
-  const T c = fv_sqrt(s.c2);
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    P.v[q][slot] = u[q];
-    P.v[5 + q][slot] = flux_comp<3, 0>(s, q);
-    P.v[10 + q][slot] = flux_comp<3, 1>(s, q);
-    P.v[15 + q][slot] = flux_comp<3, 2>(s, q);
-  }
-  P.v[20][slot] = fabs(s.v[0]) + c;
-  P.v[21][slot] = fabs(s.v[1]) + c;
-  P.v[22][slot] = fabs(s.v[2]) + c;
+  for (int q = 0; q < 5; ++q) P.v[q][slot] = u[q];
+  P.v[5][slot] = s.p;
+  P.v[6][slot] = s.r;
+  P.v[7][slot] = fv_sqrt(s.c2);
 }
 
 template <class T>
@@ -214,32 +210,43 @@ template <class T> struct SlotRaw {
   T u[kSlotsPerThread][5];
 };
 
-// Rusanov flux through the face between slot l (left) and slot r (right) in
-// direction d, from plane tiles PL and PR.
-// What a face needs from one side in direction d: U, F_d(U) and |v_d| + c.
+// One cell of a plane tile: U, p, 1/rho and c.
+template <class T> struct Cell {
+  T u[5], p, r, c;
+};
+template <class T> __device__ __forceinline__ Cell<T> cell_at(const PlaneTile<T>& P, int slot) {
+  Cell<T> x;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) x.u[q] = P.v[q][slot];
+  x.p = P.v[5][slot];
+  x.r = P.v[6][slot];
+  x.c = P.v[7][slot];
+  return x;
+}
+
+// What a face needs from one side in direction d: U, F_d(U) (the paper's
+// inviscid flux column, section 2.2, with v = m / rho) and |v_d| + c.
 template <class T> struct Side {
   T u[5], f[5], s;
 };
-template <class T, int d> __device__ __forceinline__ Side<T> side(const PlaneTile<T>& P, int slot) {
+template <class T, int d> __device__ __forceinline__ Side<T> side(const Cell<T>& e) {
   Side<T> x;
+  const T md = e.u[1 + d];
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    x.u[q] = P.v[q][slot];
-    x.f[q] = P.v[5 + 5 * d + q][slot];
+  for (int q = 0; q < 5; ++q) x.u[q] = e.u[q];
+  x.f[0] = md;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T vi = e.u[1 + i] * e.r;
+    x.f[1 + i] = i == d ? fma_(md, vi, e.p) : md * vi;
   }
-  x.s = P.v[20 + d][slot];
+  const T vd = md * e.r;
+  x.f[4] = vd * (e.u[4] + e.p);
+  x.s = fabs(vd) + e.c;
   return x;
 }
-// Same, reusing U already in registers.
-template <class T, int d> __device__ __forceinline__ Side<T> side(const PlaneTile<T>& P, int slot, const T (&u)[5]) {
-  Side<T> x;
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    x.u[q] = u[q];
-    x.f[q] = P.v[5 + 5 * d + q][slot];
-  }
-  x.s = P.v[20 + d][slot];
-  return x;
+template <class T, int d> __device__ __forceinline__ Side<T> side(const PlaneTile<T>& P, int slot) {
+  return side<T, d>(cell_at(P, slot));
 }
 
 // Rusanov flux through the face between the left side L and the right side R.
@@ -256,7 +263,15 @@ __device__ __forceinline__ void face(const Side<T>& L, const Side<T>& R, T (&Fh)
 // computed once) into a double-buffered shared-memory plane, then updates its
 // own cells from the four x/y faces of the current plane and the z faces,
 // carrying the lower z face of the next plane in registers.
-template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_constant__ FvArgs a) {
+// Resident blocks per SM the step kernel is compiled for: four for FP32 grids
+// (the shared-memory plane tiles, 2 x 8 x 340 floats = 21.8 KB, allow it and
+// the kernel is bound by issue and shared-memory latency, so occupancy
+// pays), the compiler's choice for FP64.
+template <class T> struct FvMinBlocks { static constexpr int value = 1; };
+template <> struct FvMinBlocks<float> { static constexpr int value = 4; };
+
+template <class T>
+__global__ void __launch_bounds__(kFvThreads, FvMinBlocks<T>::value) k_fv_rusanov_step(const __grid_constant__ FvArgs a) {
   extern __shared__ __align__(16) unsigned char fv_smem[];
   PlaneTile<T>* tiles = reinterpret_cast<PlaneTile<T>*>(fv_smem);  // [2]
   const Consts<T> k = fv_consts<T>(a.gamma);
@@ -324,20 +339,20 @@ template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_st
       if (z + 1 < z1) load_plane(raw, z + 2 >= n ? z + 2 - n : z + 2);  // prefetch plane z + 2
       __syncthreads();
       if (active) {
-        T lo[5], hi[5], div[5], uc[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) uc[q] = C.v[q][own];  // the cell's own state, read once
-        const Side<T> cx = side<T, 0>(C, own, uc);
+        T lo[5], hi[5], div[5];
+        const Cell<T> me = cell_at(C, own);  // the cell's own state, read once
+        const T(&uc)[5] = me.u;
+        const Side<T> cx = side<T, 0>(me);
         face<T>(side<T, 0>(C, own - 1), cx, lo);
         face<T>(cx, side<T, 0>(C, own + 1), hi);
 #pragma unroll
         for (int q = 0; q < 5; ++q) div[q] = T(0) + (hi[q] - lo[q]);
-        const Side<T> cy = side<T, 1>(C, own, uc);
+        const Side<T> cy = side<T, 1>(me);
         face<T>(side<T, 1>(C, own - kSX), cy, lo);
         face<T>(cy, side<T, 1>(C, own + kSX), hi);
 #pragma unroll
         for (int q = 0; q < 5; ++q) div[q] = div[q] + (hi[q] - lo[q]);
-        face<T>(side<T, 2>(C, own, uc), side<T, 2>(N, own), hi);
+        face<T>(side<T, 2>(me), side<T, 2>(N, own), hi);
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           div[q] = div[q] + (hi[q] - zlo[q]);
