@@ -147,7 +147,7 @@ __device__ __forceinline__ void cell_state(void* const* P, int64_t c, const Cons
 
 template <class T> __device__ __forceinline__ T wave_speed_sum(const Pt<T, 3>& s) {
   const T c = fv_sqrt(s.c2);
-  return (fabs(s.v[0]) + c) + (fabs(s.v[1]) + c) + (fabs(s.v[2]) + c);
+  return (abs_(s.v[0]) + c) + (abs_(s.v[1]) + c) + (abs_(s.v[2]) + c);
 }
 
 template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_max_speed(const __grid_constant__ FvArgs a) {
@@ -242,7 +242,7 @@ template <class T, int d> __device__ __forceinline__ Side<T> side(const Cell<T>&
   }
   const T vd = md * e.r;
   x.f[4] = vd * (e.u[4] + e.p);
-  x.s = fabs(vd) + e.c;
+  x.s = abs_(vd) + e.c;
   return x;
 }
 template <class T, int d> __device__ __forceinline__ Side<T> side(const PlaneTile<T>& P, int slot) {
