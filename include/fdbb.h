@@ -328,11 +328,12 @@ FDBB_API fdbb_status fdbb_roe_char_transform(int dim, int dir, double gamma, int
  * The kernels take the partial derivatives of p(rho, e) and rho e(rho, p)
  * from one evaluation on dual numbers.
  *
- * Storage types: FDBB_F64 (IEEE double), FDBB_F64_DW (double-word, with the
- * same range rule and IEEE fallback as for the ideal gas; if an EOS
- * parameter (gamma - 1, its reciprocal, b, 1/c_v, p_inf, q, gamma p_inf, a)
- * is non-zero and outside [2^-24, 2^24] the call runs in IEEE double) and
- * FDBB_F32 (float) for NASG and VDW; others return FDBB_ERR_DTYPE.  The Riemann invariants and the
+ * Storage types: every one, as for the ideal gas: FDBB_F64 (IEEE double),
+ * FDBB_F64_DW (double-word, with the same range rule and IEEE fallback; if an
+ * EOS parameter (gamma - 1, its reciprocal, b, 1/c_v, p_inf, q, gamma p_inf,
+ * a) is non-zero and outside [2^-24, 2^24] the call runs in IEEE double), and
+ * FDBB_F32 / FDBB_F16 / FDBB_BF16 (float arithmetic with the compensated
+ * internal energy, then the model's formulas in float).  The Riemann invariants and the
  * Roe-averaged forms have no counterpart here (no closed form for a general
  * EOS).  Argument errors (FDBB_ERR_ARG): eos NULL, unknown kind, gamma <= 1,
  * cv <= 0, b < 0, p_inf < 0 (NASG) or a < 0 (VDW).  States with

@@ -156,6 +156,8 @@ fdbb_status launch(fdbb_dtype t, OpKind op, int dim, int dir, KArgs& a, fdbb_str
       case FDBB_F64: e = fdbb::dispatch_eos_f64(r, a); break;
       case FDBB_F64_DW: e = eos_args_dw_range(a) ? dispatch_eos_f64dw(r, a) : fdbb::dispatch_eos_f64(r, a); break;
       case FDBB_F32: e = fdbb::dispatch_eos_f32(r, a); break;
+      case FDBB_F16: e = fdbb::dispatch_eos_f16(r, a); break;
+      case FDBB_BF16: e = fdbb::dispatch_eos_bf16(r, a); break;
       default: return FDBB_ERR_DTYPE;
     }
   } else {
@@ -248,7 +250,6 @@ fdbb_status eos_prologue(const fdbb_eos_model* eos, int dim, int64_t n, fdbb_dty
   FDBB_TRY(check_dtype(t));
   ideal = eos->kind == FDBB_EOS_IDEAL;
   if (ideal) return FDBB_OK;
-  if (t != FDBB_F64 && t != FDBB_F32 && t != FDBB_F64_DW) return FDBB_ERR_DTYPE;
   a = make_args(n, eos->gamma, eos->cv);
   set_eos_args(a, *eos);
   return FDBB_OK;
@@ -303,6 +304,7 @@ fdbb_status fdbb_device_status(void) {
                          fdbb::wait_timeouts_bf16() + fdbb::wait_timeouts_f64dw_d1() +
                          fdbb::wait_timeouts_f64dw_d2() + fdbb::wait_timeouts_f64dw_d3() +
                          fdbb::wait_timeouts_eos_f64() + fdbb::wait_timeouts_eos_f32() +
+                         fdbb::wait_timeouts_eos_f16() + fdbb::wait_timeouts_eos_bf16() +
                          fdbb::wait_timeouts_eos_f64dw_nasg1() + fdbb::wait_timeouts_eos_f64dw_nasg2() +
                          fdbb::wait_timeouts_eos_f64dw_nasg3() + fdbb::wait_timeouts_eos_f64dw_vdw1() +
                          fdbb::wait_timeouts_eos_f64dw_vdw2() + fdbb::wait_timeouts_eos_f64dw_vdw3();

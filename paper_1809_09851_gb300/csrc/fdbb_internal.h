@@ -60,7 +60,7 @@ cudaError_t dispatch_f64dw_d1(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f64dw_d2(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_f64dw_d3(const LaunchReq& r, const KArgs& a);
 // General-EOS blocks (r.eos != Ideal): double storage in IEEE double and in
-// double-word arithmetic, float storage.
+// double-word arithmetic, float / half / bfloat16 storage in float.
 cudaError_t dispatch_eos_f64(const LaunchReq& r, const KArgs& a);
 // (double-word: one translation unit per model and dim)
 cudaError_t dispatch_eos_f64dw_nasg1(const LaunchReq& r, const KArgs& a);
@@ -70,6 +70,8 @@ cudaError_t dispatch_eos_f64dw_vdw1(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_eos_f64dw_vdw2(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_eos_f64dw_vdw3(const LaunchReq& r, const KArgs& a);
 cudaError_t dispatch_eos_f32(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_eos_f16(const LaunchReq& r, const KArgs& a);
+cudaError_t dispatch_eos_bf16(const LaunchReq& r, const KArgs& a);
 
 // Bounded device waits that ran out since the last call, per translation unit
 // (read and cleared; synchronous).
@@ -88,5 +90,7 @@ unsigned int wait_timeouts_eos_f64dw_vdw1();
 unsigned int wait_timeouts_eos_f64dw_vdw2();
 unsigned int wait_timeouts_eos_f64dw_vdw3();
 unsigned int wait_timeouts_eos_f32();
+unsigned int wait_timeouts_eos_f16();
+unsigned int wait_timeouts_eos_bf16();
 
 }  // namespace fdbb

@@ -109,9 +109,7 @@ def test_general_eos_argument_errors(L):
     assert L.fdbb_flux_eos(_eos(), 4, 0, 10, F64, _U(6), _U(6), None) == 1
     assert L.fdbb_flux_jac_eos(_eos(), 2, -1, 10, F64, _U(4), _U(16), None) == 1
     assert L.fdbb_prim_from_cons_eos(_eos(), 3, -1, F64, _U(5), _U(5), None) == 1
-    # the general models take float64 (IEEE or double-word) and float32 planes only
-    for t in (capi.FDBB_F16, capi.FDBB_BF16):
-        assert L.fdbb_flux_eos(_eos(), 3, 0, 10, t, _U(5), _U(5), None) == 4
+    # an unknown storage type
     assert L.fdbb_flux_eos(_eos(), 3, 0, 10, 9, _U(5), _U(5), None) == 4
     # NULL / misaligned planes, W required for Y in the fused pass
     assert L.fdbb_flux_eos(_eos(), 3, 0, 10, F32, None, _U(5), None) == 2

@@ -5,8 +5,10 @@ Two equations of state stand in for a user EOS (paper section 2.2,
 gas, on the workload ``synth.euler_eos``.  FP64 storage: |gpu - oracle| <=
 1e-12 * S (S the oracle's running-error scale; S == 0 only for exact copies,
 which must be bit-equal).  FP64 storage in double-word arithmetic
-meets the same FP64 bound.  FP32 storage (float arithmetic): the oracle runs
-on the dequantised inputs and |gpu - oracle| <= 2^-24 |oracle| + 64 * 2^-24 * S.
+meets the same FP64 bound.  FP32 / FP16 / BF16 storage (float arithmetic):
+the oracle runs on the dequantised inputs and |gpu - oracle| <= u_store
+|oracle| + (half the storage type's subnormal spacing) + 64 * 2^-24 * S, u_store
+the unit roundoff of the storage type.
 """
 import ctypes
 
@@ -24,9 +26,14 @@ MODELS = [synth.EOS_NASG, synth.EOS_VDW]
 IDS = ["nasg", "vdw"]
 SIZES = [1, 7, 513, 65539]
 # storage / arithmetic forms: (dtype, double-word)
-FORMS = {"f64": (torch.float64, False), "f64dw": (torch.float64, True), "f32": (torch.float32, False)}
-U_STORE = {torch.float64: 0.0, torch.float32: 2.0 ** -24}
-TOL = {torch.float64: 1e-12, torch.float32: 64 * 2.0 ** -24}
+FORMS = {"f64": (torch.float64, False), "f64dw": (torch.float64, True), "f32": (torch.float32, False),
+         "f16": (torch.float16, False), "bf16": (torch.bfloat16, False)}
+U_STORE = {torch.float64: 0.0, torch.float32: 2.0 ** -24, torch.float16: 2.0 ** -11, torch.bfloat16: 2.0 ** -8}
+# half the subnormal spacing of the storage type (rounding below its smallest normal number)
+TINY_STORE = {torch.float64: 0.0, torch.float32: 2.0 ** -150, torch.float16: 2.0 ** -25,
+              torch.bfloat16: 2.0 ** -134}
+TOL = {torch.float64: 1e-12, torch.float32: 64 * 2.0 ** -24, torch.float16: 64 * 2.0 ** -24,
+       torch.bfloat16: 64 * 2.0 ** -24}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -50,7 +57,7 @@ def host(planes):
 def check(got, ref, S, dtype, what):
     assert len(got) == len(ref), what
     for c, (g, o, s) in enumerate(zip(got, ref, S)):
-        bound = U_STORE[dtype] * np.abs(o) + TOL[dtype] * s
+        bound = U_STORE[dtype] * np.abs(o) + TINY_STORE[dtype] + TOL[dtype] * s
         ok = np.abs(g - o) <= bound
         if not ok.all():
             i = int(np.argmin(ok))
@@ -206,8 +213,7 @@ def test_empty_and_rejected_dtypes():
                                   capi.planes([t.data_ptr() for t in F]), None)
     torch.cuda.synchronize()
     assert st == 0 and all(bool((f == 7.0).all()) for f in F)
-    for dt in (torch.float16, torch.bfloat16):
-        Uh = [torch.ones(8, dtype=dt, device=DEV) for _ in range(5)]
-        with pytest.raises(capi.FdbbError) as e:
-            blocks.flux_eos(Uh, eos, 0)
-        assert e.value.status == 4
+    # an unknown storage type is refused before any launch
+    st = capi.lib().fdbb_flux_eos(ctypes.byref(m), 3, 0, 8, 9, capi.planes([t.data_ptr() for t in U]),
+                                  capi.planes([t.data_ptr() for t in F[:5]]), None)
+    assert st == 4
