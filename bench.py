@@ -264,8 +264,8 @@ def run_configs(args, dev, stream, hbm_peak):
     """The other measurement configurations of the blocks:
     1D N = 65,536 FP64 (19 output planes: V, p, c, w+-, F_x, A_x; L2-resident,
     latency-bound: per-call device time, eager and as one CUDA graph), the
-    fused 3D pass swept over N = 2^16 .. 2^24 (L2 flushed before each
-    launch), the precision workload at N = 2^25 (5% near vacuum, 5% at
+    fused 3D pass swept over N = 2^16 .. 2^24 and at 2^28 (L2 flushed before
+    each launch), the precision workload at N = 2^25 (5% near vacuum, 5% at
     Mach 10-50) in every storage form, and the flux VJP at N = 2^24."""
     import torch
     from paper_1809_09851_gb300 import blocks, capi, synth
@@ -355,6 +355,21 @@ def run_configs(args, dev, stream, hbm_peak):
                                       "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3)}
             del Ut, Wt, out
         del U, W
+    torch.cuda.empty_cache()
+    # the paper's largest size, N = 2^28 (118 GB of planes in f64): the 2^26
+    # field tiled four times on the device
+    n = 1 << 28
+    U26, W26 = make_fields(1 << 26, 1809, dev)
+    U = [u.repeat(4) for u in U26]
+    W = [w.repeat(4) for w in W26]
+    del U26, W26
+    out = tuple([torch.empty(n, dtype=torch.float64, device=dev) for _ in range(k)] for k in (D * NV, NV * NV, NV))
+    t = time_flushed(lambda: blocks.euler_fused(U, W, 0, GAMMA, out=out, dw=True), 10, 3, stream, flush)
+    avg = sum(t) / len(t) / 1e3
+    b = (PLANES_IN + PLANES_OUT) * 8 * n
+    sweep["2^28 f64dw"] = {"gpoints_per_s": round(n / avg / 1e9, 3), "us": round(avg * 1e6, 1),
+                           "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3), "device_gb": round(b / 1e9, 1)}
+    del U, W, out
     torch.cuda.empty_cache()
     res["fused3d_sweep"] = sweep
 

@@ -105,3 +105,38 @@ def test_vjp_full_size_everywhere(dtype, dw):
         bound = [2.0 ** -24 * np.abs(r) + 64 * 2.0 ** -24 * s for r, s in zip(ref, S)]
     for k in range(5):
         assert np.all(np.abs(gU[k] - ref[k]) <= bound[k]), k
+
+
+@pytest.mark.parametrize("dw", [False, True], ids=["f64", "f64dw"])
+@pytest.mark.parametrize("eos", [synth.EOS_NASG, synth.EOS_VDW], ids=["nasg", "vdw"])
+def test_autograd_under_a_general_eos(eos, dw):
+    """The differentiable flux under a general EOS: gradients equal A_d(U)^T G
+    of the general-EOS oracle (1e-12 * S) and central differences of the GPU
+    flux."""
+    n, D = 3001, 3
+    U = oracle.eos_cons_from_prim(eos, D, synth.euler_eos(n, D, seed=31))
+    Gc = synth.cotangent(n, D + 2, seed=32)
+    for d in range(D):
+        Ud = [u.requires_grad_() for u in _dev(U)]
+        F = autograd.flux(Ud, d, eos=eos, dw=dw)
+        sum((f * g).sum() for f, g in zip(F, _dev(Gc))).backward()
+        got = [u.grad.cpu().numpy() for u in Ud]
+        ref, S = oracle.eos_flux_vjp(eos, D, d, U, Gc, scale=True)
+        for k in range(D + 2):
+            assert np.all(np.abs(got[k] - ref[k]) <= 1e-12 * S[k]), (d, k)
+    # central differences of the GPU flux along U component j, on all points
+    Ud = _dev(U)
+    Gd = _dev(Gc)
+    for j in range(D + 2):
+        h = 1e-6 * torch.clamp(Ud[j].abs(), min=1.0)
+        Up = [u.clone() for u in Ud]
+        Um = [u.clone() for u in Ud]
+        Up[j] += h
+        Um[j] -= h
+        Fp = blocks.flux_eos(Up, eos, 0, dw=dw)
+        Fm = blocks.flux_eos(Um, eos, 0, dw=dw)
+        fd = sum(((a - b) / (2 * h)) * g for a, b, g in zip(Fp, Fm, Gd))
+        Ur = [u.clone().requires_grad_() for u in Ud]
+        sum((f * g).sum() for f, g in zip(autograd.flux(Ur, 0, eos=eos, dw=dw), Gd)).backward()
+        err = (fd - Ur[j].grad).abs().max().item()
+        assert err <= 1e-6 * (1.0 + Ur[j].grad.abs().max().item()), j
