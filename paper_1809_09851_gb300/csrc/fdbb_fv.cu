@@ -302,13 +302,25 @@ __global__ void __launch_bounds__(kFvThreads, FvMinBlocks<T>::value) k_fv_rusano
     }
     const int x = x0 + lx, y = y0 + ly;
     const bool active = x < n && y < n;
-    // this thread's slots of a plane tile: cells with a periodic halo
+    // this thread's slots of a plane tile: cells with a periodic halo; their
+    // (x, y) offsets within a plane are the same for every plane of the tile
+    int64_t slot_off[kSlotsPerThread];
+#pragma unroll
+    for (int j = 0; j < kSlotsPerThread; ++j) {
+      const int sl = tid + j * kFvThreads;
+      const int gx = (x0 + sl % kSX - 1 + n) % n, gy = (y0 + sl / kSX - 1 + n) % n;
+      slot_off[j] = (int64_t)gy * n + gx;
+    }
+    const int64_t plane = (int64_t)n * n;
     auto load_plane = [&](SlotRaw<T>& r, int z) {
+      const int64_t zoff = (int64_t)z * plane;
 #pragma unroll
       for (int j = 0; j < kSlotsPerThread; ++j) {
         const int sl = tid + j * kFvThreads;
-        if (sl < kSlots)
-          load_cell<T>(g, (x0 + sl % kSX - 1 + n) % n, (y0 + sl / kSX - 1 + n) % n, z, r.u[j]);
+        if (sl < kSlots) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q) r.u[j][q] = ldg<T>(g.U[q], zoff + slot_off[j]);
+        }
       }
     };
     auto fill = [&](PlaneTile<T>& P, const SlotRaw<T>& r) {
