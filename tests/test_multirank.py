@@ -57,3 +57,33 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"]) is None
+
+
+def test_reference_arm_json_line(capsys):
+    """Rank 0 of the reference arm: the oracle on a pool of host worker
+    processes, one JSON line with the contract's keys."""
+    import json
+    res = bench.main(["--impl", "reference", "--steps", "2", "--warmup", "1", "--ref-sample", "4096"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line == res
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] >= 1 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_oracle_pool_matches_one_process():
+    """The worker pool runs the unchanged oracle on contiguous shares of the sample."""
+    pool = bench.OraclePool(3000, cores=2)
+    try:
+        assert pool.run(1) > 0
+    finally:
+        pool.close()
+    bench._orc_init(3000, 2)
+    U, W = bench.oracle_sample(3000)
+    whole = oracle.euler_fused(3, 0, 1.4, U, W)
+    parts = [oracle.euler_fused(3, 0, 1.4, *bench._ORC["chunks"][i]) for i in range(2)]
+    for k in range(45):
+        np.testing.assert_array_equal(np.concatenate([parts[0][k], parts[1][k]]), whole[k])
