@@ -13,7 +13,6 @@
 #include <stdint.h>
 
 #include "fdbb_dw.cuh"
-#include "fdbb_eos.cuh"
 
 namespace fdbb {
 
@@ -230,6 +229,13 @@ __device__ __forceinline__ double abs_(double x) { return fabs(x); }
 __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
 __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+
+}  // namespace fdbb
+
+// General EOS models and dual numbers (they use the arithmetic helpers above).
+#include "fdbb_eos.cuh"
+
+namespace fdbb {
 
 // Constants derived from gamma on the host in double, rounded once to R: the
 // ideal-gas model of the per-point formulas (general EOS models, whose

@@ -16,6 +16,9 @@
 // the one formula the model writes.  `kIdeal = false` routes the per-point
 // formulas (fdbb_device.cuh) to their general-EOS forms.
 //
+// This header is included by fdbb_device.cuh after the arithmetic helpers
+// (rcp_, fma_, ...) that the dual numbers use.
+//
 // Adding an EOS: write such a struct (parameters are the members, filled from
 // the eight slots of the kernel's EOS parameter block), give it a model tag
 // with `make`, and list it in the EOS dispatcher (kern_eos_*.cu).
@@ -42,9 +45,11 @@ template <class R> __device__ __forceinline__ D2<R> operator-(const D2<R>& a) { 
 template <class R> __device__ __forceinline__ D2<R> operator*(const D2<R>& a, const D2<R>& b) {
   return {a.v * b.v, a.dr * b.v + a.v * b.dr, a.de * b.v + a.v * b.de};
 }
+// Quotient with one reciprocal: v = a/b, dv = (da - v db) / b.
 template <class R> __device__ __forceinline__ D2<R> operator/(const D2<R>& a, const D2<R>& b) {
-  const R v = a.v / b.v;
-  return {v, (a.dr - v * b.dr) / b.v, (a.de - v * b.de) / b.v};
+  const R ib = rcp_(b.v);
+  const R v = a.v * ib;
+  return {v, (a.dr - v * b.dr) * ib, (a.de - v * b.de) * ib};
 }
 // Mixed with constants of the compute type.
 template <class R> __device__ __forceinline__ D2<R> operator+(const D2<R>& a, R c) { return {a.v + c, a.dr, a.de}; }
