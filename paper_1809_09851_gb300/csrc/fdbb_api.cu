@@ -277,7 +277,7 @@ const char* fdbb_status_string(fdbb_status s) {
   return "unknown status";
 }
 
-int fdbb_version(void) { return 100; }
+int fdbb_version(void) { return 200; }
 
 fdbb_ptr_kind fdbb_pointer_kind(const void* p) {
   if (p == nullptr) return FDBB_PTR_OTHER;
