@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(kThreads) k_pointwise(const __grid_constant__ 
 }
 
 template <class Op, class T, class R, class Mdl>
-__global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KArgs a) {
+__device__ __forceinline__ void staged_body(const KArgs& a) {
   constexpr int VW = Width<T, R>::VW;
   constexpr int TILE = kThreads * VW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -788,6 +788,20 @@ __global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KAr
   global_chunks<Op, T, R, Mdl>(a, k, ntiles * kThreads);
 }
 
+template <class Op, class T, class R, class Mdl>
+__global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KArgs a) {
+  staged_body<Op, T, R, Mdl>(a);
+}
+
+// The general-EOS double-word kernels, compiled for three resident blocks per
+// SM (at most 85 registers per thread; left to itself the compiler takes 90
+// and two blocks fit).
+template <class Op, class T, class R, class Mdl>
+__global__ void __launch_bounds__(kThreads, 3) k_staged3(const __grid_constant__ KArgs a) {
+  staged_body<Op, T, R, Mdl>(a);
+}
+template <class R, class Mdl> constexpr bool kStaged3 = std::is_same<R, dw>::value && !std::is_same<Mdl, IdealModel>::value;
+
 // Host: read and clear the timeout count of this translation unit.
 inline unsigned int take_wait_timeouts_tu() {
   unsigned int v = 0, zero = 0;
@@ -825,21 +839,27 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
   constexpr int VW = Width<T, R>::VW;
   constexpr int TILE = kThreads * VW;
   constexpr size_t kMaxSmem = (size_t)kStages * Op::kIn * TILE * sizeof(T);
+  auto kern = [] {
+    if constexpr (kStaged3<R, Mdl>)
+      return k_staged3<Op, T, R, Mdl>;
+    else
+      return k_staged<Op, T, R, Mdl>;
+  }();
   static const cudaError_t attr =
-      cudaFuncSetAttribute(k_staged<Op, T, R, Mdl>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   if (attr != cudaSuccess) return attr;
   const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T);
   static int bps_cache[Op::kIn + 1] = {};  // blocks per SM for each nin
   int& bps = bps_cache[a.nin];
   if (bps == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_staged<Op, T, R, Mdl>, kThreads, smem) != cudaSuccess) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, smem) != cudaSuccess) b = 1;
     bps = b > 0 ? b : 1;
   }
   const int64_t ntiles = a.n / TILE;
   const int64_t cap = (int64_t)device_sm_count() * bps;
   const int grid = (int)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
-  k_staged<Op, T, R, Mdl><<<grid, kThreads, smem, stream>>>(a);
+  kern<<<grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
