@@ -445,6 +445,22 @@ FDBB_API fdbb_status fdbb_fv_rusanov_step(int ngrids, const fdbb_fv_grid *grids,
                                           fdbb_stream_t stream);
 
 /*
+ * fdbb_fv_init_smooth -- smooth periodic initial state of one grid (the
+ * requests of the serving workload; the paper has no counterpart):
+ *   rho = 1 + amplitude * g_0 / max|g_0|,  v = 0,  p = 1 + amplitude * g_1 / max|g_1|,
+ *   g_r(x) = sum_{m=0..2} a_{r,m} sin(2 pi (k_{r,m} . x) + phi_{r,m}),
+ * at the cell centres x = ((i, j, k) + 1/2) / n, written as conservative
+ * U = (rho, 0, 0, 0, p / (gamma - 1)) into grid->U (only U and n are read).
+ * wave: HOST array of 30 doubles, (k_x, k_y, k_z, phi, a) of sinusoid m of
+ * plane r at wave[15 r + 5 m].  scratch: DEVICE array of two values of the
+ * storage type (the two maxima; overwritten).  Storage FDBB_F32 (evaluated in
+ * float) or FDBB_F64.  One memset and two launches on `stream`.
+ */
+FDBB_API fdbb_status fdbb_fv_init_smooth(const fdbb_fv_grid *grid, double gamma, double amplitude,
+                                         const double *wave, fdbb_dtype t, void *scratch,
+                                         fdbb_stream_t stream);
+
+/*
  * fdbb_fv_rusanov_step_noalloc -- the same step for callers that cannot
  * allocate device memory.  (The paper has no counterpart; this is an
  * interface convenience of this library.)

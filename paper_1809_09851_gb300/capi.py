@@ -59,6 +59,7 @@ SIGNATURES.update({
     "fdbb_fv_max_speed": [_i, _FVP, _i64, _d, _i, _vp, _vp],
     "fdbb_fv_rusanov_step": [_i, _FVP, _i64, _d, _d, _i, _vp, _vp],
     "fdbb_fv_rusanov_step_noalloc": [_i, _FVP, _i64, _d, _d, _i, _vp],
+    "fdbb_fv_init_smooth": [_FVP, _d, _d, _vp, _i, _vp, _vp],
 })
 
 

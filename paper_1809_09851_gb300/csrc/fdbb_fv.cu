@@ -427,6 +427,84 @@ template <class T> cudaError_t fv_launch(const FvArgs& a, bool step, cudaStream_
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Smooth periodic initial state (the serving workload's requests)
+// ---------------------------------------------------------------------------
+
+// The two sums of three sinusoids, g_r = sum_m a sin(2 pi k.x + phi).
+struct SmoothArgs {
+  void* U[5];
+  int n;
+  double w[2][3][5];  // [plane][sinusoid]: k_x, k_y, k_z, phase, amplitude
+  double amp, ia1;
+};
+
+__device__ __forceinline__ float sin_(float x) { return sinf(x); }
+__device__ __forceinline__ double sin_(double x) { return sin(x); }
+
+template <class T> __device__ __forceinline__ void smooth_g(const SmoothArgs& a, int64_t c, T (&g)[2]) {
+  const int n = a.n;
+  const int i = (int)(c % n), j = (int)((c / n) % n), kz = (int)(c / ((int64_t)n * n));
+  const T x = (T(i) + T(0.5f)) / T(n), y = (T(j) + T(0.5f)) / T(n), z = (T(kz) + T(0.5f)) / T(n);
+  const T tp = T(6.283185307179586);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const double* w = a.w[r][m];
+      const T arg = tp * (T(w[0]) * x + T(w[1]) * y + T(w[2]) * z) + T(w[3]);
+      acc = acc + T(w[4]) * sin_(arg);
+    }
+    g[r] = acc;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kFvThreads) k_fv_smooth_max(const __grid_constant__ SmoothArgs a, T* gmax) {
+  const int64_t cells = (int64_t)a.n * a.n * a.n;
+  T m0 = T(0), m1 = T(0);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += (int64_t)gridDim.x * blockDim.x) {
+    T g[2];
+    smooth_g(a, c, g);
+    m0 = abs_(g[0]) > m0 ? abs_(g[0]) : m0;
+    m1 = abs_(g[1]) > m1 ? abs_(g[1]) : m1;
+  }
+  m0 = warp_max(m0);
+  m1 = warp_max(m1);
+  if ((threadIdx.x & 31) == 0) {
+    if (m0 > T(0)) atomic_max_pos(gmax + 0, m0);
+    if (m1 > T(0)) atomic_max_pos(gmax + 1, m1);
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kFvThreads) k_fv_smooth_write(const __grid_constant__ SmoothArgs a, const T* gmax) {
+  const int64_t cells = (int64_t)a.n * a.n * a.n;
+  const T s0 = T(a.amp) / gmax[0], s1 = T(a.amp) / gmax[1], ia1 = T(a.ia1);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += (int64_t)gridDim.x * blockDim.x) {
+    T g[2];
+    smooth_g(a, c, g);
+    static_cast<T*>(a.U[0])[c] = fma_(s0, g[0], T(1));
+    static_cast<T*>(a.U[1])[c] = T(0);
+    static_cast<T*>(a.U[2])[c] = T(0);
+    static_cast<T*>(a.U[3])[c] = T(0);
+    static_cast<T*>(a.U[4])[c] = fma_(s1, g[1], T(1)) * ia1;
+  }
+}
+
+template <class T> cudaError_t smooth_launch(const SmoothArgs& a, void* scratch, cudaStream_t s) {
+  const int64_t cells = (int64_t)a.n * a.n * a.n;
+  const int64_t need = (cells + kFvThreads - 1) / kFvThreads;
+  const int64_t cap = (int64_t)device_sm_count() * 8;
+  const int grid = (int)(need < cap ? need : cap);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * sizeof(T), s);
+  if (e != cudaSuccess) return e;
+  k_fv_smooth_max<T><<<grid, kFvThreads, 0, s>>>(a, static_cast<T*>(scratch));
+  k_fv_smooth_write<T><<<grid, kFvThreads, 0, s>>>(a, static_cast<const T*>(scratch));
+  return cudaGetLastError();
+}
+
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 // Host-side checks of a grid table: sorted, tile-aligned, non-overlapping
@@ -552,6 +630,36 @@ fdbb_status fv_step_noalloc(int ngrids, const fdbb_fv_grid* grids, int64_t vcell
 }  // namespace fdbb
 
 extern "C" {
+
+fdbb_status fdbb_fv_init_smooth(const fdbb_fv_grid* grid, double gamma, double amplitude, const double* wave,
+                                fdbb_dtype t, void* scratch, fdbb_stream_t stream) {
+  using namespace fdbb;
+  if (grid == nullptr || wave == nullptr || scratch == nullptr) return FDBB_ERR_NULLPTR;
+  if (t != FDBB_F32 && t != FDBB_F64) return FDBB_ERR_DTYPE;
+  if (grid->n < 1 || grid->n > 4096 || !(gamma > 1.0) || !std::isfinite(gamma) || !std::isfinite(amplitude))
+    return FDBB_ERR_ARG;
+  const uintptr_t al = t == FDBB_F64 ? 8 : 4;
+  if (!aligned(scratch, al)) return FDBB_ERR_ALIGN;
+  SmoothArgs a = {};
+  for (int q = 0; q < 5; ++q) {
+    if (grid->U[q] == nullptr) return FDBB_ERR_NULLPTR;
+    if (!aligned(grid->U[q], 16)) return FDBB_ERR_ALIGN;
+    a.U[q] = grid->U[q];
+  }
+  for (int r = 0; r < 2; ++r)
+    for (int m = 0; m < 3; ++m)
+      for (int f = 0; f < 5; ++f) {
+        const double v = wave[15 * r + 5 * m + f];
+        if (!std::isfinite(v)) return FDBB_ERR_ARG;
+        a.w[r][m][f] = v;
+      }
+  a.n = grid->n;
+  a.amp = amplitude;
+  a.ia1 = 1.0 / (gamma - 1.0);
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const cudaError_t e = t == FDBB_F64 ? smooth_launch<double>(a, scratch, s) : smooth_launch<float>(a, scratch, s);
+  return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
+}
 
 fdbb_status fdbb_fv_rusanov_step_noalloc(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double gamma,
                                          double cfl, fdbb_dtype t, fdbb_stream_t stream) {

@@ -153,6 +153,34 @@ def new_grid(V: Sequence[torch.Tensor], n: int, slot: int, smax: torch.Tensor, g
     return g
 
 
+def new_grid_smooth(n: int, seed: int, slot: int, smax: torch.Tensor, dtype, device, gamma: float = 1.4,
+                    amplitude: float = 0.1, dt_log_steps: int = 0, stream=None) -> FvGrid:
+    """A grid holding the smooth seeded initial state of a serving request
+    (the data of synth.smooth_perturbation, built on the device by
+    fdbb_fv_init_smooth in two launches), with its wave-speed slots cleared
+    and the initial wave speed reduced into slot 0."""
+    import numpy as np
+
+    from . import synth
+    cells = n ** 3
+    U = [torch.empty(cells, dtype=dtype, device=device) for _ in range(5)]
+    Unew = [torch.empty(cells, dtype=dtype, device=device) for _ in range(5)]
+    wave = np.empty(30, dtype=np.float64)
+    for r, (k, ph, a) in enumerate(synth.smooth_params(seed)):
+        for m in range(3):
+            wave[15 * r + 5 * m: 15 * r + 5 * m + 5] = (k[m, 0], k[m, 1], k[m, 2], ph[m], a[m])
+    scratch = torch.empty(2, dtype=dtype, device=device)
+    dt_log = torch.zeros(dt_log_steps, dtype=torch.float64, device=device) if dt_log_steps else None
+    g = FvGrid(U, Unew, n, slot, dt_log)
+    tab, _ = _table([g], with_new=False)
+    s = _stream(stream, device)
+    capi.call("fdbb_fv_init_smooth", tab, gamma, amplitude, wave.ctypes.data, _CODES[dtype], scratch.data_ptr(), s)
+    with torch.cuda.stream(stream) if stream is not None else _null():
+        smax[3 * slot:3 * slot + 3].zero_()
+    max_speed([g], smax, gamma, stream)
+    return g
+
+
 class _null:
     def __enter__(self):
         return None

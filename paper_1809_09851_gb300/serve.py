@@ -109,8 +109,10 @@ class FVServer:
         self.wait_timeout = wait_timeout
         self.keep_results = keep_results
         self.log_dt = log_dt
-        self.initial_state = initial_state or (
-            lambda req: fv.primitive_on_device(req.n, req.seed, self.dtype, self.device))
+        # None: the smooth seeded state of synth.smooth_params, built on the
+        # device by fdbb_fv_init_smooth; otherwise a callable giving the
+        # primitive planes of a request
+        self.initial_state = initial_state
 
     def state_bytes(self, n: int) -> int:
         return 2 * 5 * n ** 3 * self.elem
@@ -119,9 +121,13 @@ class FVServer:
         nbytes = self.state_bytes(req.n)
         slot = self.free_slots.popleft()
         with torch.cuda.stream(self.stream):
-            V = self.initial_state(req)
-            g = fv.new_grid(V, req.n, slot, self.smax, self.gamma,
-                            dt_log_steps=req.steps if self.log_dt else 0, stream=self.stream)
+            if self.initial_state is None:
+                g = fv.new_grid_smooth(req.n, req.seed, slot, self.smax, self.dtype, self.device, self.gamma,
+                                       dt_log_steps=req.steps if self.log_dt else 0, stream=self.stream)
+            else:
+                V = self.initial_state(req)
+                g = fv.new_grid(V, req.n, slot, self.smax, self.gamma,
+                                dt_log_steps=req.steps if self.log_dt else 0, stream=self.stream)
         self.used += nbytes
         return Job(req, g, nbytes, now)
 

@@ -136,3 +136,29 @@ def test_pointer_kind_of_host_memory(L):
     buf = ctypes.create_string_buffer(64)
     assert L.fdbb_pointer_kind(None) == capi.FDBB_PTR_OTHER
     assert L.fdbb_pointer_kind(ctypes.addressof(buf)) == capi.FDBB_PTR_OTHER
+
+
+def test_fv_init_smooth_argument_errors(L):
+    g = capi.FvGrid()
+    for q in range(5):
+        g.U[q] = A + 256 * q
+    g.n = 8
+    wave = (ctypes.c_double * 30)(*([1.0] * 30))
+    F32, F64 = capi.FDBB_F32, capi.FDBB_F64
+    assert L.fdbb_fv_init_smooth(None, 1.4, 0.1, wave, F32, A, None) == 2
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, None, F32, A, None) == 2
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, wave, F32, None, None) == 2
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, wave, capi.FDBB_BF16, A, None) == 4
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.0, 0.1, wave, F32, A, None) == 1
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, float("nan"), wave, F32, A, None) == 1
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, wave, F64, A + 4, None) == 3
+    g.n = 0
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, wave, F32, A, None) == 1
+    g.n = 8
+    g.U[3] = None
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, wave, F32, A, None) == 2
+    g.U[3] = MIS
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, wave, F32, A, None) == 3
+    bad = (ctypes.c_double * 30)(*([1.0] * 29 + [float("inf")]))
+    g.U[3] = A + 768
+    assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, bad, F32, A, None) == 1

@@ -130,3 +130,31 @@ def test_serving_admission_by_budget():
     assert rep.max_active == 1
     assert rep.rejected == [99]
     assert len(rep.latencies) == 6
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 3e-6)], ids=["f64", "f32"])
+@pytest.mark.parametrize("n", [1, 7, 32, 50])
+def test_smooth_initial_state_on_device(n, dtype, tol):
+    """fdbb_fv_init_smooth builds the serving requests' initial state: it equals
+    the host generator's primitive planes converted by the oracle (tolerance:
+    a few ulp of the storage type), and its initial wave speed equals the
+    oracle's maximum."""
+    seed = 11 + n
+    smax = torch.zeros(3 * 8, dtype=dtype, device=DEV)
+    g = fv.new_grid_smooth(n, seed, 2, smax, dtype, DEV, G_)
+    torch.cuda.synchronize()
+    ref = oracle.cons_from_prim(3, G_, synth.smooth_perturbation(n, seed))
+    for k in range(5):
+        got = g.U[k].double().cpu().numpy()
+        assert np.all(np.abs(got - ref[k]) <= tol * np.maximum(1.0, np.abs(ref[k]))), k
+    dt = oracle.rusanov_dt(n, G_, 0.4, ref)
+    ref_speed = 0.4 * (1.0 / n) / dt
+    assert abs(float(smax[6]) - ref_speed) <= 1e-5 * ref_speed
+    # the served request's answer: default initial state equals the host-built one
+    reqs = [synth.Request(0, 0.0, 9, 3, 5)]
+    a = serve.FVServer(DEV, torch.float64, keep_results=True).run(reqs, realtime=False).results[0]
+    b = serve.FVServer(DEV, torch.float64, keep_results=True,
+                       initial_state=lambda r: [torch.from_numpy(v).to(DEV) for v in
+                                                synth.smooth_perturbation(r.n, r.seed)]).run(reqs, realtime=False).results[0]
+    for x, y in zip(a, b):
+        assert torch.allclose(x, y, rtol=1e-12, atol=1e-13)
