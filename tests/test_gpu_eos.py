@@ -217,3 +217,27 @@ def test_empty_and_rejected_dtypes():
     st = capi.lib().fdbb_flux_eos(ctypes.byref(m), 3, 0, 8, 9, capi.planes([t.data_ptr() for t in U]),
                                   capi.planes([t.data_ptr() for t in F[:5]]), None)
     assert st == 4
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("form", ["f64dw", "f64", "f32"])
+def test_full_size_fused_sampled(form):
+    """The fused pass under NASG at the benchmark size (N = 2^26, the
+    general-EOS leg's launch configuration): sampled points against the oracle."""
+    dtype, dw = FORMS[form]
+    eos = synth.EOS_NASG
+    n = 1 << 26
+    V = synth.euler_eos(n, 3)
+    U = oracle.eos_cons_from_prim(eos, 3, V)
+    W = synth.char_weights(n, 5)
+    del V
+    Ud, U = dev(U, dtype)
+    Wd, W = dev(W, dtype)
+    F, A, Y = blocks.euler_fused_eos(Ud, Wd, eos, 0, dw=dw)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(9)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 4096), np.arange(n - 37, n), np.arange(5)]))
+    it = torch.from_numpy(idx).to(DEV)
+    got = [t[it].double().cpu().numpy() for t in (*F, *A, *Y)]
+    ref, S = oracle.eos_euler_fused(eos, 3, 0, [u[idx] for u in U], [w[idx] for w in W], scale=True)
+    check(got, ref, S, dtype, "full-size fused nasg")

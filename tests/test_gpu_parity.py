@@ -257,8 +257,9 @@ def test_dw_copies_are_bit_exact():
 # ---------------------------------------------------------------------------
 
 @pytest.mark.slow
-@pytest.mark.parametrize("dtype,dw", [(torch.float64, False), (torch.float64, True), (torch.float32, False)],
-                         ids=["f64", "f64dw", "f32"])
+@pytest.mark.parametrize("dtype,dw", [(torch.float64, False), (torch.float64, True), (torch.float32, False),
+                                      (torch.bfloat16, False)],
+                         ids=["f64", "f64dw", "f32", "bf16"])
 def test_full_size_fused_sampled(dtype, dw):
     """3D fused pass at N = 2^26 (the benchmark size): sampled points against
     the oracle, and A_x(U) U = F_x(U) checked at every point."""
@@ -279,14 +280,19 @@ def test_full_size_fused_sampled(dtype, dw):
     Ws = [w[idx] for w in Wq]
     ref, S = oracle.euler_fused(D, 0, G, Us, Ws, scale=True)
     check(got, ref, S, dtype, "full-size fused")
-    # homogeneity at every point, evaluated on the device in float64
+    # homogeneity at every point, evaluated on the device in float64 (each
+    # output rounded to the storage type once: 2 u_store of the scale more;
+    # points whose stored state is below vacuum give NaN on both sides)
     Ux = [u.double() for u in Ud]
     tol = 1e-12 if dtype == torch.float64 else 64 * 2.0 ** -24
     for r in range(5):
         Au = sum(A[r * 5 + c].double() * Ux[c] for c in range(5))
         scale = sum((A[r * 5 + c].double() * Ux[c]).abs() for c in range(5))
         err = (Au - F[r].double()).abs()
-        assert bool((err <= 8 * tol * scale + 1e-300).all()), r
+        ok = err <= (8 * tol + 2 * U_STORE[dtype]) * (scale + F[r].double().abs()) + 1e-300
+        if dtype == torch.bfloat16:
+            ok = ok | torch.isnan(err)
+        assert bool(ok.all()), r
 
 
 # ---------------------------------------------------------------------------
