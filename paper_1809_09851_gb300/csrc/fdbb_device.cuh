@@ -229,6 +229,13 @@ __device__ __forceinline__ double abs_(double x) { return fabs(x); }
 __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
 __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+// x/2 and 2x (exact scalings; double-word scales both words).
+__device__ __forceinline__ double half_(double x) { return 0.5 * x; }
+__device__ __forceinline__ float half_(float x) { return 0.5f * x; }
+__device__ __forceinline__ dw half_(dw x) { return dw(__fmul_rn(0.5f, x.hi), __fmul_rn(0.5f, x.lo)); }
+__device__ __forceinline__ double twice_(double x) { return x + x; }
+__device__ __forceinline__ float twice_(float x) { return x + x; }
+__device__ __forceinline__ dw twice_(dw x) { return dw(__fadd_rn(x.hi, x.hi), __fadd_rn(x.lo, x.lo)); }
 
 }  // namespace fdbb
 
@@ -320,7 +327,7 @@ __device__ __forceinline__ void internal_energy(Pt<R, D>& s, R& rhoe) {
   R mv = s.m[0] * s.v[0];
 #pragma unroll
   for (int i = 1; i < D; ++i) mv = fma_(s.m[i], s.v[i], mv);
-  s.rq = R(0.5f) * mv;
+  s.rq = half_(mv);
   rhoe = s.rE - s.rq;
 }
 template <int D>
@@ -367,7 +374,7 @@ __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
     s.c2 = k.g * s.p * s.r;
   } else {
     s.ie = rhoe * s.r;
-    const D2<R> P = k.p_rhoe(arg1(s.rho), arg2(s.ie));
+    const D2<R> P = tangents(k.p_rhoe(arg1(s.rho), arg2(s.ie)));
     s.p = P.v;
     s.G = P.de * s.r;
     s.H = (s.rE + s.p) * s.r;
@@ -390,12 +397,16 @@ __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
 // ---------------------------------------------------------------------------
 
 // Flux column d: F[0] = m_d, F[1+i] = m_d v_i + delta_id p, F[nv-1] = v_d (rhoE + p).
+// For i != d, F_d[1+i] = F_i[1+d] = m_i m_d / rho; both are formed as
+// m_min(i,d) v_max(i,d), so a pass over several directions computes (and
+// converts) each such product once.
 template <int D, int d, class R>
 __device__ __forceinline__ R flux_comp(const Pt<R, D>& s, int k) {
   if (k == 0) return s.m[d];
   if (k == D + 1) return s.v[d] * (s.rE + s.p);
   const int i = k - 1;
-  return (i == d) ? fma_(s.m[d], s.v[d], s.p) : s.m[d] * s.v[i];
+  if (i == d) return fma_(s.m[d], s.v[d], s.p);
+  return i < d ? s.m[i] * s.v[d] : s.m[d] * s.v[i];
 }
 
 // Jacobian entry A_d[row][col] (row-major), u = v_d, with dp/dU =
@@ -449,14 +460,14 @@ __device__ __forceinline__ void char_fwd(const Pt<R, D>& s, const K& k, const R*
     t = fma_(s.ph, w[0], s.G * (w[nv - 1] - dot)) * (ic * ic);
   }
   const R a = fma_(s.v[d], w[0], -w[1 + d]) * ic;
-  y[0] = R(0.5f) * (t + a);
+  y[0] = half_(t + a);
   y[1] = w[0] - t;
 #pragma unroll
   for (int kk = 0; kk < D - 1; ++kk) {
     const int tk = tang<D, d>(kk);
     y[2 + kk] = fma_(-s.v[tk], w[0], w[1 + tk]);
   }
-  y[nv - 1] = R(0.5f) * (t - a);
+  y[nv - 1] = half_(t - a);
 }
 
 // Inverse characteristic transform Y = R_d W at one point.  The entropy wave's
@@ -477,7 +488,7 @@ __device__ __forceinline__ void char_inv(const Pt<R, D>& s, const K& k, const R*
   if constexpr (K::kIdeal)
     e = fma_(s.q, a2, e);
   else
-    e = fma_(fma_(R(2), s.q, -(s.ph / s.G)), a2, e);
+    e = fma_(twice_(s.q) - s.ph / s.G, a2, e);
 #pragma unroll
   for (int kk = 0; kk < D - 1; ++kk) {
     const int tk = tang<D, d>(kk);
@@ -508,7 +519,7 @@ __device__ __forceinline__ void flux_vjp_pt(const Pt<R, D>& s, const K& k, const
 #pragma unroll
   for (int j = 0; j < D; ++j)
     if (j != d) y[1 + j] = fma_(u, g[1 + j], -(a1 * s.v[j] * z));
-  y[1 + d] = g[0] + sigma + fma_(R(2) * u, gd, fma_(s.H, ge, -(a1 * u * z)));
+  y[1 + d] = g[0] + sigma + fma_(twice_(u), gd, fma_(s.H, ge, -(a1 * u * z)));
   y[nv - 1] = fma_(a1, gd, eos_1pG(s, k) * u * ge);
 }
 
@@ -526,12 +537,12 @@ __device__ __forceinline__ void derive_prim(Pt<R, D>& s, const K& k, G& g) {
     s.m[i] = s.rho * s.v[i];
     g.check(s.m[i]);
   }
-  s.q = R(0.5f) * v2;
+  s.q = half_(v2);
   s.rq = s.rho * s.q;
   if constexpr (K::kIdeal) {
     s.rE = fma_(s.p, k.ia1, s.rq);
   } else {
-    const D2<R> Z = k.rhoe_rhop(arg1(s.rho), arg2(s.p));
+    const D2<R> Z = tangents(k.rhoe_rhop(arg1(s.rho), arg2(s.p)));
     s.rE = Z.v + s.rq;
     s.zr = Z.dr;
     s.zp = Z.de;
@@ -592,7 +603,7 @@ __device__ __forceinline__ void roe_state(const Pt<R, D>& L, const Pt<R, D>& Rt,
     g.check(s.v[i]);
   }
   s.H = fma_(wL, L.H, wR * Rt.H) * iw;
-  s.q = R(0.5f) * v2;
+  s.q = half_(v2);
   s.c2 = k.a1 * (s.H - s.q);
   g.check(s.H);
   g.check(s.q);
@@ -618,7 +629,7 @@ __device__ __forceinline__ void roe_flux_pt(const Pt<R, D>& L, const Pt<R, D>& R
   char_inv<D, d>(s, k, beta, diss);
 #pragma unroll
   for (int q = 0; q < nv; ++q)
-    Fh[q] = R(0.5f) * (flux_comp<D, d>(L, q) + flux_comp<D, d>(Rt, q)) - R(0.5f) * diss[q];
+    Fh[q] = half_(flux_comp<D, d>(L, q) + flux_comp<D, d>(Rt, q) - diss[q]);
 }
 
 }  // namespace fdbb

@@ -5,11 +5,11 @@
 // (section 2.2, "Equations of state", Fig. 10).  Here an EOS model is a small
 // device struct with the same members plus the inverse rhoe_rhop(rho, p):
 //
-//   template <class X> X p_rhoe(const X& rho, const X& e) const;   // pressure
-//   R T_rhoe(R rho, R e) const;                                     // temperature
-//   template <class X> X rhoe_rhop(const X& rho, const X& p) const; // rho e
+//   template <class X, class Y> auto p_rhoe(const X& rho, const Y& e) const;   // pressure
+//   R T_rhoe(R rho, R e) const;                                                 // temperature
+//   template <class X, class Y> auto rhoe_rhop(const X& rho, const Y& p) const; // rho e
 //
-// p_rhoe and rhoe_rhop are templates over the number type X so that the
+// p_rhoe and rhoe_rhop are templates over the number types so that the
 // kernels can evaluate them on forward-mode dual numbers (D2 below) and get the
 // partial derivatives the flux Jacobians and eigenvectors need -- dp/drho at
 // constant e, dp/de at constant rho, and those of rho e(rho, p) -- exactly, from
@@ -31,41 +31,123 @@ namespace fdbb {
 
 // Forward-mode dual number with two tangents: value v and the derivatives with
 // respect to the first (dr) and second (de) argument of the evaluated function.
-template <class R> struct D2 {
-  R v, dr, de;
+// Each tangent also has a kind known at compile time -- exactly zero, exactly
+// one, or a run-time value -- and only kVal tangents are stored.  The seeds of
+// the two arguments are (1, 0) and (0, 1); propagating the kinds drops every
+// product with an exact zero or one from the derivative formulas (under IEEE
+// rules the compiler may not fold x * 0, and x * 1 still costs a double-word
+// product), so a model's derivatives cost only their nonzero terms.
+enum TangentKind : int { kZero = 0, kOne = 1, kVal = 2 };
+
+template <class R, int KR = kVal, int KE = kVal> struct D2 {
+  R v, dr, de;  // dr (de) holds a value only when KR (KE) is kVal
 };
 
-template <class R> __device__ __forceinline__ D2<R> operator+(const D2<R>& a, const D2<R>& b) {
-  return {a.v + b.v, a.dr + b.dr, a.de + b.de};
+namespace dual {
+// Tangent x of kind K as a number.
+template <int K, class R> __device__ __forceinline__ R val(const R& x) {
+  if constexpr (K == kZero) return R(0);
+  else if constexpr (K == kOne) return R(1);
+  else return x;
 }
-template <class R> __device__ __forceinline__ D2<R> operator-(const D2<R>& a, const D2<R>& b) {
-  return {a.v - b.v, a.dr - b.dr, a.de - b.de};
+__host__ __device__ constexpr int add_kind(int a, int b) { return a == kZero ? b : (b == kZero ? a : kVal); }
+__host__ __device__ constexpr int neg_kind(int a) { return a == kZero ? kZero : kVal; }
+__host__ __device__ constexpr int sub_kind(int a, int b) { return b == kZero ? a : (a == kZero ? neg_kind(b) : kVal); }
+__host__ __device__ constexpr int scale_kind(int a) { return a == kZero ? kZero : kVal; }
+
+// a + b, a - b and -a for tangents of kinds A and B (results of kinds
+// add_kind, sub_kind and neg_kind).
+template <int A, int B, class R> __device__ __forceinline__ R add(const R& a, const R& b) {
+  if constexpr (A == kZero) return b;
+  else if constexpr (B == kZero) return a;
+  else return val<A>(a) + val<B>(b);
 }
-template <class R> __device__ __forceinline__ D2<R> operator-(const D2<R>& a) { return {-a.v, -a.dr, -a.de}; }
-template <class R> __device__ __forceinline__ D2<R> operator*(const D2<R>& a, const D2<R>& b) {
-  return {a.v * b.v, a.dr * b.v + a.v * b.dr, a.de * b.v + a.v * b.de};
+template <int A, class R> __device__ __forceinline__ R neg(const R& a) {
+  if constexpr (A == kZero) return a;
+  else return -val<A>(a);
+}
+template <int A, int B, class R> __device__ __forceinline__ R sub(const R& a, const R& b) {
+  if constexpr (B == kZero) return a;
+  else if constexpr (A == kZero) return neg<B>(b);
+  else return val<A>(a) - val<B>(b);
+}
+// a c for a tangent a of kind A and a number c (kind scale_kind(A)).
+template <int A, class R> __device__ __forceinline__ R scale(const R& a, const R& c) {
+  if constexpr (A == kZero) return a;
+  else if constexpr (A == kOne) return c;
+  else return a * c;
+}
+// Product rule: at bv + av bt for tangents at, bt of kinds A, B.
+template <int A, int B> __host__ __device__ constexpr int prod_kind() { return add_kind(scale_kind(A), scale_kind(B)); }
+template <int A, int B, class R>
+__device__ __forceinline__ R prod(const R& at, const R& bv, const R& av, const R& bt) {
+  return add<scale_kind(A), scale_kind(B)>(scale<A>(at, bv), scale<B>(bt, av));
+}
+// Quotient rule with v = a / b, ib = 1 / b: (at - v bt) ib.
+template <int A, int B> __host__ __device__ constexpr int quot_kind() { return scale_kind(sub_kind(A, scale_kind(B))); }
+template <int A, int B, class R>
+__device__ __forceinline__ R quot(const R& at, const R& bt, const R& v, const R& ib) {
+  return scale<sub_kind(A, scale_kind(B))>(sub<A, scale_kind(B)>(at, scale<B>(bt, v)), ib);
+}
+}  // namespace dual
+
+template <class R, int A, int B, int C, int E>
+__device__ __forceinline__ D2<R, dual::add_kind(A, C), dual::add_kind(B, E)> operator+(const D2<R, A, B>& a,
+                                                                                      const D2<R, C, E>& b) {
+  return {a.v + b.v, dual::add<A, C>(a.dr, b.dr), dual::add<B, E>(a.de, b.de)};
+}
+template <class R, int A, int B, int C, int E>
+__device__ __forceinline__ D2<R, dual::sub_kind(A, C), dual::sub_kind(B, E)> operator-(const D2<R, A, B>& a,
+                                                                                      const D2<R, C, E>& b) {
+  return {a.v - b.v, dual::sub<A, C>(a.dr, b.dr), dual::sub<B, E>(a.de, b.de)};
+}
+template <class R, int A, int B>
+__device__ __forceinline__ D2<R, dual::neg_kind(A), dual::neg_kind(B)> operator-(const D2<R, A, B>& a) {
+  return {-a.v, dual::neg<A>(a.dr), dual::neg<B>(a.de)};
+}
+template <class R, int A, int B, int C, int E>
+__device__ __forceinline__ D2<R, dual::prod_kind<A, C>(), dual::prod_kind<B, E>()> operator*(const D2<R, A, B>& a,
+                                                                                            const D2<R, C, E>& b) {
+  return {a.v * b.v, dual::prod<A, C>(a.dr, b.v, a.v, b.dr), dual::prod<B, E>(a.de, b.v, a.v, b.de)};
 }
 // Quotient with one reciprocal: v = a/b, dv = (da - v db) / b.
-template <class R> __device__ __forceinline__ D2<R> operator/(const D2<R>& a, const D2<R>& b) {
+template <class R, int A, int B, int C, int E>
+__device__ __forceinline__ D2<R, dual::quot_kind<A, C>(), dual::quot_kind<B, E>()> operator/(const D2<R, A, B>& a,
+                                                                                            const D2<R, C, E>& b) {
   const R ib = rcp_(b.v);
   const R v = a.v * ib;
-  return {v, (a.dr - v * b.dr) * ib, (a.de - v * b.de) * ib};
+  return {v, dual::quot<A, C>(a.dr, b.dr, v, ib), dual::quot<B, E>(a.de, b.de, v, ib)};
 }
-// Mixed with constants of the compute type.
-template <class R> __device__ __forceinline__ D2<R> operator+(const D2<R>& a, R c) { return {a.v + c, a.dr, a.de}; }
-template <class R> __device__ __forceinline__ D2<R> operator+(R c, const D2<R>& a) { return {c + a.v, a.dr, a.de}; }
-template <class R> __device__ __forceinline__ D2<R> operator-(const D2<R>& a, R c) { return {a.v - c, a.dr, a.de}; }
-template <class R> __device__ __forceinline__ D2<R> operator-(R c, const D2<R>& a) { return {c - a.v, -a.dr, -a.de}; }
-template <class R> __device__ __forceinline__ D2<R> operator*(const D2<R>& a, R c) {
-  return {a.v * c, a.dr * c, a.de * c};
+// Mixed with numbers of the compute type.
+template <class R, int A, int B> __device__ __forceinline__ D2<R, A, B> operator+(const D2<R, A, B>& a, R c) {
+  return {a.v + c, a.dr, a.de};
 }
-template <class R> __device__ __forceinline__ D2<R> operator*(R c, const D2<R>& a) {
-  return {c * a.v, c * a.dr, c * a.de};
+template <class R, int A, int B> __device__ __forceinline__ D2<R, A, B> operator+(R c, const D2<R, A, B>& a) {
+  return {c + a.v, a.dr, a.de};
+}
+template <class R, int A, int B> __device__ __forceinline__ D2<R, A, B> operator-(const D2<R, A, B>& a, R c) {
+  return {a.v - c, a.dr, a.de};
+}
+template <class R, int A, int B>
+__device__ __forceinline__ D2<R, dual::neg_kind(A), dual::neg_kind(B)> operator-(R c, const D2<R, A, B>& a) {
+  return {c - a.v, dual::neg<A>(a.dr), dual::neg<B>(a.de)};
+}
+template <class R, int A, int B>
+__device__ __forceinline__ D2<R, dual::scale_kind(A), dual::scale_kind(B)> operator*(const D2<R, A, B>& a, R c) {
+  return {a.v * c, dual::scale<A>(a.dr, c), dual::scale<B>(a.de, c)};
+}
+template <class R, int A, int B>
+__device__ __forceinline__ D2<R, dual::scale_kind(A), dual::scale_kind(B)> operator*(R c, const D2<R, A, B>& a) {
+  return {c * a.v, dual::scale<A>(a.dr, c), dual::scale<B>(a.de, c)};
 }
 
 // Seeds: the first and the second argument of a two-argument function.
-template <class R> __device__ __forceinline__ D2<R> arg1(R x) { return {x, R(1), R(0)}; }
-template <class R> __device__ __forceinline__ D2<R> arg2(R x) { return {x, R(0), R(1)}; }
+template <class R> __device__ __forceinline__ D2<R, kOne, kZero> arg1(R x) { return {x, R(0), R(0)}; }
+template <class R> __device__ __forceinline__ D2<R, kZero, kOne> arg2(R x) { return {x, R(0), R(0)}; }
+// A result with both tangents as numbers.
+template <class R, int A, int B> __device__ __forceinline__ D2<R> tangents(const D2<R, A, B>& a) {
+  return {a.v, dual::val<A>(a.dr), dual::val<B>(a.de)};
+}
 
 // EOS parameter slots (KArgs::ke / kef), computed on the host in double:
 enum EosSlot { kEA1 = 0, kEIA1, kEB, kEICV, kEPINF, kEQ, kEGP, kEA };
@@ -78,11 +160,11 @@ enum EosSlot { kEA1 = 0, kEIA1, kEB, kEICV, kEPINF, kEQ, kEGP, kEA };
 template <class R> struct EosNasg {
   static constexpr bool kIdeal = false;
   R a1, ia1, b, icv, pinf, q, gp;
-  template <class X> __device__ __forceinline__ X p_rhoe(const X& rho, const X& e) const {
+  template <class X, class Y> __device__ __forceinline__ auto p_rhoe(const X& rho, const Y& e) const {
     return a1 * (e - q) * rho / (R(1) - b * rho) - gp;
   }
   __device__ __forceinline__ R T_rhoe(R rho, R e) const { return (e - q - pinf * (R(1) / rho - b)) * icv; }
-  template <class X> __device__ __forceinline__ X rhoe_rhop(const X& rho, const X& p) const {
+  template <class X, class Y> __device__ __forceinline__ auto rhoe_rhop(const X& rho, const Y& p) const {
     return (p + gp) * (R(1) - b * rho) * ia1 + rho * q;
   }
 };
@@ -92,13 +174,13 @@ template <class R> struct EosNasg {
 template <class R> struct EosVdw {
   static constexpr bool kIdeal = false;
   R a1, ia1, b, icv, a;
-  template <class X> __device__ __forceinline__ X p_rhoe(const X& rho, const X& e) const {
-    const X ar2 = a * rho * rho;
+  template <class X, class Y> __device__ __forceinline__ auto p_rhoe(const X& rho, const Y& e) const {
+    const auto ar2 = a * rho * rho;
     return a1 * (rho * e + ar2) / (R(1) - b * rho) - ar2;
   }
   __device__ __forceinline__ R T_rhoe(R rho, R e) const { return (e + a * rho) * icv; }
-  template <class X> __device__ __forceinline__ X rhoe_rhop(const X& rho, const X& p) const {
-    const X ar2 = a * rho * rho;
+  template <class X, class Y> __device__ __forceinline__ auto rhoe_rhop(const X& rho, const Y& p) const {
+    const auto ar2 = a * rho * rho;
     return (p + ar2) * (R(1) - b * rho) * ia1 - ar2;
   }
 };

@@ -286,9 +286,9 @@ template <int D> struct OpCons {
 #pragma unroll
     for (int j = 0; j < VW; ++j) {
       if constexpr (K::kIdeal)
-        x[j] = fma_(p[j], k.ia1, R(0.5f) * rho[j] * v2[j]);
+        x[j] = fma_(p[j], k.ia1, half_(rho[j] * v2[j]));
       else
-        x[j] = k.rhoe_rhop(rho[j], p[j]) + R(0.5f) * rho[j] * v2[j];
+        x[j] = k.rhoe_rhop(rho[j], p[j]) + half_(rho[j] * v2[j]);
     }
     store<T, VW, R>(outp<T>(a, D + 1), i0, cnt, x);
     return true;
