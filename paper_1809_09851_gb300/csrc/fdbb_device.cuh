@@ -360,7 +360,9 @@ __device__ __forceinline__ void internal_energy(Pt<float, D>& s, float& rhoe) {
 // dp/drho|_e and dp/de|_rho; then Gamma = (1/rho) dp/de,
 // c^2 = dp/drho|_e + Gamma p / rho (the isentropic derivative, de = p/rho^2 drho)
 // and phi = dp/drho|_e + Gamma (q - e).
-template <class R, int D, class K, class G>
+// C2 = false skips c^2 (and its range check) for blocks that never read it:
+// fluxes, Jacobians, the flux VJP, the Roe forms (which average their own).
+template <bool C2 = true, class R, int D, class K, class G>
 __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
   s.r = rcp_(s.rho);
 #pragma unroll
@@ -371,14 +373,14 @@ __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
   if constexpr (K::kIdeal) {
     s.p = k.a1 * rhoe;
     s.H = (s.rE + s.p) * s.r;
-    s.c2 = k.g * s.p * s.r;
+    if constexpr (C2) s.c2 = k.g * s.p * s.r;
   } else {
     s.ie = rhoe * s.r;
     const D2<R> P = tangents(k.p_rhoe(arg1(s.rho), arg2(s.ie)));
     s.p = P.v;
     s.G = P.de * s.r;
     s.H = (s.rE + s.p) * s.r;
-    s.c2 = fma_(s.G * s.p, s.r, P.dr);
+    if constexpr (C2) s.c2 = fma_(s.G * s.p, s.r, P.dr);
     s.ph = fma_(s.G, s.q - s.ie, P.dr);
     g.check(s.ie);
     g.check(s.G);
@@ -389,7 +391,7 @@ __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
   g.check(s.q);
   g.check(s.p);
   g.check(s.H);
-  g.check(s.c2);
+  if constexpr (C2) g.check(s.c2);
 }
 
 // ---------------------------------------------------------------------------
@@ -510,10 +512,11 @@ __device__ __forceinline__ void flux_vjp_pt(const Pt<R, D>& s, const K& k, const
   const R u = s.v[d];
   const R gd = g[1 + d], ge = g[nv - 1];
   const R z = fma_(u, ge, gd);
+  constexpr int t0 = d == 0 ? 1 : 0;  // first tangential direction
   R sigma = R(0);
 #pragma unroll
   for (int i = 0; i < D; ++i)
-    if (i != d) sigma = fma_(s.v[i], g[1 + i], sigma);
+    if (i != d) sigma = i == t0 ? s.v[i] * g[1 + i] : fma_(s.v[i], g[1 + i], sigma);
   const R phi = eos_phi(s, k), a1 = eos_G(s, k);
   y[0] = fma_(phi, z, -fma_(u, sigma, u * fma_(u, gd, s.H * ge)));
 #pragma unroll

@@ -141,10 +141,10 @@ __device__ __forceinline__ void store_field(const KArgs& a, int base, int64_t i0
   }
 }
 
-template <int VW, int D, class R, class K, class G>
+template <int VW, int D, bool C2 = true, class R, class K, class G>
 __device__ __forceinline__ void derive_all(Pt<R, D> (&s)[VW], const K& k, G& g) {
 #pragma unroll
-  for (int j = 0; j < VW; ++j) derive(s[j], k, g);
+  for (int j = 0; j < VW; ++j) derive<C2>(s[j], k, g);
 }
 
 // Flux column d into output planes base..base+nv-1.  Component 0 is the input
@@ -229,7 +229,7 @@ template <int D> struct OpPrim {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
-    derive_all<VW, D>(s, k, g);
+    derive_all<VW, D, false>(s, k, g);
     if (!g.ok) return false;
     R x[VW];
     if constexpr (std::is_same<R, dw>::value) {
@@ -359,7 +359,7 @@ template <int D, int d> struct OpFlux {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
-    derive_all<VW, D>(s, k, g);
+    derive_all<VW, D, false>(s, k, g);
     if (!g.ok) return false;
     if constexpr (d >= 0) {
       emit_flux<T, VW, D, d>(a, 0, i0, cnt, s);
@@ -380,7 +380,7 @@ template <int D, int d> struct OpJac {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
-    derive_all<VW, D>(s, k, g);
+    derive_all<VW, D, false>(s, k, g);
     if (!g.ok) return false;
     emit_jac<T, VW, D, d>(a, 0, i0, cnt, s, k);
     return true;
@@ -456,7 +456,7 @@ template <int D, int d> struct OpVjp {
     load_U<T, VW, D>(src, 0, s, g);
     R gg[VW][nv], y[VW][nv];
     load_field<T, VW, nv>(src, nv, gg, g);
-    derive_all<VW, D>(s, k, g);
+    derive_all<VW, D, false>(s, k, g);
     if (!g.ok) return false;
 #pragma unroll
     for (int j = 0; j < VW; ++j) flux_vjp_pt<D, d>(s[j], k, gg[j], y[j]);
@@ -476,8 +476,8 @@ template <int D, int d> struct OpRoeFlux {
     Pt<R, D> L[VW], Rt[VW], s[VW];
     load_U<T, VW, D>(src, 0, L, g);
     load_U<T, VW, D>(src, nv, Rt, g);
-    derive_all<VW, D>(L, k, g);
-    derive_all<VW, D>(Rt, k, g);
+    derive_all<VW, D, false>(L, k, g);
+    derive_all<VW, D, false>(Rt, k, g);
 #pragma unroll
     for (int j = 0; j < VW; ++j) roe_state(L[j], Rt[j], k, s[j], g);
     if (!g.ok) return false;
@@ -503,8 +503,8 @@ template <int D, int d, bool INV> struct OpRoeChar {
     load_U<T, VW, D>(src, nv, Rt, g);
     R w[VW][nv], y[VW][nv];
     load_field<T, VW, nv>(src, 2 * nv, w, g);
-    derive_all<VW, D>(L, k, g);
-    derive_all<VW, D>(Rt, k, g);
+    derive_all<VW, D, false>(L, k, g);
+    derive_all<VW, D, false>(Rt, k, g);
 #pragma unroll
     for (int j = 0; j < VW; ++j) roe_state(L[j], Rt[j], k, s[j], g);
     if (!g.ok) return false;
@@ -630,7 +630,7 @@ template <int D> struct OpTemp {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
-    derive_all<VW, D>(s, k, g);
+    derive_all<VW, D, false>(s, k, g);
     if (!g.ok) return false;
     R x[VW];
 #pragma unroll
@@ -795,7 +795,8 @@ __global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KAr
 
 // The general-EOS double-word kernels, compiled for three resident blocks per
 // SM (at most 85 registers per thread; left to itself the compiler takes 90
-// and two blocks fit).
+// and two blocks fit).  The ideal-gas double-word fused pass already fits
+// three blocks and runs 1.2% slower under the bound, so it keeps k_staged.
 template <class Op, class T, class R, class Mdl>
 __global__ void __launch_bounds__(kThreads, 3) k_staged3(const __grid_constant__ KArgs a) {
   staged_body<Op, T, R, Mdl>(a);
