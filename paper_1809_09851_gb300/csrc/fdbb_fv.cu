@@ -4,11 +4,13 @@
 // Each grid occupies a range of a "virtual" cell index space, padded to a
 // multiple of FDBB_FV_TILE cells, so that a block-sized tile of virtual cells
 // always belongs to one grid.  The grid table (up to FDBB_FV_MAX_GRIDS
-// descriptors) travels in the kernel's parameter block.  A thread owns one
-// cell: it reads the cell and its six periodic neighbours, forms the six face
-// fluxes from the paper's inviscid flux (section 2.2) and writes the updated
-// state.  The time step of every grid comes from a per-grid maximum wave
-// speed kept in a caller-provided scratch array of three slots per grid:
+// descriptors) travels in the kernel's parameter block.  The step kernels
+// march 32 x 8-cell column tiles along z through shared-memory plane tiles and
+// form the face fluxes from the paper's inviscid flux (section 2.2):
+// k_fv_rusanov_step one plane at a time (FP64 grids), k_fv_rusanov_step2 two
+// planes at a time in packed FP32x2 arithmetic (FP32 grids).  The time step
+// of every grid comes from a per-grid maximum wave speed kept in a
+// caller-provided scratch array of three slots per grid:
 //   step s reads slot s%3 (max of the state at its start), reduces the new
 //   state's wave speed into slot (s+1)%3 with atomicMax, and clears slot
 //   (s+2)%3, which step s-1 read and step s+1 will fill.
@@ -17,6 +19,7 @@
 #include <cmath>
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 
 #include "fdbb.h"
 #include "fdbb_device.cuh"
@@ -265,15 +268,11 @@ __device__ __forceinline__ void face(const Side<T>& L, const Side<T>& R, T (&Fh)
 // computed once) into a double-buffered shared-memory plane, then updates its
 // own cells from the four x/y faces of the current plane and the z faces,
 // carrying the lower z face of the next plane in registers.
-// Resident blocks per SM the step kernel is compiled for: four for FP32 grids
-// (the shared-memory plane tiles, 2 x 8 x 340 floats = 21.8 KB, allow it and
-// the kernel is bound by issue and shared-memory latency, so occupancy
-// pays), the compiler's choice for FP64.
-template <class T> struct FvMinBlocks { static constexpr int value = 1; };
-template <> struct FvMinBlocks<float> { static constexpr int value = 4; };
+// The scalar step kernel serves FP64 grids (compiler's choice of registers);
+// FP32 grids run the packed two-plane kernel k_fv_rusanov_step2 below.
 
 template <class T>
-__global__ void __launch_bounds__(kFvThreads, FvMinBlocks<T>::value) k_fv_rusanov_step(const __grid_constant__ FvArgs a) {
+__global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_constant__ FvArgs a) {
   extern __shared__ __align__(16) unsigned char fv_smem[];
   PlaneTile<T>* tiles = reinterpret_cast<PlaneTile<T>*>(fv_smem);  // [2]
   const Consts<T> k = fv_consts<T>(a.gamma);
@@ -396,14 +395,265 @@ __global__ void __launch_bounds__(kFvThreads, FvMinBlocks<T>::value) k_fv_rusano
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 grids: two planes per thread in packed FP32x2 arithmetic.
+//
+// A thread updates the same (x, y) cell of planes z and z + 1: lane x of each
+// packed value belongs to plane z, lane y to plane z + 1 (z - z0 even; the
+// segments start at multiples of kZSeg, which is even, so a plane has the same
+// lane in every tile).  Every operation of the faces, the update and the
+// derived state then takes one packed instruction (FFMA2 / FADD2 / FMUL2 of
+// sm_100 and later) for two cells.  Each lane rounds like the scalar FP32
+// operation, and a face computed by two threads or two tiles goes through
+// the same packed sequence on the same inputs, so its two copies agree bit for
+// bit and the update conserves mass, momentum and energy to rounding.
+// ---------------------------------------------------------------------------
+struct f2 {
+  float2 v;
+};
+__device__ __forceinline__ f2 pk(float a, float b) { return {make_float2(a, b)}; }
+__device__ __forceinline__ f2 splat(float a) { return {make_float2(a, a)}; }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return {__fmul2_rn(a.v, b.v)}; }
+// a - b as (-1) b + a: the product is exact, so one rounding as in a subtraction
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return {__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)}; }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ f2 abs2(f2 a) { return pk(fabsf(a.v.x), fabsf(a.v.y)); }
+__device__ __forceinline__ f2 max2(f2 a, f2 b) {
+  return pk(a.v.x > b.v.x ? a.v.x : b.v.x, a.v.y > b.v.y ? a.v.y : b.v.y);
+}
+
+// Plane-pair tile: for each of the kSlots cells of a (32+2) x (8+2) tile,
+// U, p, 1/rho and c of planes z (x) and z + 1 (y).
+struct PairTile {
+  float2 v[kSlotVals][kSlots];
+};
+struct Cell2 {
+  f2 u[5], p, r, c;
+};
+struct Consts2 {
+  f2 a1, g, half;
+};
+
+// U, p, 1/rho and c of a pair of cells (the scalar FP32 derivation, packed).
+__device__ __forceinline__ Cell2 derive2(const f2 (&u)[5], const Consts2& k) {
+  Cell2 e;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) e.u[q] = u[q];
+  e.r = pk(fv_rcp(u[0].v.x), fv_rcp(u[0].v.y));
+  const f2 v0 = u[1] * e.r, v1 = u[2] * e.r, v2 = u[3] * e.r;
+  const f2 rq = k.half * fma2(u[3], v2, fma2(u[2], v1, u[1] * v0));
+  e.p = k.a1 * (u[4] - rq);
+  const f2 c2 = k.g * e.p * e.r;
+  e.c = pk(fv_sqrt(c2.v.x), fv_sqrt(c2.v.y));
+  return e;
+}
+__device__ __forceinline__ void put_pair(const Cell2& e, PairTile& P, int slot) {
+#pragma unroll
+  for (int q = 0; q < 5; ++q) P.v[q][slot] = e.u[q].v;
+  P.v[5][slot] = e.p.v;
+  P.v[6][slot] = e.r.v;
+  P.v[7][slot] = e.c.v;
+}
+__device__ __forceinline__ Cell2 pair_at(const PairTile& P, int slot) {
+  Cell2 e;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) e.u[q].v = P.v[q][slot];
+  e.p.v = P.v[5][slot];
+  e.r.v = P.v[6][slot];
+  e.c.v = P.v[7][slot];
+  return e;
+}
+
+// Face side in direction d: U, F_d(U) and |v_d| + c (as side<T, d>).
+struct Side2 {
+  f2 u[5], f[5], s;
+};
+template <int d> __device__ __forceinline__ Side2 side2(const Cell2& e) {
+  Side2 x;
+  const f2 md = e.u[1 + d];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) x.u[q] = e.u[q];
+  x.f[0] = md;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const f2 vi = e.u[1 + i] * e.r;
+    x.f[1 + i] = i == d ? fma2(md, vi, e.p) : md * vi;
+  }
+  const f2 vd = md * e.r;
+  x.f[4] = vd * (e.u[4] + e.p);
+  x.s = abs2(vd) + e.c;
+  return x;
+}
+// Twice the Rusanov flux, (F(U_L) + F(U_R)) + s (U_L - U_R) (as face<T>).
+__device__ __forceinline__ void face2(const Side2& L, const Side2& R, f2 (&Fh)[5]) {
+  const f2 sm = max2(L.s, R.s);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) Fh[q] = fma2(sm, L.u[q] - R.u[q], L.f[q] + R.f[q]);
+}
+
+// Conservative values of this thread's slots of a plane pair.
+struct PairRaw {
+  f2 u[kSlotsPerThread][5];
+};
+
+__global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid_constant__ FvArgs a) {
+  extern __shared__ __align__(16) unsigned char fv_smem[];
+  PairTile* tiles = reinterpret_cast<PairTile*>(fv_smem);  // [2]
+  const Consts<float> k1 = fv_consts<float>(a.gamma);
+  const Consts2 k = {splat(k1.a1), splat(k1.g), splat(0.5f)};
+  const int tid = threadIdx.x, lx = tid % kBX, ly = tid / kBX;
+  const int own = (ly + 1) * kSX + (lx + 1);
+  for (int64_t vt = blockIdx.x; vt < a.tiles; vt += gridDim.x) {
+    const int gi = find_tile_grid(a, vt);
+    const fdbb_fv_grid& g = a.g[gi];
+    const int n = g.n;
+    const int ntx = ceil_div(n, kBX), nty = ceil_div(n, kBY);
+    int64_t loc = vt - a.tile_begin[gi];
+    const int tx = (int)(loc % ntx);
+    loc /= ntx;
+    const int ty = (int)(loc % nty);
+    const int tz = (int)(loc / nty);
+    const int x0 = tx * kBX, y0 = ty * kBY, z0 = tz * kZSeg;
+    const int z1 = z0 + kZSeg < n ? z0 + kZSeg : n;
+    float* smax = static_cast<float*>(a.smax) + 3 * g.slot;
+    const int ph = g.phase, ph1 = ph == 2 ? 0 : ph + 1, ph2 = ph1 == 2 ? 0 : ph1 + 1;
+    const float dx = 1.0f / float(n);
+    const float dt = float(a.cfl) * dx / smax[ph];
+    const f2 mhlam = splat(-(0.5f * (dt / dx)));  // -1/2 dt/dx: the faces carry twice the flux
+    if (tx == 0 && ty == 0 && tz == 0 && tid == 0) {  // the grid's first tile
+      smax[ph2] = 0.0f;  // read by the previous step, filled by the next one
+      if (g.dt_log) g.dt_log[g.step] = static_cast<double>(dt);
+    }
+    const int x = x0 + lx, y = y0 + ly;
+    const bool active = x < n && y < n;
+    int64_t slot_off[kSlotsPerThread];
+#pragma unroll
+    for (int j = 0; j < kSlotsPerThread; ++j) {
+      const int sl = tid + j * kFvThreads;
+      const int gx = (x0 + sl % kSX - 1 + n) % n, gy = (y0 + sl / kSX - 1 + n) % n;
+      slot_off[j] = (int64_t)gy * n + gx;
+    }
+    const int64_t plane = (int64_t)n * n;
+    auto wrap = [n](int z) { return z % n; };  // z >= 0
+    // planes za (lane x) and zb (lane y) of this thread's slots
+    auto load_pair = [&](PairRaw& r, int za, int zb) {
+      const int64_t oa = (int64_t)za * plane, ob = (int64_t)zb * plane;
+#pragma unroll
+      for (int j = 0; j < kSlotsPerThread; ++j) {
+        const int sl = tid + j * kFvThreads;
+        if (sl < kSlots) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q)
+            r.u[j][q] = pk(ldg<float>(g.U[q], oa + slot_off[j]), ldg<float>(g.U[q], ob + slot_off[j]));
+        }
+      }
+    };
+    auto fill = [&](PairTile& P, const PairRaw& r) {
+#pragma unroll
+      for (int j = 0; j < kSlotsPerThread; ++j) {
+        const int sl = tid + j * kFvThreads;
+        if (sl < kSlots) put_pair(derive2(r.u[j], k), P, sl);
+      }
+    };
+    PairRaw raw;
+    load_pair(raw, z0, wrap(z0 + 1));
+    fill(tiles[0], raw);
+    load_pair(raw, wrap(z0 + 2), wrap(z0 + 3));  // in flight during the prologue
+    __syncthreads();
+    // lower z face of plane z0, from the cells of planes z0 - 1 and z0 (lane x;
+    // the same packed sequence as the upper faces of the tile below)
+    f2 carry[5];
+    if (active) {
+      const int64_t cm = (int64_t)(z0 == 0 ? n - 1 : z0 - 1) * plane + (int64_t)y * n + x;
+      f2 um[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) um[q] = splat(ldg<float>(g.U[q], cm));
+      const Cell2 lower = derive2(um, k);
+      Cell2 cur = pair_at(tiles[0], own);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) cur.u[q] = splat(cur.u[q].v.x);
+      cur.p = splat(cur.p.v.x);
+      cur.r = splat(cur.r.v.x);
+      cur.c = splat(cur.c.v.x);
+      face2(side2<2>(lower), side2<2>(cur), carry);
+    }
+    float vmax = 0.0f;
+    for (int z = z0; z < z1; z += 2) {
+      const int b = ((z - z0) >> 1) & 1;
+      const PairTile& C = tiles[b];
+      PairTile& N = tiles[b ^ 1];
+      fill(N, raw);  // planes z + 2, z + 3
+      if (z + 2 < z1) load_pair(raw, wrap(z + 4), wrap(z + 5));  // prefetch planes z + 4, z + 5
+      __syncthreads();
+      if (active) {
+        const bool two = z + 1 < z1;  // lane y is a cell of this segment
+        f2 lo[5], hi[5], div[5];
+        const Cell2 me = pair_at(C, own);
+        const Side2 cx = side2<0>(me);
+        face2(side2<0>(pair_at(C, own - 1)), cx, lo);
+        face2(cx, side2<0>(pair_at(C, own + 1)), hi);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) div[q] = hi[q] - lo[q];
+        const Side2 cy = side2<1>(me);
+        face2(side2<1>(pair_at(C, own - kSX)), cy, lo);
+        face2(cy, side2<1>(pair_at(C, own + kSX)), hi);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) div[q] = div[q] + (hi[q] - lo[q]);
+        // z faces: upper faces of planes z and z + 1 from the cells of planes
+        // (z + 1, z + 2); the lower faces are (carry, upper face of plane z)
+        const Cell2 nx = pair_at(N, own);
+        Cell2 up;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) up.u[q] = pk(me.u[q].v.y, nx.u[q].v.x);
+        up.p = pk(me.p.v.y, nx.p.v.x);
+        up.r = pk(me.r.v.y, nx.r.v.x);
+        up.c = pk(me.c.v.y, nx.c.v.x);
+        face2(side2<2>(me), side2<2>(up), hi);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          div[q] = div[q] + (hi[q] - pk(carry[q].v.x, hi[q].v.x));
+          carry[q] = splat(hi[q].v.y);
+        }
+        const int64_t c = ((int64_t)z * n + y) * n + x;
+        f2 un[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          un[q] = fma2(mhlam, div[q], me.u[q]);
+          static_cast<float*>(g.Unew[q])[c] = un[q].v.x;
+          if (two) static_cast<float*>(g.Unew[q])[c + plane] = un[q].v.y;
+        }
+        const Cell2 nw = derive2(un, k);
+        const f2 vs = abs2(un[1] * nw.r) + nw.c + (abs2(un[2] * nw.r) + nw.c) + (abs2(un[3] * nw.r) + nw.c);
+        vmax = vs.v.x > vmax ? vs.v.x : vmax;
+        if (two) vmax = vs.v.y > vmax ? vs.v.y : vmax;
+      }
+      __syncthreads();  // the next iteration refills the current pair tile
+    }
+    vmax = warp_max(vmax);
+    if ((tid & 31) == 0 && vmax > 0.0f) atomic_max_pos(smax + ph1, vmax);
+  }
+}
+
 constexpr size_t fv_step_smem(size_t es) { return 2 * (size_t)kSlotVals * kSlots * es; }
+
+// Step kernel and its dynamic shared memory for storage T: FP32 grids take
+// the packed two-plane kernel, FP64 grids the scalar one.
+template <class T> auto step_kernel() {
+  if constexpr (std::is_same<T, float>::value)
+    return k_fv_rusanov_step2;
+  else
+    return k_fv_rusanov_step<T>;
+}
+template <class T> constexpr size_t step_smem() {
+  return std::is_same<T, float>::value ? 2 * sizeof(PairTile) : fv_step_smem(sizeof(T));
+}
 
 template <class T> int fv_blocks_per_sm(bool step) {
   static const int bs = [] {
     int b = 0;
-    cudaFuncSetAttribute(k_fv_rusanov_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fv_step_smem(sizeof(T)));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fv_rusanov_step<T>, kFvThreads, fv_step_smem(sizeof(T))) !=
-        cudaSuccess)
+    cudaFuncSetAttribute(step_kernel<T>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<T>());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<T>(), kFvThreads, step_smem<T>()) != cudaSuccess)
       b = 1;
     return b > 0 ? b : 1;
   }();
@@ -421,7 +671,7 @@ template <class T> cudaError_t fv_launch(const FvArgs& a, bool step, cudaStream_
   const int grid = (int)(work < cap ? work : cap);
   if (grid <= 0) return cudaSuccess;
   if (step)
-    k_fv_rusanov_step<T><<<grid, kFvThreads, fv_step_smem(sizeof(T)), s>>>(a);
+    step_kernel<T>()<<<grid, kFvThreads, step_smem<T>(), s>>>(a);
   else
     k_fv_max_speed<T><<<grid, kFvThreads, 0, s>>>(a);
   return cudaGetLastError();
