@@ -64,6 +64,30 @@ def test_fv_fp32_matches_oracle():
         assert abs(tot - tot0) <= 1e-5 * max(1.0, np.abs(Uq[k]).sum())
 
 
+@pytest.mark.parametrize("n", [33, 45, 64])
+def test_fv_fp32_across_plane_segments(n):
+    """FP32 grids taller than one 32-plane column segment: the z face between
+    two segments is formed by both tiles (as the upper face of the lower tile's
+    last plane pair and as the carried lower face of the upper tile), and a
+    segment of odd length ends with a half-used plane pair (33 = 32 + 1,
+    45 = 32 + 13, 64 = 32 + 32).  Matches the FP64 oracle to 2e-5 and
+    conserves mass, momentum and energy to float rounding."""
+    steps = 3
+    U = _initial(n, 6)
+    Uq = [u.astype(np.float32).astype(np.float64) for u in U]
+    smax = torch.zeros(3, dtype=torch.float32, device=DEV)
+    g = fv.grid_from_conservative(_dev(Uq, torch.float32), n, 0, smax, G_, dt_log_steps=steps)
+    for _ in range(steps):
+        fv.rusanov_step([g], smax, G_, 0.4)
+    ref, dts = oracle.rusanov_run(n, G_, 0.4, steps, Uq)
+    np.testing.assert_allclose(g.dt_log.cpu().numpy(), dts, rtol=1e-5)
+    for k in range(5):
+        got = g.U[k].double().cpu().numpy()
+        assert np.abs(got - ref[k]).max() <= 2e-5 * max(1.0, np.abs(ref[k]).max()), (n, k)
+        tot0, tot = Uq[k].sum(), got.sum()
+        assert abs(tot - tot0) <= 1e-5 * max(1.0, np.abs(Uq[k]).sum()), (n, k)
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_fv_batched_equals_alone(dtype):
     sizes = [3, 5, 8, 13, 16, 7]
