@@ -236,6 +236,8 @@ __device__ __forceinline__ dw half_(dw x) { return dw(__fmul_rn(0.5f, x.hi), __f
 __device__ __forceinline__ double twice_(double x) { return x + x; }
 __device__ __forceinline__ float twice_(float x) { return x + x; }
 __device__ __forceinline__ dw twice_(dw x) { return dw(__fadd_rn(x.hi, x.hi), __fadd_rn(x.lo, x.lo)); }
+__device__ __forceinline__ dw2 half_(dw2 x) { return dw2(p_mul(make_float2(0.5f, 0.5f), x.hi), p_mul(make_float2(0.5f, 0.5f), x.lo)); }
+__device__ __forceinline__ dw2 twice_(dw2 x) { return dw2(p_add(x.hi, x.hi), p_add(x.lo, x.lo)); }
 
 }  // namespace fdbb
 

@@ -216,4 +216,110 @@ __device__ __forceinline__ double dw_to_double(dw x) {
   return mag < 0x00800000u ? __hiloint2double(static_cast<int>(sign), 0) : __longlong_as_double(out);
 }
 
+// ---------------------------------------------------------------------------
+// Two double-word values in packed FP32x2 registers (sm_100 and later).
+// Lane x and lane y are two independent points; every operation is the
+// double-word operation above, lane by lane, with each FP32 step issued as one
+// packed instruction (FADD2 / FMUL2 / FFMA2) for both points.  Each lane
+// rounds exactly as the scalar operation, so a lane's result equals the
+// double-word result bit for bit.
+// ---------------------------------------------------------------------------
+struct dw2 {
+  float2 hi, lo;
+  dw2() = default;
+  __device__ __forceinline__ dw2(float2 h, float2 l) : hi(h), lo(l) {}
+  __device__ __forceinline__ dw2(float h) : hi(make_float2(h, h)), lo(make_float2(0.0f, 0.0f)) {}
+  __device__ __forceinline__ dw2(int h) : dw2(static_cast<float>(h)) {}
+  __device__ __forceinline__ dw2(double) = delete;
+};
+
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as (-1) b + a: the product is exact, so one rounding as in a subtraction
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void dw2_fast_two_sum(float2 a, float2 b, float2& s, float2& e) {
+  s = p_add(a, b);
+  e = p_sub(b, p_sub(s, a));
+}
+
+__device__ __forceinline__ dw2 operator-(dw2 a) { return dw2(p_neg(a.hi), p_neg(a.lo)); }
+
+__device__ __forceinline__ dw2 operator+(dw2 a, dw2 b) {
+  const float2 s = p_add(a.hi, b.hi);
+  const float2 bb = p_sub(s, a.hi);
+  const float2 e = p_add(p_sub(a.hi, p_sub(s, bb)), p_sub(b.hi, bb));
+  const float2 w = p_add(e, p_add(a.lo, b.lo));
+  dw2 z;
+  dw2_fast_two_sum(s, w, z.hi, z.lo);
+  return z;
+}
+
+// a + (-b) of the scalar type with the negations folded in:
+// (-b) - bb = -(b + bb) and a.lo + (-b.lo) = a.lo - b.lo exactly.
+__device__ __forceinline__ dw2 operator-(dw2 a, dw2 b) {
+  const float2 s = p_sub(a.hi, b.hi);
+  const float2 bb = p_sub(s, a.hi);
+  const float2 e = p_sub(p_sub(a.hi, p_sub(s, bb)), p_add(b.hi, bb));
+  const float2 w = p_add(e, p_sub(a.lo, b.lo));
+  dw2 z;
+  dw2_fast_two_sum(s, w, z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ dw2 operator*(dw2 a, dw2 b) {
+  const float2 p = p_mul(a.hi, b.hi);
+  const float2 pe = p_fma(a.hi, b.hi, p_neg(p));
+  const float2 t = p_mul(a.hi, b.lo);
+  const float2 c = p_fma(a.lo, b.hi, t);
+  const float2 l = p_add(pe, c);
+  dw2 z;
+  dw2_fast_two_sum(p, l, z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ dw2 fma_(dw2 a, dw2 b, dw2 c) {
+  const float2 p = p_mul(a.hi, b.hi);
+  const float2 pe = p_fma(a.hi, b.hi, p_neg(p));
+  const float2 s = p_add(p, c.hi);
+  const float2 bb = p_sub(s, p);
+  const float2 se = p_add(p_sub(p, p_sub(s, bb)), p_sub(c.hi, bb));
+  float2 t = p_fma(a.hi, b.lo, pe);
+  t = p_fma(a.lo, b.hi, t);
+  t = p_add(t, c.lo);
+  t = p_add(t, se);
+  dw2 z;
+  dw2_fast_two_sum(s, t, z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ dw2 rcp_(dw2 y) {
+  const float2 r0 = make_float2(dw_rcp_approx(y.hi.x), dw_rcp_approx(y.hi.y));
+  float2 e = p_fma(p_neg(y.hi), r0, make_float2(1.0f, 1.0f));
+  e = p_fma(p_neg(y.lo), r0, e);
+  const float2 c = p_fma(e, e, e);
+  dw2 z;
+  dw2_fast_two_sum(r0, p_mul(r0, c), z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ dw2 operator/(dw2 a, dw2 b) { return a * rcp_(b); }
+
+// Lanes and their assembly.
+__device__ __forceinline__ dw lane_x(dw2 v) { return dw(v.hi.x, v.lo.x); }
+__device__ __forceinline__ dw lane_y(dw2 v) { return dw(v.hi.y, v.lo.y); }
+__device__ __forceinline__ dw2 pack2(dw a, dw b) { return dw2(make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)); }
+__device__ __forceinline__ dw2 splat2(dw a) { return pack2(a, a); }
+
+// Range guard of packed values: both lanes.
+struct DwGuard2 : DwGuard {
+  using DwGuard::check;
+  __device__ __forceinline__ void check(dw2 x) {
+    check(lane_x(x));
+    check(lane_y(x));
+  }
+};
+
 }  // namespace fdbb

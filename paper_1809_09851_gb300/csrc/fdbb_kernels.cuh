@@ -445,11 +445,51 @@ template <int D, int dj> struct OpFused {
   }
 };
 
+// The flux VJP of two points per thread in packed double-word arithmetic
+// (ideal gas, FP64 storage): the two points' doubles are split lane by lane,
+// the algebra runs on dw2 values (one packed FP32x2 instruction per step for
+// both points), and the results are rebuilt lane by lane.  Returns false,
+// like the scalar double-word path, when a value leaves the fast-path range.
+template <int D, int d, class Src>
+__device__ __forceinline__ bool vjp_packed(const KArgs& a, const Consts<dw>& k1, const Src& src, int64_t i0,
+                                           int cnt) {
+  constexpr int nv = D + 2;
+  DwGuard2 g;
+  const Consts<dw2> k = {splat2(k1.g),  splat2(k1.a1),   splat2(k1.g3),   splat2(k1.ta1),
+                         splat2(k1.ia1), splat2(k1.mg), splat2(k1.gia1), splat2(k1.tcv)};
+  double raw[2];
+  auto ld = [&](int q, float fill) {
+    src.raw(q, raw, fill);
+    const dw x0 = dw_from_double(raw[0], g);
+    const dw x1 = dw_from_double(raw[1], g);
+    return pack2(x0, x1);
+  };
+  Pt<dw2, D> s;
+  s.rho = ld(0, 1.0f);
+#pragma unroll
+  for (int i = 0; i < D; ++i) s.m[i] = ld(1 + i, 0.0f);
+  s.rE = ld(D + 1, 1.0f);
+  dw2 gg[nv], y[nv];
+#pragma unroll
+  for (int q = 0; q < nv; ++q) gg[q] = ld(nv + q, 0.0f);
+  derive<false>(s, k, g);
+  if (!g.ok) return false;
+  flux_vjp_pt<D, d>(s, k, gg, y);
+#pragma unroll
+  for (int q = 0; q < nv; ++q) {
+    raw[0] = dw_to_double(lane_x(y[q]));
+    raw[1] = dw_to_double(lane_y(y[q]));
+    store_raw<double, 2>(outp<double>(a, q), i0, cnt, raw);
+  }
+  return true;
+}
+
 template <int D, int d> struct OpVjp {
   static constexpr int kIn = 2 * (D + 2);
   template <class T, int VW, class R, class K, class Src>
   static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
+    if constexpr (std::is_same<R, dw>::value && VW == 2 && K::kIdeal) return vjp_packed<D, d>(a, k, src, i0, cnt);
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -697,9 +737,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // Kernels
 // ---------------------------------------------------------------------------
 
+// Points per thread and plane of an op: the storage's width, except the
+// ideal-gas double-word flux VJP, which takes two points per thread in packed
+// FP32x2 double-word arithmetic (vjp_packed).
+template <class Op, class T, class R, class Mdl> struct OpWidth { static constexpr int VW = Width<T, R>::VW; };
+template <int D, int d> struct OpWidth<OpVjp<D, d>, double, dw, IdealModel> { static constexpr int VW = 2; };
+
 template <class Op, class T, class R, class Mdl, class K, class Src>
 __device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Src& src, int64_t i0, int cnt) {
-  constexpr int VW = Width<T, R>::VW;
+  constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   if constexpr (std::is_same<R, dw>::value) {
     // double-word fast path; chunks outside its range run in native FP64
     if (!Op::template apply<T, VW, dw>(a, k, src, i0, cnt))
@@ -712,7 +758,7 @@ __device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Sr
 // Chunks [ch0, nchunk) of VW points read straight from global memory.
 template <class Op, class T, class R, class Mdl, class K>
 __device__ __forceinline__ void global_chunks(const KArgs& a, const K& k, int64_t ch0) {
-  constexpr int VW = Width<T, R>::VW;
+  constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   const int64_t nchunk = (a.n + VW - 1) / VW;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t ch = ch0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunk; ch += stride) {
@@ -730,7 +776,7 @@ __global__ void __launch_bounds__(kThreads) k_pointwise(const __grid_constant__ 
 
 template <class Op, class T, class R, class Mdl>
 __device__ __forceinline__ void staged_body(const KArgs& a) {
-  constexpr int VW = Width<T, R>::VW;
+  constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   constexpr int TILE = kThreads * VW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kStages];
@@ -826,7 +872,7 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_direct(const
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pointwise<Op, T, R, Mdl>, kThreads, 0) != cudaSuccess) b = 1;
     return b > 0 ? b : 1;
   }();
-  constexpr int VW = Width<T, R>::VW;
+  constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   const int64_t nchunk = (a.n + VW - 1) / VW;
   const int64_t need = (nchunk + kThreads - 1) / kThreads;
   const int64_t cap = (int64_t)device_sm_count() * blocks_per_sm;
@@ -837,7 +883,7 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_direct(const
 
 // Staged kernel: kStages * nin planes of one tile in dynamic shared memory.
 template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const KArgs& a, cudaStream_t stream) {
-  constexpr int VW = Width<T, R>::VW;
+  constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   constexpr int TILE = kThreads * VW;
   constexpr size_t kMaxSmem = (size_t)kStages * Op::kIn * TILE * sizeof(T);
   auto kern = [] {
@@ -870,7 +916,7 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
 // kernel, kDirectOnly).
 template <class Op, class T, class R, class Mdl = IdealModel>
 cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
-  constexpr int TILE = kThreads * Width<T, R>::VW;
+  constexpr int TILE = kThreads * OpWidth<Op, T, R, Mdl>::VW;
   const size_t ring = (size_t)kStages * a.nin * TILE * sizeof(T);
   if (!(a.flags & kDirectOnly) && a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn &&
       ring <= (100u << 10))
