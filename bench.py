@@ -48,8 +48,8 @@ L2_BYTES = 129 * 2 ** 20
 # (dram__bytes_read.sum + dram__bytes_write.sum per launch / points), valid only
 # for the kernel sources whose hash is recorded beside it.
 # Measured with ncu on N = 2^22 (profiles/fused3d_n2e26_launch_list.md):
-# (335.6 MB read + 1448.2 MB written) / 2^22 points; scaled to the launch size.
-NCU_TRAFFIC = {"source_hash": "c98ac591131ead54", "bytes_per_point": 425.3}
+# (335.6 MB read + 1448.9 MB written) / 2^22 points; scaled to the launch size.
+NCU_TRAFFIC = {"source_hash": "3525bae18bdfac2b", "bytes_per_point": 425.5}
 
 
 FUSED_KERNEL_SOURCES = ("fdbb_device.cuh", "fdbb_dw.cuh", "fdbb_eos.cuh", "fdbb_kernels.cuh", "fdbb_internal.h",
@@ -403,7 +403,20 @@ def run_configs(args, dev, stream, hbm_peak):
     torch.cuda.empty_cache()
 
     # ---- flux VJP, N = 2^24 --------------------------------------------------
-    n = 1 << 24
+    res["flux_vjp_n2e24"] = run_vjp(1 << 24, dev, stream, hbm_peak, flush)
+    del flush
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_vjp(n, dev, stream, hbm_peak, flush, steps=20, warmup=3):
+    """The flux VJP gU = A_x^T G (10 planes in, 5 out) at N points in FP64
+    storage (double-word and IEEE arithmetic) and FP32, L2 flushed before every
+    launch."""
+    import torch
+
+    from paper_1809_09851_gb300 import blocks, synth
+
     U, W = make_fields(n, 1809, dev)
     G = [torch.from_numpy(g).to(dev) for g in synth.cotangent(n, NV)]
     vjp = {}
@@ -411,15 +424,14 @@ def run_configs(args, dev, stream, hbm_peak):
         Ut = U if dt == torch.float64 else [u.to(dt) for u in U]
         Gt = G if dt == torch.float64 else [g.to(dt) for g in G]
         gU = [torch.empty(n, dtype=dt, device=dev) for _ in range(NV)]
-        t = time_flushed(lambda: blocks.flux_vjp(Ut, Gt, 0, GAMMA, out=gU, dw=dw), 20, 3, stream, flush)
+        t = time_flushed(lambda: blocks.flux_vjp(Ut, Gt, 0, GAMMA, out=gU, dw=dw), steps, warmup, stream, flush)
         avg = sum(t) / len(t) / 1e3
         b = 15 * (8 if dt == torch.float64 else 4) * n
         vjp[tag] = {"gpoints_per_s": round(n / avg / 1e9, 3), "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3)}
         del Ut, Gt, gU
-    res["flux_vjp_n2e24"] = vjp
-    del U, W, G, flush
+    del U, W, G
     torch.cuda.empty_cache()
-    return res
+    return vjp
 
 
 def pct(xs, q):
@@ -445,6 +457,10 @@ def run_gpu(args):
     hbm_peak, peak_kind = measured_peaks()
     if args.only == "fv":  # the finite-volume step kernel alone (profiling runs)
         print(json.dumps({"fv_batch": run_fv_batch(args, dev, hbm_peak)}), flush=True)
+        return None
+    if args.only == "vjp":  # the flux VJP alone at --n points (profiling runs)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"flux_vjp": run_vjp(n, dev, stream, hbm_peak, flush, args.steps, args.warmup)}), flush=True)
         return None
 
     U64, W64 = make_fields(n, seed, dev)
@@ -811,7 +827,7 @@ def main(argv=None):
     ap.add_argument("--fv-n", type=int, default=128)
     ap.add_argument("--fv-grids", type=int, default=8)
     ap.add_argument("--fv-steps", type=int, default=20)
-    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16", "eos", "configs", "fv"], default="all",
+    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16", "eos", "configs", "fv", "vjp"], default="all",
                     help="storage types to time besides the f64 headline (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
