@@ -232,6 +232,17 @@ def test_dw_out_of_range_points_fall_back_to_fp64():
         check(host([*Fn, *An, *Yn]), ref, S, torch.float64, f"native fused {dj}")
     ref, S = oracle.prim_from_cons(D, G, U, scale=True)
     check(host(blocks.prim_from_cons(Ud, G, dw=True)), ref, S, torch.float64, "dw fallback prim")
+    # the flux VJP runs two points per thread in packed double-word arithmetic:
+    # a pair with one lane out of range (points 12, 513, 4100 above; the tiny
+    # and huge cotangents below) or both (10, 11) falls back as a whole, and
+    # n = 4103 leaves a one-point tail
+    Gc = [g.copy() for g in synth.cotangent(n, 5)]
+    Gc[4][41] = 1e-35
+    Gc[1][50] = 3e27
+    Gd, _ = quantise(Gc, torch.float64)
+    for d in range(D):
+        ref, S = oracle.flux_vjp(D, d, G, U, Gc, scale=True)
+        check(host(blocks.flux_vjp(Ud, Gd, d, G, dw=True)), ref, S, torch.float64, f"dw fallback vjp {d}")
     # a NaN state gives NaN outputs in both arithmetics
     U[0][40] = np.nan
     Ud, _ = quantise(U, torch.float64)
