@@ -424,10 +424,12 @@ __device__ __forceinline__ f2 max2(f2 a, f2 b) {
 }
 
 // Plane-pair tile: for each of the kSlots cells of a (32+2) x (8+2) tile,
-// U, p, 1/rho and c of planes z (x) and z + 1 (y).
+// U, p, 1/rho and c of planes z (x) and z + 1 (y); the kernel keeps a ring of
+// three (3 x 21.8 KB).
 struct PairTile {
   float2 v[kSlotVals][kSlots];
 };
+constexpr int kPairRing = 3;
 struct Cell2 {
   f2 u[5], p, r, c;
 };
@@ -499,7 +501,7 @@ struct PairRaw {
 
 __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid_constant__ FvArgs a) {
   extern __shared__ __align__(16) unsigned char fv_smem[];
-  PairTile* tiles = reinterpret_cast<PairTile*>(fv_smem);  // [2]
+  PairTile* tiles = reinterpret_cast<PairTile*>(fv_smem);  // ring of kPairRing
   const Consts<float> k1 = fv_consts<float>(a.gamma);
   const Consts2 k = {splat(k1.a1), splat(k1.g), splat(0.5f)};
   const int tid = threadIdx.x, lx = tid % kBX, ly = tid / kBX;
@@ -579,10 +581,13 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
       face2(side2<2>(lower), side2<2>(cur), carry);
     }
     float vmax = 0.0f;
-    for (int z = z0; z < z1; z += 2) {
-      const int b = ((z - z0) >> 1) & 1;
+    // Pair tiles in a ring of three: iteration i reads tiles i and i + 1 and
+    // fills tile i + 1, whose previous contents (tile i - 2) every thread
+    // finished reading before the barrier of iteration i - 1; one barrier per
+    // plane pair.
+    for (int z = z0, b = 0; z < z1; z += 2, b = b == kPairRing - 1 ? 0 : b + 1) {
       const PairTile& C = tiles[b];
-      PairTile& N = tiles[b ^ 1];
+      PairTile& N = tiles[b == kPairRing - 1 ? 0 : b + 1];
       fill(N, raw);  // planes z + 2, z + 3
       if (z + 2 < z1) load_pair(raw, wrap(z + 4), wrap(z + 5));  // prefetch planes z + 4, z + 5
       __syncthreads();
@@ -628,8 +633,8 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
         vmax = vs.v.x > vmax ? vs.v.x : vmax;
         if (two) vmax = vs.v.y > vmax ? vs.v.y : vmax;
       }
-      __syncthreads();  // the next iteration refills the current pair tile
     }
+    __syncthreads();  // the next tile's prologue refills the ring
     vmax = warp_max(vmax);
     if ((tid & 31) == 0 && vmax > 0.0f) atomic_max_pos(smax + ph1, vmax);
   }
@@ -646,7 +651,7 @@ template <class T> auto step_kernel() {
     return k_fv_rusanov_step<T>;
 }
 template <class T> constexpr size_t step_smem() {
-  return std::is_same<T, float>::value ? 2 * sizeof(PairTile) : fv_step_smem(sizeof(T));
+  return std::is_same<T, float>::value ? kPairRing * sizeof(PairTile) : fv_step_smem(sizeof(T));
 }
 
 template <class T> int fv_blocks_per_sm(bool step) {
