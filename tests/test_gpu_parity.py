@@ -341,6 +341,28 @@ def test_staged_path_parity(dtype, dw):
     assert capi.lib().fdbb_device_status() == 0  # no bounded wait ran out
 
 
+@pytest.mark.parametrize("n", [4099, 4 * 152 * 512 + 1001], ids=["direct", "staged"])
+def test_packed_vjp_lanes_are_independent(n):
+    """The double-word flux VJP runs two points per thread as the two lanes of
+    packed FP32x2 values.  A point's result must not depend on the point that
+    shares its pair: shifting the field by one point re-pairs every point, and
+    the results are the same bits (in-range fields, so no pair falls back)."""
+    D = 3
+    _, U, _ = fields(n + 1, D, seed=77)
+    Gc = synth.cotangent(n + 1, 5)
+    # keep every momentum and cotangent at magnitude >= 1e-5 (a normal draw
+    # below 2^-24 would send its pair to the IEEE fallback)
+    floor = lambda x: np.where(np.abs(x) < 1e-5, np.copysign(1e-5, x), x)
+    U = [U[0], *(floor(m) for m in U[1:4]), U[4]]
+    Gc = [floor(g) for g in Gc]
+    Ud = [torch.from_numpy(u).to(DEV) for u in U]
+    Gd = [torch.from_numpy(g).to(DEV) for g in Gc]
+    a = blocks.flux_vjp([u[:n].clone() for u in Ud], [g[:n].clone() for g in Gd], 0, G, dw=True)
+    b = blocks.flux_vjp([u[1:].clone() for u in Ud], [g[1:].clone() for g in Gd], 0, G, dw=True)
+    for k in range(5):
+        assert torch.equal(a[k][1:], b[k][:-1]), k
+
+
 def test_fused_over_host_buffers_matches_device_call():
     """blocks.euler_fused_host (pinned host fields, chunked pipeline) gives the
     same bits as the device-resident call."""
