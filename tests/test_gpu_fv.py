@@ -88,6 +88,28 @@ def test_fv_fp32_across_plane_segments(n):
         assert abs(tot - tot0) <= 1e-5 * max(1.0, np.abs(Uq[k]).sum()), (n, k)
 
 
+@pytest.mark.parametrize("n", [12, 45])
+def test_fv_fp32_plane_pairing_is_invisible(n):
+    """FP32 grids run two z planes per thread as the lanes of packed FP32x2
+    values, in 32-plane column segments.  Rolling the periodic grid by one
+    plane in z re-pairs every plane and moves every segment boundary relative
+    to the data, and the result is the rolled result bit for bit: a face is the
+    same packed sequence in either lane, and a carried lower face the same as
+    the upper face the tile below forms."""
+    steps = 3
+    U = [u.astype(np.float32) for u in _initial(n, 8)]
+    roll = lambda u: np.roll(u.reshape(n, n, n), 1, axis=0).reshape(-1)
+    outs = []
+    for V in (U, [roll(u) for u in U]):
+        smax = torch.zeros(3, dtype=torch.float32, device=DEV)
+        g = fv.grid_from_conservative([torch.from_numpy(np.ascontiguousarray(v)).to(DEV) for v in V], n, 0, smax, G_)
+        for _ in range(steps):
+            fv.rusanov_step([g], smax, G_, 0.4)
+        outs.append([t.cpu().numpy() for t in g.U])
+    for k in range(5):
+        assert np.array_equal(roll(outs[0][k]), outs[1][k]), k
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_fv_batched_equals_alone(dtype):
     sizes = [3, 5, 8, 13, 16, 7]
