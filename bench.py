@@ -745,32 +745,64 @@ class OraclePool:
         self.pool.join()
 
 
-def cpu_baseline(args):
-    """FP64 oracle on the first `cpu_sample` points of the same field: one
-    thread for about `cpu_seconds`, then the same work on all host cores (the
-    reported value)."""
+def _rates(ns, reps, times):
+    """Best and median throughput (Gpoints/s) of timed runs of `reps` passes over `ns` points."""
+    r = sorted(ns * reps / t / 1e9 for t in times)
+    return round(r[-1], 6), round(r[len(r) // 2], 6)
+
+
+def _single_runs(ns, reps, runs):
+    """Wall times of `runs` single-thread runs of `reps` oracle passes over `ns` points."""
     import oracle
-    ns = args.cpu_sample
     U, W = oracle_sample(ns)
     oracle.euler_fused(D, 0, GAMMA, U, W)  # warm (load, page in)
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        oracle.euler_fused(D, 0, GAMMA, U, W)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= args.cpu_seconds:
-            break
-    single = ns * reps / el / 1e9
-    pool = OraclePool(ns)
+    times = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            oracle.euler_fused(D, 0, GAMMA, U, W)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_baseline(args):
+    """FP64 oracle on the first `cpu_sample` points of the same field, on one
+    thread and on all host cores (a pool of worker processes), five timed runs
+    each: best and median (the reported value is the all-core median); then the
+    same at each size of the sweep (2^16 .. 2^22 points by default)."""
+    import oracle
+    runs = 5
+    cores = getattr(args, "cpu_cores", None)
+    ns = args.cpu_sample
+    U, W = oracle_sample(ns)
+    oracle.euler_fused(D, 0, GAMMA, U, W)
+    t0 = time.perf_counter()
+    oracle.euler_fused(D, 0, GAMMA, U, W)
+    reps = max(1, int(args.cpu_seconds / runs / (time.perf_counter() - t0)))
+    s_best, s_med = _rates(ns, reps, _single_runs(ns, reps, runs))
+    pool = OraclePool(ns, cores)
     try:
-        wall = pool.run(reps)
+        a_best, a_med = _rates(ns, reps, [pool.run(reps) for _ in range(runs)])
     finally:
         pool.close()
-    allc = ns * reps / wall / 1e9
-    return {"value": round(allc, 6), "unit": UNIT, "cores": pool.cores, "kind": "oracle",
-            "single_thread_value": round(single, 6),
-            "sample": f"first {ns} points of the seeded 3D field, fused pass repeated {reps}x: {el:.1f} s on "
-                      f"1 thread, {wall:.2f} s on {pool.cores} worker processes (g++ -O2 -ffp-contract=off)"}
+    sweep = {}
+    for e in getattr(args, "cpu_sweep", (16, 18, 20, 22)):
+        m = 1 << e
+        r = max(1, int(0.2 * s_med * 1e9 / m))  # about 0.2 s per single-thread run
+        sb, sm = _rates(m, r, _single_runs(m, r, runs))
+        p = OraclePool(m, cores)
+        try:
+            ab, am = _rates(m, r, [p.run(r) for _ in range(runs)])
+        finally:
+            p.close()
+        sweep[f"2^{e}"] = {"single_best": sb, "single_median": sm, "allcore_best": ab, "allcore_median": am,
+                           "passes_per_run": r}
+    return {"value": a_med, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "best_value": a_best, "single_thread_value": s_med, "single_thread_best": s_best, "runs": runs,
+            "sample": f"first {ns} points of the seeded 3D field, fused pass repeated {reps}x per run, {runs} runs "
+                      f"on 1 thread and on {pool.cores} worker processes (median reported; "
+                      f"g++ -O2 -ffp-contract=off)",
+            "sweep": sweep}
 
 
 def run_reference(args):

@@ -87,3 +87,17 @@ def test_oracle_pool_matches_one_process():
     parts = [oracle.euler_fused(3, 0, 1.4, *bench._ORC["chunks"][i]) for i in range(2)]
     for k in range(45):
         np.testing.assert_array_equal(np.concatenate([parts[0][k], parts[1][k]]), whole[k])
+
+
+def test_cpu_baseline_runs_and_sweep():
+    """The CPU baseline: five timed runs on one thread and on all worker
+    processes (best >= median), the all-core median as the reported value, and
+    the same figures at every size of the sweep."""
+    import argparse
+    res = bench.cpu_baseline(argparse.Namespace(cpu_sample=4096, cpu_seconds=0.2, cpu_cores=2, cpu_sweep=(10, 12)))
+    assert res["kind"] == "oracle" and res["cores"] == 2 and res["runs"] == 5
+    assert res["best_value"] >= res["value"] > 0
+    assert res["single_thread_best"] >= res["single_thread_value"] > 0
+    assert set(res["sweep"]) == {"2^10", "2^12"}
+    for v in res["sweep"].values():
+        assert v["single_best"] >= v["single_median"] > 0 and v["allcore_best"] >= v["allcore_median"] > 0
