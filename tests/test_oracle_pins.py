@@ -625,3 +625,68 @@ def test_temperature_is_the_ideal_gas_law(D):
     np.testing.assert_allclose(T, V[D + 1] / V[0], rtol=1e-13)
     T2 = oracle.temperature(D, GAMMA, 5.0, U)[0]
     np.testing.assert_allclose(T2, 0.5 * T, rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Rusanov step: hand-derived values of one step on a 4-cell contact
+# ---------------------------------------------------------------------------
+
+RUSANOV_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "rusanov_contact_step.txt")
+
+
+def _rusanov_golden():
+    cases = {}
+    with open(RUSANOV_GOLDEN) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "case":
+                cases[tok[1]] = {"u": float(tok[2]), "rho": {}}
+            elif tok[1] == "dt":
+                cases[tok[0]]["dt"] = _eval(tok[2])
+            else:
+                cases[tok[0]]["rho"][int(tok[2])] = _eval(tok[3])
+    return cases
+
+
+def contact_state(n, axis, u, levels=(1.0, 1.0, 4.0, 4.0)):
+    """Conservative planes of the contact of the golden file along `axis`
+    (0 = x, the fastest index; 1 = y; 2 = z), n = len(levels): rho by the
+    cell's coordinate along the axis, p = 1, velocity u along the axis."""
+    coord = np.indices((n, n, n))[2 - axis].reshape(-1)  # [z, y, x] layout
+    rho = np.asarray(levels, dtype=np.float64)[coord]
+    zero = np.zeros(n ** 3)
+    V = [rho, zero.copy(), zero.copy(), zero.copy(), np.ones(n ** 3)]
+    V[1 + axis] = np.full(n ** 3, u)
+    return oracle.cons_from_prim(3, GAMMA, V), coord
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2], ids=["x", "y", "z"])
+def test_rusanov_step_hand_values(axis):
+    """One step of the oracle's scheme reproduces the hand-derived densities,
+    time step, momentum u rho' and energy 2.5 + u^2 rho'/2 of
+    tests/golden/rusanov_contact_step.txt along every axis.  The density moves
+    by (dt/dx) times the face-flux difference, so a time step taken as dt
+    instead of dt/dx (4x too small here), a sign slip in the dissipation or a
+    face speed taken from the wrong side fails it."""
+    n = 4
+    cases = _rusanov_golden()
+    assert set(cases) == {"rest", "right", "left"}
+    for name, cs in cases.items():
+        u = cs["u"]
+        U, coord = contact_state(n, axis, u)
+        U2, dts = oracle.rusanov_run(n, GAMMA, 0.4, 1, U)
+        assert dts[0] == pytest.approx(cs["dt"], rel=1e-14), name
+        assert oracle.rusanov_dt(n, GAMMA, 0.4, U) == pytest.approx(cs["dt"], rel=1e-14)
+        want = np.array([cs["rho"][i] for i in range(n)])[coord]
+        np.testing.assert_allclose(U2[0], want, rtol=1e-14, err_msg=name)
+        np.testing.assert_allclose(U2[1 + axis], u * want, rtol=1e-14, atol=1e-15, err_msg=name)
+        for k in range(3):
+            if k != axis:
+                np.testing.assert_array_equal(U2[1 + k], 0.0)
+        np.testing.assert_allclose(U2[4], 2.5 + 0.5 * u * u * want, rtol=1e-14, err_msg=name)
+        # rusanov_step with the golden dt gives the same state
+        U3 = oracle.rusanov_step(n, GAMMA, cs["dt"], U)
+        np.testing.assert_allclose(U3[0], want, rtol=1e-14, err_msg=name)
