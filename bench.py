@@ -47,8 +47,8 @@ L2_BYTES = 129 * 2 ** 20
 # DRAM traffic per point of the fused FP64 kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum per launch / points), valid only
 # for the kernel sources whose hash is recorded beside it.
-# Measured with ncu on N = 2^22 (profiles/fused3d_n2e26_launch_list.md):
-# (335.6 MB read + 1448.9 MB written) / 2^22 points; scaled to the launch size.
+# Measured with ncu on N = 2^22: (335.6 MB read + 1448.9 MB written) / 2^22
+# points; scaled to the launch size.
 NCU_TRAFFIC = {"source_hash": "3525bae18bdfac2b", "bytes_per_point": 425.5}
 
 
@@ -146,6 +146,18 @@ def shard_seed(base: int, rank: int) -> int:
     return base + 1000 * rank
 
 
+SHARD_ALIGN = 256  # points: a rank's range starts on a tile, so its planes stay 16-byte aligned
+
+
+def shard_bounds(n: int, world: int, rank: int):
+    """Contiguous index range [lo, hi) of one n-point field that rank `rank`
+    of `world` evaluates when the field is split (the points are independent,
+    so the ranks exchange nothing): near-equal shares whose starts are
+    multiples of SHARD_ALIGN points; the last rank ends at n."""
+    cut = lambda r: n if r >= world else (n * r // world) // SHARD_ALIGN * SHARD_ALIGN
+    return cut(rank), cut(rank + 1)
+
+
 def max_over_ranks(value: float, world: int, device=None) -> float:
     if world == 1:
         return value
@@ -160,13 +172,14 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def make_fields(n, seed, dev):
+def make_fields(n, seed, dev, lo=0):
+    """Points [lo, lo + n) of the seeded 3D field (U built on the GPU) and W."""
     import torch
     from paper_1809_09851_gb300 import blocks, synth
-    V = [torch.from_numpy(v).to(dev) for v in synth.euler3d(n, seed=seed)]
+    V = [torch.from_numpy(v[lo:]).to(dev) for v in synth.euler3d(lo + n, seed=seed)]
     U = blocks.cons_from_prim(V, GAMMA)  # conservative state built on the GPU
     del V
-    W = [torch.from_numpy(w).to(dev) for w in synth.char_weights(n, NV, seed=seed + 1)]
+    W = [torch.from_numpy(w[lo:]).to(dev) for w in synth.char_weights(lo + n, NV, seed=seed + 1)]
     return U, W
 
 
@@ -434,6 +447,81 @@ def run_vjp(n, dev, stream, hbm_peak, flush, steps=20, warmup=3):
     return vjp
 
 
+# Building blocks of the per-block leg: name -> (input planes, output planes)
+# for the 3D field (U: 5 planes; W / G / U_R: 5 more).
+BLOCKS_3D = {
+    "v_mag2": (4, 1), "eos": (5, 2), "prim_from_cons": (5, 5), "cons_from_prim": (5, 5),
+    "riemann_inv": (5, 2), "flux_x": (5, 5), "flux_all": (5, 15), "flux_jac_x": (5, 25),
+    "char_fwd_x": (10, 5), "char_inv_x": (10, 5), "flux_vjp_x": (10, 5), "roe_flux_x": (10, 5),
+    "flux_prim_all": (5, 15), "temperature": (5, 1),
+}
+
+
+def run_blocks(n, dev, stream, hbm_peak, steps=10, warmup=3, forms=("f64dw", "f64", "f32", "bf16")):
+    """Every building block of the C ABI on its own, 3D, N points: Gpoints/s
+    and the fraction of the measured HBM bandwidth its algorithmic bytes (each
+    input plane read once, each output plane written once) reach, per storage
+    form, timed back to back with CUDA events (every block's planes exceed the
+    L2 at N = 2^26, so no flush is needed); and which kernel each launch took."""
+    import torch
+    from paper_1809_09851_gb300 import blocks, capi
+    U64, W64 = make_fields(n, 1809, dev)
+    res = {}
+    dtypes = {"f64dw": torch.float64, "f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+    for form in forms:
+        dt = dtypes[form]
+        dw = form == "f64dw"
+        U = U64 if dt == torch.float64 else [u.to(dt) for u in U64]
+        W = W64 if dt == torch.float64 else [w.to(dt) for w in W64]
+        V = blocks.prim_from_cons(U, GAMMA, dw=dw)
+        UR = [torch.roll(u, 1) for u in U]  # a second physical state for the Roe flux
+        out = [torch.empty(n, dtype=dt, device=dev) for _ in range(25)]
+        calls = {
+            "v_mag2": lambda: blocks.v_mag2(U, out=out[0], dw=dw),
+            "eos": lambda: capi.call("fdbb_eos", D, GAMMA, n, blocks._code(dt, dw), blocks._ptrs(U),
+                                     out[0].data_ptr(), out[1].data_ptr(), stream.cuda_stream),
+            "prim_from_cons": lambda: blocks.prim_from_cons(U, GAMMA, out=out[:5], dw=dw),
+            "cons_from_prim": lambda: blocks.cons_from_prim(V, GAMMA, out=out[:5], dw=dw),
+            "riemann_inv": lambda: capi.call("fdbb_riemann_inv", D, 0, GAMMA, n, blocks._code(dt, dw),
+                                             blocks._ptrs(U), out[0].data_ptr(), out[1].data_ptr(), None,
+                                             stream.cuda_stream),
+            "flux_x": lambda: blocks.flux(U, 0, GAMMA, out=out[:5], dw=dw),
+            "flux_all": lambda: blocks.flux(U, -1, GAMMA, out=out[:15], dw=dw),
+            "flux_jac_x": lambda: blocks.flux_jac(U, 0, GAMMA, out=out[:25], dw=dw),
+            "char_fwd_x": lambda: blocks.char_transform(U, W, 0, GAMMA, out=out[:5], dw=dw),
+            "char_inv_x": lambda: blocks.char_transform(U, W, 0, GAMMA, inverse=True, out=out[:5], dw=dw),
+            "flux_vjp_x": lambda: blocks.flux_vjp(U, W, 0, GAMMA, out=out[:5], dw=dw),
+            "roe_flux_x": lambda: blocks.roe_flux(U, UR, 0, GAMMA, out=out[:5], dw=dw),
+            "flux_prim_all": lambda: blocks.flux_prim(V, -1, GAMMA, out=out[:15], dw=dw),
+            "temperature": lambda: blocks.temperature(U, 2.5, GAMMA, out=out[0], dw=dw),
+        }
+        es = torch.empty(0, dtype=dt).element_size()
+        tab = {}
+        for name, fn in calls.items():
+            pin, pout = BLOCKS_3D[name]
+            with torch.cuda.stream(stream):
+                fn()
+            kind = capi.last_launch().kernel
+            per, _ = time_launch(fn, steps, warmup, stream)
+            avg = sum(per) / len(per) / 1e3
+            gbs = (pin + pout) * es * n / avg / 1e9
+            tab[name] = {"gpoints_per_s": round(n / avg / 1e9, 3), "hbm_gbs": round(gbs, 1),
+                         "hbm_frac": round(gbs / hbm_peak, 3), "us": round(avg * 1e6, 1),
+                         "kernel": {1: "direct", 2: "staged"}.get(kind, "none")}
+        tab["bytes_per_point"] = {k: (a + b) * es for k, (a, b) in BLOCKS_3D.items()}
+        res[form] = tab
+        del U, W, V, UR, out
+        torch.cuda.empty_cache()
+    res["workload"] = (f"3D field of euler3d_fused, N=2^{int(math.log2(n))}: each block alone (dir 0 where a "
+                       "direction applies), every plane read or written once; W doubles as the VJP's G, "
+                       "U rolled by one point is the Roe flux's U_R")
+    res["note"] = ("f64dw: double-word arithmetic (the inverse characteristic transform runs IEEE double); "
+                   "f64: IEEE double, FP64-pipe bound where a block divides or takes square roots")
+    del U64, W64
+    torch.cuda.empty_cache()
+    return res
+
+
 def pct(xs, q):
     xs = sorted(xs)
     k = max(0, min(len(xs) - 1, int(math.ceil(q / 100.0 * len(xs))) - 1))
@@ -453,17 +541,26 @@ def run_gpu(args):
     build.build()
     n = args.n
     seed = shard_seed(1809, rank)
+    lo = 0
+    if args.split and world > 1:
+        # strong scaling: the ranks split one n-point field into contiguous ranges
+        lo, hi = shard_bounds(args.n, world, rank)
+        n, seed = hi - lo, 1809
     stream = torch.cuda.Stream(dev)
     hbm_peak, peak_kind = measured_peaks()
     if args.only == "fv":  # the finite-volume step kernel alone (profiling runs)
         print(json.dumps({"fv_batch": run_fv_batch(args, dev, hbm_peak)}), flush=True)
+        return None
+    if args.only == "blocks":  # every building block alone at --n points (profiling runs)
+        print(json.dumps({"blocks": run_blocks(n, dev, stream, hbm_peak, args.steps, args.warmup,
+                                               tuple(args.block_forms.split(",")))}), flush=True)
         return None
     if args.only == "vjp":  # the flux VJP alone at --n points (profiling runs)
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
         print(json.dumps({"flux_vjp": run_vjp(n, dev, stream, hbm_peak, flush, args.steps, args.warmup)}), flush=True)
         return None
 
-    U64, W64 = make_fields(n, seed, dev)
+    U64, W64 = make_fields(n, seed, dev, lo)
     alloc = lambda k, dt: [torch.empty(n, dtype=dt, device=dev) for _ in range(k)]
     out64 = (alloc(D * NV, torch.float64), alloc(NV * NV, torch.float64), alloc(NV, torch.float64))
 
@@ -485,7 +582,8 @@ def run_gpu(args):
     barrier()
     clocks = clk.summary()
     t_max = max_over_ranks(total_h / 1e3, world, dev)
-    value = world * n * args.steps / t_max / 1e9
+    job_points = args.n if (args.split and world > 1) else world * n  # points of all ranks per step
+    value = job_points * args.steps / t_max / 1e9
     avg_h = sum(per_h) / len(per_h) / 1e3
     achieved = bytes64 / avg_h / 1e9
     traffic = None
@@ -500,7 +598,7 @@ def run_gpu(args):
         barrier()
         t = max_over_ranks(total / 1e3, world, dev)
         avg = sum(per) / len(per) / 1e3
-        f64_native = {"value": round(world * n * args.steps / t / 1e9, 3), "unit": UNIT,
+        f64_native = {"value": round(job_points * args.steps / t / 1e9, 3), "unit": UNIT,
                       "ms_per_step": round(t * 1e3 / args.steps, 4),
                       "p50_ms": round(pct(per, 50), 4), "p99_ms": round(pct(per, 99), 4),
                       "hbm_gbs": round(bytes64 / avg / 1e9, 1), "hbm_frac": round(bytes64 / avg / 1e9 / hbm_peak, 3),
@@ -521,7 +619,7 @@ def run_gpu(args):
         t = max_over_ranks(total / 1e3, world, dev)
         avg = sum(per) / len(per) / 1e3
         b = (PLANES_IN + PLANES_OUT) * BYTES[tag] * n
-        extra[tag] = {"value": round(world * n * args.steps / t / 1e9, 3), "unit": UNIT,
+        extra[tag] = {"value": round(job_points * args.steps / t / 1e9, 3), "unit": UNIT,
                       "ms_per_step": round(t * 1e3 / args.steps, 4),
                       "p50_ms": round(pct(per, 50), 4), "p99_ms": round(pct(per, 99), 4),
                       "hbm_gbs": round(b / avg / 1e9, 1), "hbm_frac": round(b / avg / 1e9 / hbm_peak, 3),
@@ -543,6 +641,7 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         out64 = None
         configs = run_configs(args, dev, stream, hbm_peak)
+        configs["blocks_n2e26"] = run_blocks(n, dev, stream, hbm_peak)
     del out64
     torch.cuda.empty_cache()
     serving = run_serving(args, dev) if (args.serve_requests > 0 and world == 1) else None
@@ -557,12 +656,15 @@ def run_gpu(args):
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t_max * 1e3 / args.steps, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if (args.split and world > 1) else "weak",
+            "vs_baseline": None,
             "dtype": "f64 storage, f32x2 double-word arithmetic", "data": "synthetic",
             "stated_err": "|gpu - oracle| <= 1e-12 * S per output (S: running-error scale of the FP64 oracle)",
             "config": {"workload": f"euler3d_fused N=2^{int(math.log2(n))} per GPU, f64 SoA, gamma=1.4, "
                                    "outputs F_x,F_y,F_z + A_x + L_x W",
-                       "points_per_gpu": n, "parallelism": f"dp{world} (independent fields per GPU)",
+                       "points_per_gpu": n,
+                       "parallelism": (f"dp{world} (one field split into contiguous ranges)"
+                                       if (args.split and world > 1) else f"dp{world} (independent fields per GPU)"),
                        "l2": f"inputs+outputs {bytes64 / 1e9:.1f} GB >> L2 {L2_BYTES / 2**20:.0f} MiB: no flush needed"},
             "p50_ms": round(pct(per_h, 50), 4), "p99_ms": round(pct(per_h, 99), 4),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
@@ -629,8 +731,7 @@ def run_fv_batch(args, dev, hbm_peak):
     from paper_1809_09851_gb300 import fv
     n, ngrid = args.fv_n, args.fv_grids
     smax = torch.zeros(3 * ngrid, dtype=torch.float32, device=dev)
-    grids = [fv.new_grid(fv.primitive_on_device(n, 100 + i, torch.float32, dev), n, i, smax)
-             for i in range(ngrid)]
+    grids = [fv.new_grid_smooth(n, 100 + i, i, smax, torch.float32, dev) for i in range(ngrid)]
     for _ in range(max(3, args.warmup)):
         fv.rusanov_step(grids, smax)
     steps = max(3, args.fv_steps)
@@ -703,46 +804,56 @@ def oracle_sample(n_sample, seed=1809):
     return U, W
 
 
-# The oracle on all host cores: a pool of spawned worker processes (spawned, so
-# that no worker inherits a CUDA context), each holding the seeded sample and
-# running the unchanged FP64 oracle on its share of the points.
-_ORC = {}
+def host_cores() -> int:
+    """Host cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
-def _orc_init(ns, nchunks):
-    U, W = oracle_sample(ns)
-    b = [ns * i // nchunks for i in range(nchunks + 1)]
-    _ORC["chunks"] = [([u[b[i]:b[i + 1]].copy() for u in U], [w[b[i]:b[i + 1]].copy() for w in W])
-                      for i in range(nchunks)]
-
-
-def _orc_run(task):
-    import oracle
-    i, reps = task
-    U, W = _ORC["chunks"][i]
-    for _ in range(reps):
-        oracle.euler_fused(D, 0, GAMMA, U, W)
-    return i
+def host_mem_available() -> int:
+    """MemAvailable of /proc/meminfo in bytes (0 if unknown)."""
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
 
 
 class OraclePool:
-    """All-core oracle runs: run(reps) times every chunk `reps` times, in parallel."""
+    """The oracle on all host cores: `cores` threads, each running the unchanged
+    FP64 oracle on its contiguous share of the points.  The oracle is a C
+    library called through ctypes, which releases the interpreter lock for the
+    call, so the threads run in parallel on one shared copy of the inputs.
+    run(reps) times every share `reps` times."""
 
-    def __init__(self, ns, cores=None):
-        import multiprocessing as mp
-        self.cores = cores or os.cpu_count() or 1
-        self.ns = ns
-        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_orc_init, initargs=(ns, self.cores))
-        self.run(1)  # warm: import, build check, page in
+    def __init__(self, U, W, cores=None):
+        from concurrent.futures import ThreadPoolExecutor
+        self.cores = cores or host_cores()
+        ns = U[0].shape[0]
+        b = [ns * i // self.cores for i in range(self.cores + 1)]
+        self.shares = [([u[b[i]:b[i + 1]] for u in U], [w[b[i]:b[i + 1]] for w in W]) for i in range(self.cores)]
+        self.ex = ThreadPoolExecutor(self.cores)
+        self.run(1)  # warm: library load, page in
+
+    @staticmethod
+    def _share(task):
+        import oracle
+        (U, W), reps = task
+        for _ in range(reps):
+            oracle.euler_fused(D, 0, GAMMA, U, W)
 
     def run(self, reps):
         t0 = time.perf_counter()
-        self.pool.map(_orc_run, [(i, reps) for i in range(self.cores)], chunksize=1)
+        list(self.ex.map(self._share, [(sh, reps) for sh in self.shares]))
         return time.perf_counter() - t0
 
     def close(self):
-        self.pool.close()
-        self.pool.join()
+        self.ex.shutdown()
 
 
 def _rates(ns, reps, times):
@@ -751,10 +862,9 @@ def _rates(ns, reps, times):
     return round(r[-1], 6), round(r[len(r) // 2], 6)
 
 
-def _single_runs(ns, reps, runs):
-    """Wall times of `runs` single-thread runs of `reps` oracle passes over `ns` points."""
+def _single_runs(U, W, reps, runs):
+    """Wall times of `runs` single-thread runs of `reps` oracle passes."""
     import oracle
-    U, W = oracle_sample(ns)
     oracle.euler_fused(D, 0, GAMMA, U, W)  # warm (load, page in)
     times = []
     for _ in range(runs):
@@ -765,44 +875,73 @@ def _single_runs(ns, reps, runs):
     return times
 
 
+def _reps_for(seconds, one_pass):
+    return max(1, int(math.ceil(seconds / max(one_pass, 1e-9))))
+
+
 def cpu_baseline(args):
     """FP64 oracle on the first `cpu_sample` points of the same field, on one
-    thread and on all host cores (a pool of worker processes), five timed runs
-    each: best and median (the reported value is the all-core median); then the
-    same at each size of the sweep (2^16 .. 2^22 points by default)."""
+    thread and on all host cores (one thread per core), five timed runs each:
+    best and median (the reported value is the all-core median); then the same
+    at each size of the sweep (2^16 .. 2^26 points by default, as far as host
+    memory allows), every timed run at least `cpu_run_seconds` long.  Every
+    size is a prefix of one seeded field (the benchmark's field), generated
+    once at the largest size."""
     import oracle
     runs = 5
-    cores = getattr(args, "cpu_cores", None)
+    cores = getattr(args, "cpu_cores", None) or host_cores()
+    sweep_exp = [int(e) for e in str(getattr(args, "cpu_sweep", "16,18,20,22,24,26")).split(",") if e]
+    min_run = getattr(args, "cpu_run_seconds", 1.0)
+    # each pass holds 10 input and 45 output planes (plus the primitive
+    # planes while the field is built): keep it within half of free memory
+    avail = host_mem_available()
+    fits = lambda m: avail == 0 or 64 * 8 * m <= 0.5 * avail
+    sizes = [e for e in sweep_exp if fits(1 << e)]
+    skipped = [e for e in sweep_exp if e not in sizes]
     ns = args.cpu_sample
-    U, W = oracle_sample(ns)
-    oracle.euler_fused(D, 0, GAMMA, U, W)
+    big = max([ns] + [1 << e for e in sizes])
+    U, W = oracle_sample(big)
+    pre = lambda m: ([u[:m] for u in U], [w[:m] for w in W])
+    Us, Ws = pre(ns)
+    oracle.euler_fused(D, 0, GAMMA, Us, Ws)
     t0 = time.perf_counter()
-    oracle.euler_fused(D, 0, GAMMA, U, W)
-    reps = max(1, int(args.cpu_seconds / runs / (time.perf_counter() - t0)))
-    s_best, s_med = _rates(ns, reps, _single_runs(ns, reps, runs))
-    pool = OraclePool(ns, cores)
+    oracle.euler_fused(D, 0, GAMMA, Us, Ws)
+    one = time.perf_counter() - t0
+    reps = _reps_for(args.cpu_seconds / runs, one)
+    s_best, s_med = _rates(ns, reps, _single_runs(Us, Ws, reps, runs))
+    pool = OraclePool(Us, Ws, cores)
     try:
-        a_best, a_med = _rates(ns, reps, [pool.run(reps) for _ in range(runs)])
+        a_reps = _reps_for(min_run, one / cores)
+        a_best, a_med = _rates(ns, a_reps, [pool.run(a_reps) for _ in range(runs)])
     finally:
         pool.close()
     sweep = {}
-    for e in getattr(args, "cpu_sweep", (16, 18, 20, 22)):
+    for e in sizes:
         m = 1 << e
-        r = max(1, int(0.2 * s_med * 1e9 / m))  # about 0.2 s per single-thread run
-        sb, sm = _rates(m, r, _single_runs(m, r, runs))
-        p = OraclePool(m, cores)
+        Um, Wm = pre(m)
+        t0 = time.perf_counter()
+        oracle.euler_fused(D, 0, GAMMA, Um, Wm)
+        one = time.perf_counter() - t0
+        r = _reps_for(min_run, one)
+        sb, sm = _rates(m, r, _single_runs(Um, Wm, r, runs))
+        p = OraclePool(Um, Wm, cores)
         try:
-            ab, am = _rates(m, r, [p.run(r) for _ in range(runs)])
+            ra = _reps_for(min_run, p.run(1))
+            ab, am = _rates(m, ra, [p.run(ra) for _ in range(runs)])
         finally:
             p.close()
         sweep[f"2^{e}"] = {"single_best": sb, "single_median": sm, "allcore_best": ab, "allcore_median": am,
-                           "passes_per_run": r}
-    return {"value": a_med, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
-            "best_value": a_best, "single_thread_value": s_med, "single_thread_best": s_best, "runs": runs,
-            "sample": f"first {ns} points of the seeded 3D field, fused pass repeated {reps}x per run, {runs} runs "
-                      f"on 1 thread and on {pool.cores} worker processes (median reported; "
-                      f"g++ -O2 -ffp-contract=off)",
-            "sweep": sweep}
+                           "passes_per_run": r, "allcore_passes_per_run": ra}
+    del U, W
+    out = {"value": a_med, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "best_value": a_best, "single_thread_value": s_med, "single_thread_best": s_best, "runs": runs,
+           "sample": f"first {ns} points of the seeded 3D field, fused pass repeated {reps}x per single-thread "
+                     f"run and {a_reps}x per all-core run, {runs} runs on 1 thread and on {cores} threads "
+                     f"(one per core; median reported; g++ -O2 -ffp-contract=off)",
+           "sweep": sweep, "min_run_s": min_run}
+    if skipped:
+        out["sweep_skipped"] = {f"2^{e}": "more than half of the host's free memory" for e in skipped}
+    return out
 
 
 def run_reference(args):
@@ -810,7 +949,8 @@ def run_reference(args):
     if rank != 0:
         return None
     ns = args.ref_sample
-    pool = OraclePool(ns)
+    U, W = oracle_sample(ns)
+    pool = OraclePool(U, W)
     try:
         for _ in range(args.warmup):
             pool.run(1)
@@ -829,7 +969,7 @@ def run_reference(args):
                    "points_per_gpu": args.n, "parallelism": f"oracle on {pool.cores} host cores"},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                          "sample": f"each step: first {ns} points of the seeded 3D field split over "
-                                   f"{pool.cores} worker processes (g++ -O2 -ffp-contract=off)"},
+                                   f"{pool.cores} threads, one per core (g++ -O2 -ffp-contract=off)"},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -844,23 +984,32 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["fdbb", "reference"], default="fdbb")
     ap.add_argument("--n", type=int, default=N_POINTS, help="points per GPU (default 2^26)")
+    ap.add_argument("--split", action="store_true",
+                    help="with N > 1: split one --n-point field into contiguous ranges (strong scaling) "
+                         "instead of one field per rank (weak scaling, the default)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-chunk", type=int, default=1 << 23)
     ap.add_argument("--e2e-mode", choices=["mapped_out", "mapped", "copy"], default="mapped_out",
                     help="how the end-to-end leg moves host data (blocks.euler_fused_host)")
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-sweep", default="16,18,20,22,24,26",
+                    help="log2 sizes of the oracle sweep (comma-separated; empty: none)")
+    ap.add_argument("--cpu-run-seconds", type=float, default=1.0,
+                    help="minimum length of each timed oracle run of the sweep")
     ap.add_argument("--ref-sample", type=int, default=1 << 20)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests in the serving window (0 skips the serving leg)")
     ap.add_argument("--serve-fp64-requests", type=int, default=20)
     ap.add_argument("--fv-n", type=int, default=128)
     ap.add_argument("--fv-grids", type=int, default=8)
     ap.add_argument("--fv-steps", type=int, default=20)
-    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16", "eos", "configs", "fv", "vjp"], default="all",
-                    help="storage types to time besides the f64 headline (profiling runs)")
+    ap.add_argument("--only", choices=["all", "f64", "f32", "bf16", "eos", "configs", "fv", "vjp", "blocks"],
+                    default="all", help="storage types to time besides the f64 headline (profiling runs)")
+    ap.add_argument("--block-forms", default="f64dw,f64,f32,bf16",
+                    help="storage forms of --only blocks (comma-separated)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         print("bench: warning: fewer than 3 warm-up steps", file=sys.stderr)

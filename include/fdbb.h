@@ -110,6 +110,44 @@ FDBB_API int fdbb_version(void);
 FDBB_API fdbb_status fdbb_device_status(void);
 
 /*
+ * Poll limit of the bounded waits above, for testing the failure path.
+ * polls < 0 restores the default (2^22 polls per wait); polls >= 0 makes every
+ * staged kernel launched afterwards, by any host thread, give up after that
+ * many polls of each wait for its input copies (0: at the first wait, before
+ * it computes or writes anything).  A kernel that gives up still waits, with
+ * the default limit, for the copies it has issued, then returns; the next
+ * fdbb_device_status reports FDBB_ERR_TIMEOUT.  Not meant for production use:
+ * outputs of a launch that gave up are left unwritten.  Returns the previous
+ * setting.
+ */
+FDBB_API int fdbb_set_wait_limit(int polls);
+
+/*
+ * Which kernel the calling host thread's most recent point-wise block launch
+ * took (a diagnostic: the library picks the kernel from n, the storage type
+ * and the device).
+ *   kernel      FDBB_KERNEL_NONE (no launch yet on this thread),
+ *               FDBB_KERNEL_DIRECT (plane loads straight from global memory),
+ *               FDBB_KERNEL_STAGED (bulk asynchronous copies of 256-thread
+ *               tiles into a two-stage shared-memory ring; ragged tail direct);
+ *   grid, block blocks and threads per block of that launch;
+ *   smem_bytes  its dynamic shared memory;
+ *   points_per_thread  consecutive points each thread takes per plane (the
+ *               tile of the staged kernel is block * points_per_thread points).
+ * Host-side only; enqueues nothing.  FDBB_ERR_NULLPTR if info is NULL.
+ */
+typedef enum { FDBB_KERNEL_NONE = 0, FDBB_KERNEL_DIRECT = 1, FDBB_KERNEL_STAGED = 2 } fdbb_kernel_kind;
+typedef struct fdbb_launch_info {
+  int32_t kernel;
+  int32_t grid;
+  int32_t block;
+  int32_t smem_bytes;
+  int32_t points_per_thread;
+  int32_t reserved;
+} fdbb_launch_info;
+FDBB_API fdbb_status fdbb_last_launch(fdbb_launch_info *info);
+
+/*
  * Where a plane pointer lives, for callers that hand the blocks host memory:
  *   FDBB_PTR_DEVICE  memory of the current CUDA device (cudaMalloc, stream-ordered
  *                    pools; another device's memory is FDBB_PTR_OTHER);
@@ -480,10 +518,16 @@ FDBB_API fdbb_status fdbb_fv_init_smooth(const fdbb_fv_grid *grid, double gamma,
  * state at the start of the step, and dt_log[step] is written as usual).  The
  * results equal those of fdbb_fv_max_speed + fdbb_fv_rusanov_step.
  * At most FDBB_FV_MAX_GRIDS grids per call; more returns FDBB_ERR_ARG.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, once per device, with that device current); make
- * that first call before any stream capture.  All calls share the array and
- * it keeps the last call's contents, so calls that overlap on the GPU (on
+ * The grid table is checked first (as in fdbb_fv_rusanov_step); a call with
+ * invalid arguments returns its error before any CUDA call.  The first valid
+ * call on a device then looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current) and
+ * caches it for the rest of the process; make that first call before any
+ * stream capture.  The cached address belongs to the device's context at that
+ * time: after cudaDeviceReset of that device the library's module is loaded
+ * again and the address may change, so a process that resets a device must
+ * not call this entry point on that device again.  All calls share the array
+ * and it keeps the last call's contents, so calls that overlap on the GPU (on
  * different streams, or from different threads) race: serialise them.
  */
 FDBB_API fdbb_status fdbb_fv_rusanov_step_noalloc(int ngrids, const fdbb_fv_grid *grids,

@@ -30,6 +30,14 @@ DTYPES = {
 GAMMA = 1.4
 
 
+def check_device() -> None:
+    """Synchronise with the device and raise capi.FdbbError (status
+    FDBB_ERR_TIMEOUT) if a staged kernel gave up waiting for its input copies
+    since the previous check, leaving its outputs unwritten.  Set
+    capi.CHECK_DEVICE (or FDBB_CHECK_DEVICE=1) to check after every call."""
+    capi.check_device()
+
+
 def _info(planes: Sequence[torch.Tensor]):
     if not planes:
         raise ValueError("empty field")

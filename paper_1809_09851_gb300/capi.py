@@ -17,6 +17,7 @@ STATUS = {
     0: "FDBB_OK", 1: "FDBB_ERR_ARG", 2: "FDBB_ERR_NULLPTR", 3: "FDBB_ERR_ALIGN",
     4: "FDBB_ERR_DTYPE", 5: "FDBB_ERR_CUDA", 6: "FDBB_ERR_TIMEOUT", 7: "FDBB_ERR_NOMEM",
 }
+STATUS_CODES = {name: code for code, name in STATUS.items()}
 FDBB_F64, FDBB_F32, FDBB_F16, FDBB_BF16, FDBB_F64_DW = 0, 1, 2, 3, 4
 FDBB_PTR_OTHER, FDBB_PTR_DEVICE, FDBB_PTR_HOST, FDBB_PTR_MANAGED = 0, 1, 2, 3
 
@@ -100,6 +101,16 @@ SIGNATURES.update({
     "fdbb_flux_jac_prim_eos": [_EP, _i, _i, _i64, _i, _PP, _PP, _vp],
 })
 
+class LaunchInfo(ctypes.Structure):
+    """struct fdbb_launch_info (include/fdbb.h)."""
+    _fields_ = [("kernel", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+FDBB_KERNEL_NONE, FDBB_KERNEL_DIRECT, FDBB_KERNEL_STAGED = 0, 1, 2
+SIGNATURES["fdbb_last_launch"] = [ctypes.POINTER(LaunchInfo)]
+
 _lib = None
 
 
@@ -130,6 +141,8 @@ def lib():
         L.fdbb_device_status.restype = _i
         L.fdbb_pointer_kind.argtypes = [_vp]
         L.fdbb_pointer_kind.restype = _i
+        L.fdbb_set_wait_limit.argtypes = [_i]
+        L.fdbb_set_wait_limit.restype = _i
         _lib = L
     return _lib
 
@@ -141,11 +154,42 @@ def planes(ptrs):
     return (ctypes.c_void_p * max(1, len(ptrs)))(*[p if p else None for p in ptrs])
 
 
+# With CHECK_DEVICE (environment FDBB_CHECK_DEVICE=1) every launching call
+# synchronises with the device afterwards and raises FdbbError(FDBB_ERR_TIMEOUT)
+# if a staged kernel's bounded wait for its input copies ran out (that kernel
+# left its outputs unwritten).  Off by default: it makes every call blocking.
+CHECK_DEVICE = os.environ.get("FDBB_CHECK_DEVICE", "0") == "1"
+_NO_LAUNCH = {"fdbb_last_launch"}
+
+
+def check_device() -> None:
+    """Synchronise and raise FdbbError if a bounded device wait ran out since
+    the previous check (fdbb_device_status)."""
+    st = device_status()
+    if st != FDBB_OK:
+        raise FdbbError("fdbb_device_status", st)
+
+
 def call(name: str, *args) -> None:
     """Call fdbb_<name> and raise FdbbError on a non-zero status."""
     st = getattr(lib(), name)(*args)
     if st != FDBB_OK:
         raise FdbbError(name, st)
+    if CHECK_DEVICE and name not in _NO_LAUNCH:
+        check_device()
+
+
+def last_launch() -> LaunchInfo:
+    """Kernel, grid and shared memory of this thread's last point-wise launch."""
+    info = LaunchInfo()
+    call("fdbb_last_launch", ctypes.byref(info))
+    return info
+
+
+def device_status() -> int:
+    """fdbb_device_status(): synchronises; FDBB_ERR_TIMEOUT if a bounded device
+    wait ran out since the previous call, else FDBB_OK."""
+    return lib().fdbb_device_status()
 
 
 def status_string(status: int) -> str:
@@ -153,4 +197,5 @@ def status_string(status: int) -> str:
 
 
 def exported_symbols():
-    return ["fdbb_status_string", "fdbb_version", "fdbb_device_status", "fdbb_pointer_kind", *SIGNATURES.keys()]
+    return ["fdbb_status_string", "fdbb_version", "fdbb_device_status", "fdbb_pointer_kind", "fdbb_set_wait_limit",
+            *SIGNATURES.keys()]

@@ -9,11 +9,20 @@
 
 namespace fdbb {
 
+int current_device_slot() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return dev >= 0 && dev < kMaxDevices ? dev : -1;
+}
+
 int device_sm_count() {
-  static std::atomic<int> cache[64];
+  static std::atomic<int> cache[kMaxDevices];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-  const bool cached = dev >= 0 && dev < 64;
+  const bool cached = dev >= 0 && dev < kMaxDevices;
   if (cached) {
     const int v = cache[dev].load(std::memory_order_relaxed);
     if (v > 0) return v;
@@ -23,6 +32,22 @@ int device_sm_count() {
   if (cached) cache[dev].store(v, std::memory_order_relaxed);
   return v;
 }
+
+namespace {
+thread_local fdbb_launch_info t_last_launch = {};
+std::atomic<int> g_wait_limit{-1};
+}  // namespace
+
+void record_launch(int kernel, int grid, int block, int smem_bytes, int points_per_thread) {
+  t_last_launch.kernel = kernel;
+  t_last_launch.grid = grid;
+  t_last_launch.block = block;
+  t_last_launch.smem_bytes = smem_bytes;
+  t_last_launch.points_per_thread = points_per_thread;
+  t_last_launch.reserved = 0;
+}
+
+int wait_limit_setting() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 }  // namespace fdbb
 
@@ -82,6 +107,8 @@ fdbb_status take_out1(KArgs& a, int slot, void* p) {
 KArgs make_args(int64_t n, double gamma, double cv = 0.0) {
   KArgs a = {};
   a.n = n;
+  const int polls = fdbb::wait_limit_setting();
+  a.wait_override = polls < 0 ? 0 : polls + 1;
   const double g = gamma, a1 = gamma - 1.0;
   const double tcv = cv > 0.0 ? 1.0 / (a1 * cv) : 1.0;
   const double kd[8] = {g, a1, 3.0 - g, 2.0 / a1, 1.0 / a1, -g, g / a1, tcv};
@@ -309,6 +336,16 @@ fdbb_status fdbb_device_status(void) {
                          fdbb::wait_timeouts_eos_f64dw_nasg3() + fdbb::wait_timeouts_eos_f64dw_vdw1() +
                          fdbb::wait_timeouts_eos_f64dw_vdw2() + fdbb::wait_timeouts_eos_f64dw_vdw3();
   return n ? FDBB_ERR_TIMEOUT : FDBB_OK;
+}
+
+int fdbb_set_wait_limit(int polls) {
+  return fdbb::g_wait_limit.exchange(polls < 0 ? -1 : polls, std::memory_order_relaxed);
+}
+
+fdbb_status fdbb_last_launch(fdbb_launch_info* info) {
+  if (info == nullptr) return FDBB_ERR_NULLPTR;
+  *info = fdbb::t_last_launch;
+  return FDBB_OK;
 }
 
 fdbb_status fdbb_v_mag2(int dim, int64_t n, fdbb_dtype t, const void* const* U, void* y, fdbb_stream_t stream) {

@@ -16,10 +16,12 @@
 //   (s+2)%3, which step s-1 read and step s+1 will fill.
 // The maximum is order independent, so a grid's results do not depend on
 // which other grids share the launch.
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "fdbb.h"
 #include "fdbb_device.cuh"
@@ -654,20 +656,33 @@ template <class T> constexpr size_t step_smem() {
   return std::is_same<T, float>::value ? kPairRing * sizeof(PairTile) : fv_step_smem(sizeof(T));
 }
 
+// Resident blocks per SM of the step (step = true, after its opt-in to more
+// than 48 KB of dynamic shared memory) or wave-speed kernel on the current
+// device.  Function attributes belong to each device's context, so the opt-in
+// and the occupancy are taken, and cached, per device.
 template <class T> int fv_blocks_per_sm(bool step) {
-  static const int bs = [] {
-    int b = 0;
-    cudaFuncSetAttribute(step_kernel<T>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<T>());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<T>(), kFvThreads, step_smem<T>()) != cudaSuccess)
-      b = 1;
-    return b > 0 ? b : 1;
-  }();
-  static const int bm = [] {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fv_max_speed<T>, kFvThreads, 0) != cudaSuccess) b = 1;
-    return b > 0 ? b : 1;
-  }();
-  return step ? bs : bm;
+  static std::atomic<int> cache[2][kMaxDevices];
+  const int slot = current_device_slot();
+  if (slot >= 0) {
+    const int v = cache[step][slot].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int b = 0;
+  cudaError_t e = cudaSuccess;
+  if (step) {
+    e = cudaFuncSetAttribute(step_kernel<T>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<T>());
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<T>(), kFvThreads, step_smem<T>());
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fv_max_speed<T>, kFvThreads, 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b = 1;
+  }
+  if (b <= 0) b = 1;
+  if (slot >= 0 && e == cudaSuccess) cache[step][slot].store(b, std::memory_order_relaxed);
+  return b;
 }
 
 template <class T> cudaError_t fv_launch(const FvArgs& a, bool step, cudaStream_t s) {
@@ -822,18 +837,21 @@ static __device__ __align__(256) double g_fv_noalloc_smax[3 * FDBB_FV_MAX_GRIDS]
 // Device address of g_fv_noalloc_smax on the current device.  In host code the
 // symbol's name is a host-side stand-in, not a device address, so the address
 // is looked up with cudaGetSymbolAddress, with the device current, the first
-// time the entry point runs on that device, and cached.
+// time the entry point runs on that device, and cached by device number for
+// the rest of the process (a device reset would invalidate it; the header
+// says so).
 fdbb_status noalloc_scratch(void** out) {
   static std::mutex mu;
-  static void* cache[64] = {};
+  static std::unordered_map<int, void*> cache;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return FDBB_ERR_CUDA;
   }
   std::lock_guard<std::mutex> lock(mu);
-  if (dev >= 0 && dev < 64 && cache[dev] != nullptr) {
-    *out = cache[dev];
+  const auto it = cache.find(dev);
+  if (it != cache.end()) {
+    *out = it->second;
     return FDBB_OK;
   }
   void* p = nullptr;
@@ -841,7 +859,7 @@ fdbb_status noalloc_scratch(void** out) {
     cudaGetLastError();
     return FDBB_ERR_CUDA;
   }
-  if (dev >= 0 && dev < 64) cache[dev] = p;
+  cache.emplace(dev, p);
   *out = p;
   return FDBB_OK;
 }
@@ -852,23 +870,26 @@ fdbb_status fv_step_noalloc(int ngrids, const fdbb_fv_grid* grids, int64_t vcell
   if (ngrids < 0 || !(gamma > 1.0) || !std::isfinite(gamma) || !(cfl > 0.0 && std::isfinite(cfl)))
     return FDBB_ERR_ARG;
   if (ngrids > 0 && grids == nullptr) return FDBB_ERR_NULLPTR;
-  void* scratch = nullptr;
-  const fdbb_status sst = noalloc_scratch(&scratch);
-  if (sst != FDBB_OK) return sst;
   FvArgs a;
   a.ngrids = ngrids;
   a.vcells = vcells;
   a.gamma = gamma;
   a.cfl = cfl;
-  a.smax = scratch;
   for (int i = 0; i < ngrids; ++i) {
     a.g[i] = grids[i];
     a.g[i].slot = i;   // slot and phase of the caller's table are not used:
     a.g[i].phase = 0;  // every call recomputes the wave speed of U
   }
-  const fdbb_status st = fv_check(ngrids, a.g, vcells, t, scratch, true, nullptr);
+  // Arguments first, before any CUDA call; the scratch pointer is not known
+  // yet, so the check sees a stand-in with the array's alignment.
+  alignas(256) static const double kStandIn = 0.0;
+  const fdbb_status st = fv_check(ngrids, a.g, vcells, t, &kStandIn, true, nullptr);
   if (st != FDBB_OK) return st;
   if (ngrids == 0 || vcells == 0) return FDBB_OK;
+  void* scratch = nullptr;
+  const fdbb_status sst = noalloc_scratch(&scratch);
+  if (sst != FDBB_OK) return sst;
+  a.smax = scratch;
   fv_tiles(a);
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // the slots keep the previous call's contents: clear them first

@@ -25,6 +25,8 @@ struct KArgs {
   int64_t n;
   int nin;       // input planes in use (the leading non-NULL entries of in[])
   int flags;     // launch options (kDirectOnly); not read by the kernels
+  int wait_override;  // staged kernels' polls per bounded wait: 0 = the default
+                      // limit, k > 0 = k - 1 polls (fdbb_set_wait_limit)
   double kd[8];  // gamma, gamma-1, 3-gamma, 2/(gamma-1), 1/(gamma-1), -gamma,
                  // gamma/(gamma-1), 1/((gamma-1) c_v)
   float kf[8];   // the same, rounded once to float
@@ -49,6 +51,19 @@ struct LaunchReq {
 
 // Streaming multiprocessors of the current device (cached per device).
 int device_sm_count();
+
+// The current device, for per-device caches of kMaxDevices entries (-1 when
+// it cannot be read or lies beyond the caches; callers then do not cache).
+constexpr int kMaxDevices = 64;
+int current_device_slot();
+
+// Host-side record of the calling thread's last point-wise launch
+// (fdbb_last_launch): kernel kind 1 = direct, 2 = staged.
+void record_launch(int kernel, int grid, int block, int smem_bytes, int points_per_thread);
+
+// Poll limit for the staged kernels' bounded waits (fdbb_set_wait_limit;
+// < 0: the kernels' default).
+int wait_limit_setting();
 
 // Defined once per storage type (one translation unit each).
 cudaError_t dispatch_f64(const LaunchReq& r, const KArgs& a);

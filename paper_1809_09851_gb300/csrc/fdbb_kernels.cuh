@@ -22,6 +22,7 @@
 // source.
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "fdbb_device.cuh"
@@ -715,11 +716,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
-// Wait for the phase with the given parity to complete; false after
-// kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity to complete; false after `limit`
+// polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = kWaitLimit) {
   const uint32_t addr = smem_addr(bar);
-  for (int i = 0; i < kWaitLimit; ++i) {
+  for (int i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -786,6 +787,9 @@ __device__ __forceinline__ void staged_body(const KArgs& a) {
   const int64_t ntiles = a.n / TILE;
   const uint32_t plane_bytes = TILE * sizeof(T);
   const auto k = Mdl::template make<R>(a);
+  // polls per wait for a tile's copies (the drain after a timeout below keeps
+  // the default limit, so every issued copy lands before the block exits)
+  const int limit = a.wait_override > 0 ? a.wait_override - 1 : kWaitLimit;
   // The j-th tile of this block is tile blockIdx.x + j * gridDim.x, streamed
   // into stage j % kStages; its copy completes phase j / kStages of that
   // stage's mbarrier.
@@ -810,7 +814,7 @@ __device__ __forceinline__ void staged_body(const KArgs& a) {
   int j = 0;
   for (; has_tile(j); ++j) {
     const int s = j % kStages;
-    const bool ok = mbar_wait(&bars[s], (uint32_t)(j / kStages) & 1u);
+    const bool ok = mbar_wait(&bars[s], (uint32_t)(j / kStages) & 1u, limit);
     if (__syncthreads_or(!ok)) break;
     const SmemSrc<T, VW, TILE> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW};
     const int64_t i0 = (blockIdx.x + (int64_t)j * gridDim.x) * TILE + (int64_t)tid * VW;
@@ -866,18 +870,36 @@ inline unsigned int take_wait_timeouts_tu() {
 
 // Persistent grid of the direct kernel: enough blocks to fill every SM at its
 // occupancy, no more than there are chunks.
+// Resident blocks per SM of `kern` with `smem` bytes of dynamic shared memory
+// on the current device, cached per device in `cache` (one per kernel and
+// shared-memory size).
+template <class K>
+int blocks_per_sm(K kern, size_t smem, std::atomic<int> (&cache)[kMaxDevices]) {
+  const int slot = current_device_slot();
+  if (slot >= 0) {
+    const int v = cache[slot].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    b = 1;
+  }
+  if (b <= 0) b = 1;
+  if (slot >= 0) cache[slot].store(b, std::memory_order_relaxed);
+  return b;
+}
+
 template <class Op, class T, class R, class Mdl> cudaError_t launch_direct(const KArgs& a, cudaStream_t stream) {
-  static const int blocks_per_sm = [] {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pointwise<Op, T, R, Mdl>, kThreads, 0) != cudaSuccess) b = 1;
-    return b > 0 ? b : 1;
-  }();
+  static std::atomic<int> bps_cache[kMaxDevices];
+  const int bps = blocks_per_sm(k_pointwise<Op, T, R, Mdl>, 0, bps_cache);
   constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   const int64_t nchunk = (a.n + VW - 1) / VW;
   const int64_t need = (nchunk + kThreads - 1) / kThreads;
-  const int64_t cap = (int64_t)device_sm_count() * blocks_per_sm;
+  const int64_t cap = (int64_t)device_sm_count() * bps;
   const int grid = (int)(need < cap ? need : cap);
   k_pointwise<Op, T, R, Mdl><<<grid, kThreads, 0, stream>>>(a);
+  record_launch(1, grid, kThreads, 0, VW);
   return cudaGetLastError();
 }
 
@@ -892,21 +914,23 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
     else
       return k_staged<Op, T, R, Mdl>;
   }();
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  if (attr != cudaSuccess) return attr;
-  const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T);
-  static int bps_cache[Op::kIn + 1] = {};  // blocks per SM for each nin
-  int& bps = bps_cache[a.nin];
-  if (bps == 0) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, smem) != cudaSuccess) b = 1;
-    bps = b > 0 ? b : 1;
+  // the opt-in to more than 48 KB of dynamic shared memory is a property of
+  // the kernel in each device's context: set it once per device
+  static std::atomic<int> attr_set[kMaxDevices];
+  const int slot = current_device_slot();
+  if (slot < 0 || !attr_set[slot].load(std::memory_order_relaxed)) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    if (e != cudaSuccess) return e;
+    if (slot >= 0) attr_set[slot].store(1, std::memory_order_relaxed);
   }
+  const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T);
+  static std::atomic<int> bps_cache[Op::kIn + 1][kMaxDevices];  // blocks per SM for each nin
+  const int bps = blocks_per_sm(kern, smem, bps_cache[a.nin]);
   const int64_t ntiles = a.n / TILE;
   const int64_t cap = (int64_t)device_sm_count() * bps;
   const int grid = (int)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
   kern<<<grid, kThreads, smem, stream>>>(a);
+  record_launch(2, grid, kThreads, (int)smem, VW);
   return cudaGetLastError();
 }
 

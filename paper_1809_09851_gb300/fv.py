@@ -9,7 +9,6 @@ grid, storage dtype) is owned by the caller.
 """
 from __future__ import annotations
 
-import math
 from typing import List, Optional, Sequence
 
 import torch
@@ -95,44 +94,6 @@ def rusanov_step(grids: Sequence[FvGrid], smax: torch.Tensor, gamma: float = 1.4
                   _stream(stream, smax.device))
     for g in grids:
         g.advance()
-
-
-def primitive_on_device(n: int, seed: int, dtype, device, amplitude: float = 0.1):
-    """The smooth seeded initial data of a serving request, evaluated on the
-    device in the state's precision (rho, v = 0, p), from the sinusoid
-    parameters of synth.smooth_params: 1 + amplitude * g / max |g| with g a sum
-    of three sinusoids sin(2 pi k.x + phi).  The per-axis phase terms
-    (2 pi k_j x_j, the phase folded into the x term) are formed on the host
-    and sent in one copy; each sinusoid then costs two broadcast adds, the
-    sine and the accumulation on the device."""
-    import numpy as np
-
-    from . import synth
-    x = (np.arange(n) + 0.5) / n
-    terms = []
-    params = synth.smooth_params(seed)
-    for k, ph, a in params:
-        for m in range(3):
-            terms.append(2 * math.pi * int(k[m, 0]) * x + float(ph[m]))
-            terms.append(2 * math.pi * int(k[m, 1]) * x)
-            terms.append(2 * math.pi * int(k[m, 2]) * x)
-    # one asynchronous copy from page-locked memory (the allocator keeps the
-    # buffer until the copy has run), so admission never waits on the stream
-    host = torch.empty((len(terms), n), dtype=torch.float64, pin_memory=torch.cuda.is_available())
-    host.numpy()[:] = np.stack(terms)
-    t_dev = host.to(device=device, non_blocking=True).to(dtype)  # (18, n)
-    planes = []
-    for p_i, (k, ph, a) in enumerate(params):
-        g = None
-        for m in range(3):
-            tx, ty, tz = t_dev[9 * p_i + 3 * m], t_dev[9 * p_i + 3 * m + 1], t_dev[9 * p_i + 3 * m + 2]
-            s = (tx[None, None, :] + ty[None, :, None]) + tz[:, None, None]
-            s.sin_()
-            g = s.mul_(float(a[m])) if g is None else g.add_(s, alpha=float(a[m]))
-        gmax = g.abs().max()
-        planes.append(g.div_(gmax).mul_(amplitude).add_(1.0).reshape(-1))
-    zero = torch.zeros(n ** 3, dtype=dtype, device=device)
-    return [planes[0], zero, zero.clone(), zero.clone(), planes[1]]
 
 
 def new_grid(V: Sequence[torch.Tensor], n: int, slot: int, smax: torch.Tensor, gamma: float = 1.4,

@@ -14,7 +14,9 @@ Each request asks for `steps` Rusanov steps on its own periodic n^3 grid
   * retires a request when its last step's event completes, recording its
     completion time on the device clock, and frees its memory and slot.
 Latency = completion - arrival (seconds on the same clock); throughput =
-cell-steps / wall time.  A grid's results do not depend on the other grids
+cell-steps / wall time.  Admission, each batched step and each retirement are
+NVTX ranges ("fdbb.admit", "fdbb.step", "fdbb.retire") for profilers that
+show a timeline.  A grid's results do not depend on the other grids
 in its launches (per-cell arithmetic is fixed and the time-step reduction is
 an exact maximum), so a request's answer is the same alone and in the mix.
 """
@@ -28,6 +30,15 @@ from typing import Callable, Dict, List, Optional
 import torch
 
 from . import fv, synth
+
+
+def _range(name: str):
+    """NVTX range around a phase of the loop (a no-op when NVTX is unavailable)."""
+    try:
+        return torch.cuda.nvtx.range(name)
+    except Exception:  # pragma: no cover - builds without NVTX
+        import contextlib
+        return contextlib.nullcontext()
 
 
 class FvTimeout(RuntimeError):
@@ -145,35 +156,37 @@ class FVServer:
 
         def retire(entry):
             ev, finishing = entry
-            wait_event(ev, self.wait_timeout)
-            t_done = ev0.elapsed_time(ev) / 1e3
-            for job in finishing:
-                job.t_done = t_done
-                rep.latencies[job.req.rid] = t_done - (job.req.arrival if realtime else 0.0)
-                if self.keep_results:
-                    rep.results[job.req.rid] = [u.clone() for u in job.grid.U]
-                self.used -= job.nbytes
-                self.free_slots.append(job.grid.slot)
-                job.grid = None
+            with _range("fdbb.retire"):
+                wait_event(ev, self.wait_timeout)
+                t_done = ev0.elapsed_time(ev) / 1e3
+                for job in finishing:
+                    job.t_done = t_done
+                    rep.latencies[job.req.rid] = t_done - (job.req.arrival if realtime else 0.0)
+                    if self.keep_results:
+                        rep.results[job.req.rid] = [u.clone() for u in job.grid.U]
+                    self.used -= job.nbytes
+                    self.free_slots.append(job.grid.slot)
+                    job.grid = None
 
         while pending or active or inflight:
             now = time.perf_counter() - t0
             # admission, in arrival order, while the state fits the budget
             admitted = 0
-            while pending and (not realtime or pending[0].arrival <= now):
-                if self.admit_per_iter is not None and admitted >= self.admit_per_iter and active:
-                    break
-                req = pending[0]
-                need = self.state_bytes(req.n)
-                if need > self.budget:
-                    rep.rejected.append(req.rid)
-                    pending.popleft()
-                    continue
-                if (self.used + need > self.budget or not self.free_slots
-                        or (self.max_active is not None and len(active) >= self.max_active)):
-                    break
-                active.append(self._admit(pending.popleft(), now))
-                admitted += 1
+            with _range("fdbb.admit"):
+                while pending and (not realtime or pending[0].arrival <= now):
+                    if self.admit_per_iter is not None and admitted >= self.admit_per_iter and active:
+                        break
+                    req = pending[0]
+                    need = self.state_bytes(req.n)
+                    if need > self.budget:
+                        rep.rejected.append(req.rid)
+                        pending.popleft()
+                        continue
+                    if (self.used + need > self.budget or not self.free_slots
+                            or (self.max_active is not None and len(active) >= self.max_active)):
+                        break
+                    active.append(self._admit(pending.popleft(), now))
+                    admitted += 1
             rep.max_active = max(rep.max_active, len(active))
             if not active:
                 if inflight:
@@ -184,7 +197,8 @@ class FVServer:
                 continue
             # one batched step for every active grid
             grids = [j.grid for j in active]
-            fv.rusanov_step(grids, self.smax, self.gamma, self.cfl, stream=self.stream)
+            with _range("fdbb.step"):
+                fv.rusanov_step(grids, self.smax, self.gamma, self.cfl, stream=self.stream)
             rep.iterations += 1
             rep.launches += -(-len(grids) // fv.MAX_GRIDS)
             rep.cell_steps += sum(g.n ** 3 for g in grids)

@@ -162,3 +162,27 @@ def test_fv_init_smooth_argument_errors(L):
     bad = (ctypes.c_double * 30)(*([1.0] * 29 + [float("inf")]))
     g.U[3] = A + 768
     assert L.fdbb_fv_init_smooth(ctypes.byref(g), 1.4, 0.1, bad, F32, A, None) == 1
+
+
+def test_launch_record_and_wait_limit_need_no_device(L):
+    """fdbb_last_launch and fdbb_set_wait_limit are host-side: a thread that
+    launched nothing reports FDBB_KERNEL_NONE, NULL is rejected, and the wait
+    limit setting round-trips (negative values restore the default, -1)."""
+    import threading
+    out = {}
+
+    def probe():
+        out["info"] = capi.last_launch()
+
+    t = threading.Thread(target=probe)
+    t.start()
+    t.join()
+    assert out["info"].kernel == capi.FDBB_KERNEL_NONE
+    assert L.fdbb_last_launch(None) == 2
+    prev = L.fdbb_set_wait_limit(5)
+    try:
+        assert L.fdbb_set_wait_limit(0) == 5
+        assert L.fdbb_set_wait_limit(-7) == 0
+        assert L.fdbb_set_wait_limit(-1) == -1
+    finally:
+        L.fdbb_set_wait_limit(prev)

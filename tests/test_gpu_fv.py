@@ -204,3 +204,29 @@ def test_smooth_initial_state_on_device(n, dtype, tol):
                                                 synth.smooth_perturbation(r.n, r.seed)]).run(reqs, realtime=False).results[0]
     for x, y in zip(a, b):
         assert torch.allclose(x, y, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("axis", [0, 1, 2], ids=["x", "y", "z"])
+def test_fv_step_hand_values(axis, dtype):
+    """One step of the batched kernels on the 4-cell contact of
+    tests/golden/rusanov_contact_step.txt gives the hand-derived density,
+    momentum u rho' and energy 2.5 + u^2 rho'/2, and the hand-derived dt, in
+    every direction (FP64: 1e-13 relative; FP32: 2e-5)."""
+    from test_oracle_pins import _rusanov_golden, contact_state
+    n = 4
+    tol = 1e-13 if dtype == torch.float64 else 2e-5
+    for name, cs in _rusanov_golden().items():
+        u = cs["u"]
+        U, coord = contact_state(n, axis, u)
+        smax = torch.zeros(3, dtype=dtype, device=DEV)
+        g = fv.grid_from_conservative(_dev(U, dtype), n, 0, smax, G_, dt_log_steps=1)
+        fv.rusanov_step([g], smax, G_, 0.4)
+        torch.cuda.synchronize()
+        want = np.array([cs["rho"][i] for i in range(n)])[coord]
+        np.testing.assert_allclose(g.dt_log.cpu().numpy()[0], cs["dt"], rtol=tol, err_msg=name)
+        np.testing.assert_allclose(g.U[0].double().cpu().numpy(), want, rtol=tol, err_msg=name)
+        np.testing.assert_allclose(g.U[1 + axis].double().cpu().numpy(), u * want, rtol=tol, atol=tol,
+                                   err_msg=name)
+        np.testing.assert_allclose(g.U[4].double().cpu().numpy(), 2.5 + 0.5 * u * u * want, rtol=tol,
+                                   err_msg=name)

@@ -40,6 +40,21 @@ def _lib():
 DEV = "cuda:0"
 
 
+def sm_count() -> int:
+    return torch.cuda.get_device_properties(DEV).multi_processor_count
+
+
+def staged_n(tile: int, tail: int) -> int:
+    """A size at which every SM gets at least four tiles of `tile` points (the
+    staged kernel's threshold), plus a ragged tail."""
+    return 4 * sm_count() * tile + tail
+
+
+def assert_staged():
+    info = capi.last_launch()
+    assert info.kernel == capi.FDBB_KERNEL_STAGED, (info.kernel, info.grid, info.points_per_thread)
+
+
 def fields(n, D, seed=1809):
     V = synth.euler3d(n, seed=seed, D=D) if D > 1 else synth.euler1d(n, seed=seed)
     U = oracle.cons_from_prim(D, G, V)
@@ -251,6 +266,59 @@ def test_dw_out_of_range_points_fall_back_to_fp64():
     assert torch.isnan(p_dw[40]) and torch.isnan(p_nat[40])
 
 
+def test_dw_out_of_range_points_fall_back_on_staged_path():
+    """The same out-of-range, tiny, huge and non-finite points, at a size
+    where the staged kernel runs: most sit inside shared-memory tiles (where
+    the IEEE-double fallback recomputes the chunk from the staged inputs), a
+    few in the ragged tail.  Fused pass (every Jacobian direction), packed
+    flux VJP (pairs with one or both lanes out of range) and cons -> prim."""
+    n, D = staged_n(1024, 4103), 3
+    V, U, W = fields(n, D, seed=98)
+    U = [u.copy() for u in U]
+    W = [w.copy() for w in W]
+    last = n - 300  # inside the last 256- and 512-point tiles
+    scaled = ((10, 1e-30), (11, 1e30), (12, 1e-9), (513, 1e12), (4100, 2.0 ** -25), (70001, 1e-20),
+              (70002, 3e20), (last, 1e-12), (n - 3, 1e15), (n - 1, 2.0 ** -26))
+    for i, sc in scaled:
+        for k in range(5):
+            U[k][i] *= sc
+    U[1][20] = 1e-40            # tiny nonzero momentum
+    U[2][21] = -3e-300
+    U[3][90001] = 1e-38
+    W[3][30] = 1e-200           # tiny characteristic weight
+    W[0][31] = 5e25
+    W[4][n - 2] = 1e-33         # in the tail
+    Ud, _ = quantise(U, torch.float64)
+    Wd, _ = quantise(W, torch.float64)
+    for dj in range(D):
+        ref, S = oracle.euler_fused(D, dj, G, U, W, scale=True)
+        Fo, Ao, Yo = blocks.euler_fused(Ud, Wd, dj, G, dw=True)
+        assert_staged()
+        check(host([*Fo, *Ao, *Yo]), ref, S, torch.float64, f"staged dw fallback fused {dj}")
+    ref, S = oracle.prim_from_cons(D, G, U, scale=True)
+    Vo = blocks.prim_from_cons(Ud, G, dw=True)
+    assert_staged()
+    check(host(Vo), ref, S, torch.float64, "staged dw fallback prim")
+    Gc = [g.copy() for g in synth.cotangent(n, 5)]
+    Gc[4][41] = 1e-35
+    Gc[1][50] = 3e27
+    Gc[2][last + 1] = 1e-30
+    Gd, _ = quantise(Gc, torch.float64)
+    for d in range(D):
+        ref, S = oracle.flux_vjp(D, d, G, U, Gc, scale=True)
+        gU = blocks.flux_vjp(Ud, Gd, d, G, dw=True)
+        assert_staged()
+        check(host(gU), ref, S, torch.float64, f"staged dw fallback vjp {d}")
+    # a NaN state inside a staged tile gives NaN in both arithmetics
+    U[0][4000] = np.nan
+    Ud, _ = quantise(U, torch.float64)
+    p_dw, _ = blocks.eos(Ud, G, dw=True)
+    assert_staged()
+    p_nat, _ = blocks.eos(Ud, G)
+    assert torch.isnan(p_dw[4000]) and torch.isnan(p_nat[4000])
+    assert capi.device_status() == 0
+
+
 def test_dw_copies_are_bit_exact():
     n, D = 1001, 3
     V, U, W = fields(n, D, seed=5)
@@ -316,8 +384,8 @@ def test_full_size_fused_sampled(dtype, dw):
 def test_staged_path_parity(dtype, dw):
     """n = 4 tiles per SM of the widest tile (1024 points) plus a ragged tail,
     every point against the oracle, for ops with 5, 10 and 10-with-skipped-W
-    input planes."""
-    n = 4 * 152 * 1024 + 4099
+    input planes; each call is checked to have taken the staged kernel."""
+    n = staged_n(1024, 4099)
     D = 3
     V, U, W = fields(n, D, seed=2024)
     Ud, Uq = quantise(U, dtype)
@@ -326,28 +394,36 @@ def test_staged_path_parity(dtype, dw):
     Gd, Gq = quantise(Gc, dtype)
     ref, S = oracle.euler_fused(D, 1, G, Uq, Wq, scale=True)
     Fo, Ao, Yo = blocks.euler_fused(Ud, Wd, 1, G, dw=dw)
+    assert_staged()
     check(host([*Fo, *Ao, *Yo]), ref, S, dtype, "staged fused")
     Fo, Ao, _ = blocks.euler_fused(Ud, None, 2, G, out=(blocks._alloc(15, n, dtype, DEV),
                                                         blocks._alloc(25, n, dtype, DEV), None), dw=dw)
+    assert_staged()
     ref, S = oracle.euler_fused(D, 2, G, Uq, Wq, scale=True)
     check(host([*Fo, *Ao]), ref[:40], S[:40], dtype, "staged fused without W")
     ref, S = oracle.flux_vjp(D, 0, G, Uq, Gq, scale=True)
-    check(host(blocks.flux_vjp(Ud, Gd, 0, G, dw=dw)), ref, S, dtype, "staged vjp")
+    gU = blocks.flux_vjp(Ud, Gd, 0, G, dw=dw)
+    assert_staged()
+    check(host(gU), ref, S, dtype, "staged vjp")
     ref, S = oracle.prim_from_cons(D, G, Uq, scale=True)
-    check(host(blocks.prim_from_cons(Ud, G, dw=dw)), ref, S, dtype, "staged prim")
+    Vo = blocks.prim_from_cons(Ud, G, dw=dw)
+    assert_staged()
+    check(host(Vo), ref, S, dtype, "staged prim")
     ref, S = oracle.v_mag2(D, Uq, scale=True)
-    check(host([blocks.v_mag2(Ud, dw=dw)]), ref, S, dtype, "staged v_mag2")
-    from paper_1809_09851_gb300 import capi
-    assert capi.lib().fdbb_device_status() == 0  # no bounded wait ran out
+    y = blocks.v_mag2(Ud, dw=dw)
+    assert_staged()
+    check(host([y]), ref, S, dtype, "staged v_mag2")
+    assert capi.device_status() == 0  # no bounded wait ran out
 
 
-@pytest.mark.parametrize("n", [4099, 4 * 152 * 512 + 1001], ids=["direct", "staged"])
-def test_packed_vjp_lanes_are_independent(n):
+@pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
+def test_packed_vjp_lanes_are_independent(staged):
     """The double-word flux VJP runs two points per thread as the two lanes of
     packed FP32x2 values.  A point's result must not depend on the point that
     shares its pair: shifting the field by one point re-pairs every point, and
     the results are the same bits (in-range fields, so no pair falls back)."""
     D = 3
+    n = staged_n(512, 1001) if staged else 4099
     _, U, _ = fields(n + 1, D, seed=77)
     Gc = synth.cotangent(n + 1, 5)
     # keep every momentum and cotangent at magnitude >= 1e-5 (a normal draw
@@ -359,6 +435,8 @@ def test_packed_vjp_lanes_are_independent(n):
     Gd = [torch.from_numpy(g).to(DEV) for g in Gc]
     a = blocks.flux_vjp([u[:n].clone() for u in Ud], [g[:n].clone() for g in Gd], 0, G, dw=True)
     b = blocks.flux_vjp([u[1:].clone() for u in Ud], [g[1:].clone() for g in Gd], 0, G, dw=True)
+    kind = capi.last_launch().kernel
+    assert kind == (capi.FDBB_KERNEL_STAGED if staged else capi.FDBB_KERNEL_DIRECT)
     for k in range(5):
         assert torch.equal(a[k][1:], b[k][:-1]), k
 
@@ -404,13 +482,15 @@ def test_roe_blocks(D, n, dtype, dw):
 
 @pytest.mark.parametrize("dw", [False, True], ids=["f64", "f64dw"])
 def test_roe_flux_staged_path(dw):
-    n, D = 4 * 152 * 512 + 333, 3
+    n, D = staged_n(512, 333), 3
     _, UL, _ = fields(n, D, seed=310)
     _, UR, _ = fields(n, D, seed=311)
     ULd, _ = quantise(UL, torch.float64)
     URd, _ = quantise(UR, torch.float64)
     ref, S = oracle.roe_flux(D, 1, G, UL, UR, scale=True)
-    check(host(blocks.roe_flux(ULd, URd, 1, G, dw=dw)), ref, S, torch.float64, "staged roe flux")
+    F = blocks.roe_flux(ULd, URd, 1, G, dw=dw)
+    assert_staged()
+    check(host(F), ref, S, torch.float64, "staged roe flux")
 
 
 # ---------------------------------------------------------------------------

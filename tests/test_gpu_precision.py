@@ -18,7 +18,7 @@ import pytest
 import torch
 
 import oracle
-from paper_1809_09851_gb300 import blocks, synth
+from paper_1809_09851_gb300 import blocks, capi, synth
 
 pytestmark = pytest.mark.gpu
 G_ = 1.4
@@ -56,14 +56,23 @@ def _rel(err, ref):
     return err / np.maximum(np.abs(ref), 1e-300)
 
 
+def staged_n(tail: int) -> int:
+    """Every SM gets at least four 1024-point tiles (the f32/f16/bf16 tile):
+    the staged kernel the benchmark times runs, plus a ragged tail."""
+    return 4 * torch.cuda.get_device_properties(DEV).multi_processor_count * 1024 + tail
+
+
+@pytest.mark.parametrize("path", ["direct", "staged"])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16], ids=["f32", "f16", "bf16"])
-def test_precision_form(dtype):
-    n = 1 << 18
+def test_precision_form(dtype, path):
+    n = (1 << 18) if path == "direct" else staged_n(4099)
     U, W, vac, fast = precision_fields(n)
     assert 0.04 < vac.mean() < 0.06 and 0.04 < fast.mean() < 0.06
     Ud, Uq = quantise(U, dtype)
     Wd, Wq = quantise(W, dtype)
     F, A, Y = blocks.euler_fused(Ud, Wd, 0, G_)
+    want = capi.FDBB_KERNEL_STAGED if path == "staged" else capi.FDBB_KERNEL_DIRECT
+    assert capi.last_launch().kernel == want
     got = host([*F, *A, *Y])
     ref, S = oracle.euler_fused(3, 0, G_, Uq, Wq, scale=True)
     u, tiny = U_STORE[dtype], TINY[dtype]
@@ -87,6 +96,7 @@ def test_precision_form(dtype):
         assert ok[cmp].all(), (c, int(np.argmin(ok | ~cmp)))
     # the pressure, in particular at the high-Mach and near-vacuum points
     p_gpu, c_gpu = blocks.eos(Ud, G_)
+    assert capi.last_launch().kernel == want
     p_gpu = p_gpu.double().cpu().numpy()
     p_ref = oracle.eos(3, G_, Uq)[0]
     fin = np.isfinite(p_gpu) & ~unphysical
@@ -98,7 +108,7 @@ def test_precision_form(dtype):
         rel = np.concatenate([_rel(np.abs(got[i] - ref64[i]), ref64[i])[np.isfinite(got[i])] for i in idx])
         report.append(f"{name}: max {rel.max():.2e} rms {np.sqrt(np.mean(rel ** 2)):.2e}")
     nonfinite = sum(int((~np.isfinite(g)).sum()) for g in got)
-    print(f"\n[{dtype}] end-to-end vs FP64 oracle: " + "; ".join(report)
+    print(f"\n[{dtype}, {path}, n={n}] end-to-end vs FP64 oracle: " + "; ".join(report)
           + f"; non-finite outputs {nonfinite}; stored states at or below vacuum: {int(unphysical.sum())}")
 
 

@@ -72,3 +72,20 @@ def test_wait_event_times_out():
             return True
 
     serve.wait_event(Done(), 1.0)
+
+
+def test_noalloc_checks_arguments_before_any_cuda_call(L):
+    """The allocation-free step validates its grid table before it looks up
+    its device array: on a host without a GPU (where any CUDA call fails) bad
+    tables still give their argument errors, and an empty batch is a no-op."""
+    F32, F16 = capi.FDBB_F32, capi.FDBB_F16
+    step = L.fdbb_fv_rusanov_step_noalloc
+    ok = _tab(_grid(4, 0), _grid(4, 256, 1, base=A + (1 << 18), new_base=A + (1 << 19)))
+    assert step(2, ok, 300, 1.4, 0.4, F32, None) == 1                     # vcells not a tile multiple
+    assert step(2, _tab(_grid(4, 256), _grid(4, 0, 1)), 512, 1.4, 0.4, F32, None) == 1  # unsorted
+    assert step(1, _tab(_grid(4, 0, new_base=A)), 256, 1.4, 0.4, F32, None) == 1       # Unew aliases U
+    assert step(2, ok, 512, 1.4, 0.4, F16, None) == 4                     # storage type
+    assert step(1, _tab(_grid(4, 0, base=A + 2)), 256, 1.4, 0.4, F32, None) == 3       # misaligned plane
+    assert step(2, ok, 512, 1.4, 0.0, F32, None) == 1                     # cfl
+    assert step(capi.FV_MAX_GRIDS + 1, ok, 512, 1.4, 0.4, F32, None) == 1  # beyond the array
+    assert step(0, None, 0, 1.4, 0.4, F32, None) == 0

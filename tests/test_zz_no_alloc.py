@@ -5,9 +5,11 @@ it, or their loop must not synchronise the device.  This entry point keeps the
 per-grid wave-speed scratch in a fixed array of the library's own device
 memory instead of a caller-provided buffer.  Here it is called through the C
 ABI twice in a row and compared with the scratch-using path
-(fdbb_fv_max_speed + fdbb_fv_rusanov_step) within the tolerances of the other
-finite-volume tests; it runs the same kernels, so the results are expected to
-be identical.
+(fdbb_fv_max_speed + fdbb_fv_rusanov_step): it runs the same kernels on the
+same values, so the states and time steps must be identical bit for bit.
+They are also checked against the FP64 oracle, within the tolerances of the
+other finite-volume tests, and a call after a warm-up call must leave the
+device's free memory unchanged.
 """
 import numpy as np
 import pytest
@@ -52,19 +54,32 @@ def test_noalloc_step_matches_scratch_step(dtype):
                       dt_log=torch.zeros(steps, dtype=torch.float64, device=DEV))
         g.phase = 2  # ignored by the entry point
         grids.append(g)
+    free = []
     for _ in range(steps):
         tab, vcells = fv._table(grids, with_new=True)
         capi.call("fdbb_fv_rusanov_step_noalloc", len(grids), tab, vcells, G_, CFL, code, stream)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info(DEV)[0])
         for g in grids:
             g.advance()
     torch.cuda.synchronize()
+    # the second call (after the first has loaded the kernels and looked up
+    # the array's address) leaves the device's free memory as it was
+    assert free[1] == free[0]
 
-    for a, b in zip(ref, grids):
+    for i, (a, b) in enumerate(zip(ref, grids)):
         assert a.step == b.step == steps
-        np.testing.assert_allclose(b.dt_log.cpu().numpy(), a.dt_log.cpu().numpy(), rtol=TOL[dtype])
+        assert torch.equal(b.dt_log, a.dt_log), i
         for k in range(5):
-            x, y = a.U[k].double(), b.U[k].double()
-            assert (x - y).abs().max().item() <= TOL[dtype] * max(1.0, x.abs().max().item()), k
+            assert torch.equal(a.U[k], b.U[k]), (i, k)
+    # and against the FP64 oracle, from the same (stored-precision) start
+    for i, (n, b) in enumerate(zip(sizes, grids)):
+        start = [u.double().cpu().numpy() for u in U0[i]]
+        want, dts = oracle.rusanov_run(n, G_, CFL, steps, start)
+        np.testing.assert_allclose(b.dt_log.cpu().numpy(), dts, rtol=TOL[dtype])
+        for k in range(5):
+            got = b.U[k].double().cpu().numpy()
+            assert np.abs(got - want[k]).max() <= TOL[dtype] * max(1.0, np.abs(want[k]).max()), (i, k)
 
 
 def test_noalloc_rejects_more_grids_than_its_array_holds():
