@@ -478,17 +478,17 @@ __device__ __forceinline__ void char_fwd(const Pt<R, D>& s, const K& k, const R*
 // energy component is q for the ideal gas and 2q - phi/Gamma for a general EOS
 // (the value that leaves the pressure unchanged across the wave).
 template <int D, int d, class R, class K>
-__device__ __forceinline__ void char_inv(const Pt<R, D>& s, const K& k, const R* w, R* y) {
+__device__ __forceinline__ void char_inv_sums(const Pt<R, D>& s, const K& k, const R* w, R sum, R anm1, R a1pn,
+                                              R* y) {
   constexpr int nv = D + 2;
   const R c = sqrt_(s.c2);
-  const R a1 = w[0], a2 = w[1], an = w[nv - 1];
-  const R sum = a1 + a2 + an;
-  const R dif = c * (an - a1);
+  const R a2 = w[1];
+  const R dif = c * anm1;
   y[0] = sum;
 #pragma unroll
   for (int i = 0; i < D; ++i) y[1 + i] = s.v[i] * sum;
   y[1 + d] = y[1 + d] + dif;
-  R e = fma_(s.H, a1 + an, s.v[d] * dif);
+  R e = fma_(s.H, a1pn, s.v[d] * dif);
   if constexpr (K::kIdeal)
     e = fma_(s.q, a2, e);
   else
@@ -500,6 +500,14 @@ __device__ __forceinline__ void char_inv(const Pt<R, D>& s, const K& k, const R*
     e = fma_(s.v[tk], w[2 + kk], e);
   }
   y[nv - 1] = e;
+}
+
+// The same with the weight sums formed here, in R: for weights that are
+// themselves computed (the Roe flux's wave strengths).
+template <int D, int d, class R, class K>
+__device__ __forceinline__ void char_inv(const Pt<R, D>& s, const K& k, const R* w, R* y) {
+  constexpr int nv = D + 2;
+  char_inv_sums<D, d>(s, k, w, w[0] + w[1] + w[nv - 1], w[nv - 1] - w[0], w[0] + w[nv - 1], y);
 }
 
 // gU = A_d^T G at one point, with z = g_d + u g_e and sigma = sum_{i != d} v_i g_i:

@@ -64,9 +64,11 @@ struct IdealModel {
 
 // Straight from global memory (cnt < VW only in the ragged last chunk).
 template <class T, int VW> struct GlobalSrc {
+  static constexpr int kStageOut = 0;  // outputs go straight to global memory
   const KArgs& a;
   int64_t i0;
   int cnt;
+  template <int W> __device__ __forceinline__ void stage_out(int, const typename Storage<T>::L (&)[W]) const {}
   __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float fill) const {
     load_raw<T, VW>(inp<T>(a, k), i0, cnt, r, fill);
   }
@@ -74,13 +76,50 @@ template <class T, int VW> struct GlobalSrc {
 
 // From the block's shared-memory stage: this thread's VW points of plane k sit
 // at base + k * TILE (the stage stays valid until the block has finished the
-// tile, so a double-word chunk can be re-read for its FP64 fallback).
-template <class T, int VW, int TILE> struct SmemSrc {
+// tile, so a double-word chunk can be re-read for its FP64 fallback).  With
+// NOUT > 0 the first NOUT output planes are written to the block's output
+// stage (this thread's points of plane k at obase + k * TILE), from which
+// thread 0 moves whole tiles to global memory with bulk copies.
+template <class T, int VW, int TILE, int NOUT = 0> struct SmemSrc {
+  static constexpr int kStageOut = NOUT;
   const T* base;
+  T* obase;
   __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float) const {
     ld_sh(base + (size_t)k * TILE, r);
   }
+  template <int W> __device__ __forceinline__ void stage_out(int k, const typename Storage<T>::L (&r)[W]) const {
+#pragma unroll
+    for (int j = 0; j < W; ++j) obase[(size_t)k * TILE + j] = from_r<T>(r[j]);
+  }
 };
+
+// Output plane k of the current VW points: into the source's output stage
+// when it stages plane k, else straight to global memory (a NULL plane is
+// skipped there; a staged NULL plane is simply never copied out).
+template <class T, int VW, class R, class Src>
+__device__ __forceinline__ void put(const KArgs& a, const Src& src, int k, int64_t i0, int cnt, const R (&x)[VW]) {
+  if constexpr (Src::kStageOut > 0) {
+    if (k < Src::kStageOut) {
+      typename Storage<T>::L raw[VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) raw[j] = to_load(x[j]);
+      src.template stage_out<VW>(k, raw);
+      return;
+    }
+  }
+  store<T, VW, R>(outp<T>(a, k), i0, cnt, x);
+}
+template <class T, int VW, class Src>
+__device__ __forceinline__ void put_raw(const KArgs& a, const Src& src, int k, int64_t i0, int cnt,
+                                        const typename Storage<T>::L (&raw)[VW]) {
+  if constexpr (Src::kStageOut > 0) {
+    if (k < Src::kStageOut) {
+      src.template stage_out<VW>(k, raw);
+      return;
+    }
+  }
+  store_raw<T, VW>(outp<T>(a, k), i0, cnt, raw);
+}
 
 // Conservative state of VW points from input planes base..base+D+1.
 template <class T, int VW, int D, class R, class G, class Src>
@@ -128,17 +167,41 @@ __device__ __forceinline__ void load_field(const Src& src, int base, R (&w)[VW][
   }
 }
 
+// Characteristic weights W (planes base..base+NV-1, inputs) for the inverse
+// transform, with the three sums of weights it needs -- w_1 + w_2 + w_nv,
+// w_nv - w_1 and w_1 + w_nv -- formed in the storage's own IEEE type before
+// the conversion to R: sums of two exact inputs can cancel, and a double-word
+// value carries ~47 of a double's 53 bits, so in double-word arithmetic they
+// would not be accurate relative to their own magnitude.
+template <class T, int VW, int NV, class R, class G, class Src>
+__device__ __forceinline__ void load_weights_inv(const Src& src, int base, R (&w)[VW][NV], R (&sum)[VW],
+                                                 R (&anm1)[VW], R (&a1pn)[VW], G& g) {
+  using L = typename Storage<T>::L;
+  L raw[NV][VW];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) src.raw(base + c, raw[c], 0.0f);
+#pragma unroll
+  for (int j = 0; j < VW; ++j) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) w[j][c] = to_compute<R, G>(raw[c][j], g);
+    const L a1 = raw[0][j], a2 = raw[1][j], an = raw[NV - 1][j];
+    sum[j] = to_compute<R, G>(a1 + a2 + an, g);
+    anm1[j] = to_compute<R, G>(an - a1, g);
+    a1pn[j] = to_compute<R, G>(a1 + an, g);
+  }
+}
+
 // Store y[point][component] into output planes base..base+NV-1.
-template <class T, int VW, int NV, class R>
-__device__ __forceinline__ void store_field(const KArgs& a, int base, int64_t i0, int cnt, const R (&y)[VW][NV]) {
+template <class T, int VW, int NV, class R, class Src>
+__device__ __forceinline__ void store_field(const KArgs& a, const Src& src, int base, int64_t i0, int cnt,
+                                            const R (&y)[VW][NV]) {
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
-    T* o = outp<T>(a, base + c);
-    if (!o) continue;
+    if (!outp<T>(a, base + c)) continue;
     R x[VW];
 #pragma unroll
     for (int j = 0; j < VW; ++j) x[j] = y[j][c];
-    store<T, VW, R>(o, i0, cnt, x);
+    put<T, VW, R>(a, src, base + c, i0, cnt, x);
   }
 }
 
@@ -150,43 +213,42 @@ __device__ __forceinline__ void derive_all(Pt<R, D> (&s)[VW], const K& k, G& g) 
 
 // Flux column d into output planes base..base+nv-1.  Component 0 is the input
 // momentum m_d itself, stored bit for bit.
-template <class T, int VW, int D, int d, class R>
-__device__ __forceinline__ void emit_flux(const KArgs& a, int base, int64_t i0, int cnt, const Pt<R, D> (&s)[VW]) {
+template <class T, int VW, int D, int d, class R, class Src>
+__device__ __forceinline__ void emit_flux(const KArgs& a, const Src& src, int base, int64_t i0, int cnt,
+                                          const Pt<R, D> (&s)[VW]) {
 #pragma unroll
   for (int c = 0; c < D + 2; ++c) {
-    T* o = outp<T>(a, base + c);
-    if (!o) continue;
+    if (!outp<T>(a, base + c)) continue;
     if constexpr (std::is_same<R, dw>::value) {
       if (c == 0) {  // F_d[0] = m_d: the input itself, bit for bit
         double raw[VW];
 #pragma unroll
         for (int j = 0; j < VW; ++j) raw[j] = s[j].raw.m[d];
-        store_raw<T, VW>(o, i0, cnt, raw);
+        put_raw<T, VW>(a, src, base + c, i0, cnt, raw);
         continue;
       }
     }
     R x[VW];
 #pragma unroll
     for (int j = 0; j < VW; ++j) x[j] = flux_comp<D, d>(s[j], c);
-    store<T, VW, R>(o, i0, cnt, x);
+    put<T, VW, R>(a, src, base + c, i0, cnt, x);
   }
 }
 
 // Jacobian A_d into output planes base..base+nv*nv-1 (row-major).
-template <class T, int VW, int D, int d, class R, class K>
-__device__ __forceinline__ void emit_jac(const KArgs& a, int base, int64_t i0, int cnt, const Pt<R, D> (&s)[VW],
-                                         const K& k) {
+template <class T, int VW, int D, int d, class R, class K, class Src>
+__device__ __forceinline__ void emit_jac(const KArgs& a, const Src& src, int base, int64_t i0, int cnt,
+                                         const Pt<R, D> (&s)[VW], const K& k) {
   constexpr int nv = D + 2;
 #pragma unroll
   for (int row = 0; row < nv; ++row) {
 #pragma unroll
     for (int col = 0; col < nv; ++col) {
-      T* o = outp<T>(a, base + row * nv + col);
-      if (!o) continue;
+      if (!outp<T>(a, base + row * nv + col)) continue;
       R x[VW];
 #pragma unroll
       for (int j = 0; j < VW; ++j) x[j] = jac_entry<D, d>(s[j], k, row, col);
-      store<T, VW, R>(o, i0, cnt, x);
+      put<T, VW, R>(a, src, base + row * nv + col, i0, cnt, x);
     }
   }
 }
@@ -363,11 +425,11 @@ template <int D, int d> struct OpFlux {
     derive_all<VW, D, false>(s, k, g);
     if (!g.ok) return false;
     if constexpr (d >= 0) {
-      emit_flux<T, VW, D, d>(a, 0, i0, cnt, s);
+      emit_flux<T, VW, D, d>(a, src, 0, i0, cnt, s);
     } else {
-      emit_flux<T, VW, D, 0>(a, 0, i0, cnt, s);
-      if constexpr (D > 1) emit_flux<T, VW, D, 1>(a, D + 2, i0, cnt, s);
-      if constexpr (D > 2) emit_flux<T, VW, D, 2>(a, 2 * (D + 2), i0, cnt, s);
+      emit_flux<T, VW, D, 0>(a, src, 0, i0, cnt, s);
+      if constexpr (D > 1) emit_flux<T, VW, D, 1>(a, src, D + 2, i0, cnt, s);
+      if constexpr (D > 2) emit_flux<T, VW, D, 2>(a, src, 2 * (D + 2), i0, cnt, s);
     }
     return true;
   }
@@ -383,7 +445,7 @@ template <int D, int d> struct OpJac {
     load_U<T, VW, D>(src, 0, s, g);
     derive_all<VW, D, false>(s, k, g);
     if (!g.ok) return false;
-    emit_jac<T, VW, D, d>(a, 0, i0, cnt, s, k);
+    emit_jac<T, VW, D, d>(a, src, 0, i0, cnt, s, k);
     return true;
   }
 };
@@ -398,17 +460,21 @@ template <int D, int d, bool INV> struct OpChar {
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
     R w[VW][nv], y[VW][nv];
-    load_field<T, VW, nv>(src, nv, w, g);
-    derive_all<VW, D>(s, k, g);
-    if (!g.ok) return false;
+    if constexpr (INV) {
+      R sum[VW], anm1[VW], a1pn[VW];
+      load_weights_inv<T, VW, nv>(src, nv, w, sum, anm1, a1pn, g);
+      derive_all<VW, D>(s, k, g);
+      if (!g.ok) return false;
 #pragma unroll
-    for (int j = 0; j < VW; ++j) {
-      if constexpr (INV)
-        char_inv<D, d>(s[j], k, w[j], y[j]);
-      else
-        char_fwd<D, d>(s[j], k, w[j], y[j]);
+      for (int j = 0; j < VW; ++j) char_inv_sums<D, d>(s[j], k, w[j], sum[j], anm1[j], a1pn[j], y[j]);
+    } else {
+      load_field<T, VW, nv>(src, nv, w, g);
+      derive_all<VW, D>(s, k, g);
+      if (!g.ok) return false;
+#pragma unroll
+      for (int j = 0; j < VW; ++j) char_fwd<D, d>(s[j], k, w[j], y[j]);
     }
-    store_field<T, VW, nv>(a, 0, i0, cnt, y);
+    store_field<T, VW, nv>(a, src, 0, i0, cnt, y);
     return true;
   }
 };
@@ -432,15 +498,15 @@ template <int D, int dj> struct OpFused {
     if (want_y) load_field<T, VW, nv>(src, nv, w, g);
     derive_all<VW, D>(s, k, g);
     if (!g.ok) return false;
-    emit_flux<T, VW, D, 0>(a, 0, i0, cnt, s);
-    if constexpr (D > 1) emit_flux<T, VW, D, 1>(a, nv, i0, cnt, s);
-    if constexpr (D > 2) emit_flux<T, VW, D, 2>(a, 2 * nv, i0, cnt, s);
-    emit_jac<T, VW, D, dj>(a, D * nv, i0, cnt, s, k);
+    emit_flux<T, VW, D, 0>(a, src, 0, i0, cnt, s);
+    if constexpr (D > 1) emit_flux<T, VW, D, 1>(a, src, nv, i0, cnt, s);
+    if constexpr (D > 2) emit_flux<T, VW, D, 2>(a, src, 2 * nv, i0, cnt, s);
+    emit_jac<T, VW, D, dj>(a, src, D * nv, i0, cnt, s, k);
     if (want_y) {
       R y[VW][nv];
 #pragma unroll
       for (int j = 0; j < VW; ++j) char_fwd<D, dj>(s[j], k, w[j], y[j]);
-      store_field<T, VW, nv>(a, D * nv + nv * nv, i0, cnt, y);
+      store_field<T, VW, nv>(a, src, D * nv + nv * nv, i0, cnt, y);
     }
     return true;
   }
@@ -501,7 +567,7 @@ template <int D, int d> struct OpVjp {
     if (!g.ok) return false;
 #pragma unroll
     for (int j = 0; j < VW; ++j) flux_vjp_pt<D, d>(s[j], k, gg[j], y[j]);
-    store_field<T, VW, nv>(a, 0, i0, cnt, y);
+    store_field<T, VW, nv>(a, src, 0, i0, cnt, y);
     return true;
   }
 };
@@ -525,7 +591,7 @@ template <int D, int d> struct OpRoeFlux {
     R y[VW][nv];
 #pragma unroll
     for (int j = 0; j < VW; ++j) roe_flux_pt<D, d>(L[j], Rt[j], s[j], k, y[j]);
-    store_field<T, VW, nv>(a, 0, i0, cnt, y);
+    store_field<T, VW, nv>(a, src, 0, i0, cnt, y);
     return true;
   }
 };
@@ -543,7 +609,11 @@ template <int D, int d, bool INV> struct OpRoeChar {
     load_U<T, VW, D>(src, 0, L, g);
     load_U<T, VW, D>(src, nv, Rt, g);
     R w[VW][nv], y[VW][nv];
-    load_field<T, VW, nv>(src, 2 * nv, w, g);
+    R sum[VW], anm1[VW], a1pn[VW];
+    if constexpr (INV)
+      load_weights_inv<T, VW, nv>(src, 2 * nv, w, sum, anm1, a1pn, g);
+    else
+      load_field<T, VW, nv>(src, 2 * nv, w, g);
     derive_all<VW, D, false>(L, k, g);
     derive_all<VW, D, false>(Rt, k, g);
 #pragma unroll
@@ -552,11 +622,11 @@ template <int D, int d, bool INV> struct OpRoeChar {
 #pragma unroll
     for (int j = 0; j < VW; ++j) {
       if constexpr (INV)
-        char_inv<D, d>(s[j], k, w[j], y[j]);
+        char_inv_sums<D, d>(s[j], k, w[j], sum[j], anm1[j], a1pn[j], y[j]);
       else
         char_fwd<D, d>(s[j], k, w[j], y[j]);
     }
-    store_field<T, VW, nv>(a, 0, i0, cnt, y);
+    store_field<T, VW, nv>(a, src, 0, i0, cnt, y);
     return true;
   }
 };
@@ -716,6 +786,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// bytes from shared src to global dst as one bulk asynchronous copy of this
+// thread's current bulk group; both 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Until every committed bulk group of this thread has finished reading its
+// shared-memory source (the source may then be overwritten) ...
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... or has completed entirely.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Wait for the phase with the given parity to complete; false after `limit`
 // polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = kWaitLimit) {
@@ -743,6 +827,44 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
 // FP32x2 double-word arithmetic (vjp_packed).
 template <class Op, class T, class R, class Mdl> struct OpWidth { static constexpr int VW = Width<T, R>::VW; };
 template <int D, int d> struct OpWidth<OpVjp<D, d>, double, dw, IdealModel> { static constexpr int VW = 2; };
+
+// The light ideal-gas double-word blocks (few planes and little arithmetic
+// per point; 32-56 registers at one point per thread) take two points per
+// thread: twice the independent work between the staged kernel's barriers
+// and half its per-tile overhead per point.
+#ifndef FDBB_DW_LIGHT_VW
+#define FDBB_DW_LIGHT_VW 2
+#endif
+template <int D> struct OpWidth<OpVMag2<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+template <int D> struct OpWidth<OpEos<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+template <int D> struct OpWidth<OpPrim<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+template <int D> struct OpWidth<OpCons<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+template <int D> struct OpWidth<OpTemp<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+template <int D, int d> struct OpWidth<OpRiemann<D, d>, double, dw, IdealModel> {
+  static constexpr int VW = FDBB_DW_LIGHT_VW;
+};
+template <int D, int d> struct OpWidth<OpFlux<D, d>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+template <int D, int d> struct OpWidth<OpFluxPrim<D, d>, double, dw, IdealModel> {
+  static constexpr int VW = FDBB_DW_LIGHT_VW;
+};
+template <int D, int d> struct OpWidth<OpJac<D, d>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+template <int D, int d> struct OpWidth<OpJacPrim<D, d>, double, dw, IdealModel> {
+  static constexpr int VW = FDBB_DW_LIGHT_VW;
+};
+
+// Output planes that the staged kernel writes through a shared-memory output
+// stage and bulk copies (one 2 KB copy per plane and 256-point tile) instead
+// of per-thread streaming stores: the 15 flux planes of the ideal-gas 3D fused
+// pass in double-word arithmetic.  Its 45 output planes are 82% of its
+// traffic; the stage costs 30 KB per block, which still leaves three blocks
+// per SM beside the 40 KB input ring.
+#ifndef FDBB_FUSED_STAGE_OUT
+#define FDBB_FUSED_STAGE_OUT 15
+#endif
+template <class Op, class T, class R, class Mdl> struct StageOut { static constexpr int planes = 0; };
+template <int dj> struct StageOut<OpFused<3, dj>, double, dw, IdealModel> {
+  static constexpr int planes = FDBB_FUSED_STAGE_OUT;
+};
 
 template <class Op, class T, class R, class Mdl, class K, class Src>
 __device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Src& src, int64_t i0, int cnt) {
@@ -779,10 +901,12 @@ template <class Op, class T, class R, class Mdl>
 __device__ __forceinline__ void staged_body(const KArgs& a) {
   constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   constexpr int TILE = kThreads * VW;
+  constexpr int NOUT = StageOut<Op, T, R, Mdl>::planes;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kStages];
-  T* buf = reinterpret_cast<T*>(smem_raw);  // [kStages][nin][TILE]
+  T* buf = reinterpret_cast<T*>(smem_raw);  // [kStages][nin][TILE], then the output stage [NOUT][TILE]
   const int nin = a.nin;
+  T* obuf = buf + (size_t)kStages * nin * TILE;
   const int tid = threadIdx.x;
   const int64_t ntiles = a.n / TILE;
   const uint32_t plane_bytes = TILE * sizeof(T);
@@ -814,17 +938,32 @@ __device__ __forceinline__ void staged_body(const KArgs& a) {
   int j = 0;
   for (; has_tile(j); ++j) {
     const int s = j % kStages;
+    // the previous tile's bulk stores have read the output stage before the
+    // barrier below lets anyone write it again
+    if constexpr (NOUT > 0)
+      if (tid == 0) bulk_wait_read();
     const bool ok = mbar_wait(&bars[s], (uint32_t)(j / kStages) & 1u, limit);
     if (__syncthreads_or(!ok)) break;
-    const SmemSrc<T, VW, TILE> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW};
-    const int64_t i0 = (blockIdx.x + (int64_t)j * gridDim.x) * TILE + (int64_t)tid * VW;
+    const int64_t tile = blockIdx.x + (int64_t)j * gridDim.x;
+    const SmemSrc<T, VW, TILE, NOUT> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW, obuf + (size_t)tid * VW};
+    const int64_t i0 = tile * TILE + (int64_t)tid * VW;
     apply_chunk<Op, T, R, Mdl>(a, k, src, i0, VW);
-    __syncthreads();  // the whole block is done with stage s: refill it
-    if (tid == 0 && has_tile(j + kStages)) {
-      fence_proxy_async();
-      issue(j + kStages);
+    if constexpr (NOUT > 0) fence_proxy_async();  // this thread's stage writes before the bulk reads
+    __syncthreads();  // the whole block is done with stage s (refill it) and has filled the output stage
+    if (tid == 0) {
+      if constexpr (NOUT > 0) {
+        for (int q = 0; q < NOUT; ++q)
+          if (T* o = outp<T>(a, q)) bulk_s2g(o + tile * TILE, obuf + (size_t)q * TILE, TILE * sizeof(T));
+        bulk_commit();
+      }
+      if (has_tile(j + kStages)) {
+        fence_proxy_async();
+        issue(j + kStages);
+      }
     }
   }
+  if constexpr (NOUT > 0)
+    if (tid == 0) bulk_wait_all();  // the output stage lives until the block exits
   if (has_tile(j)) {
     // A wait ran out: record it, wait (bounded again) for this block's copies
     // still in flight so that none lands after the block exits, and return.
@@ -907,7 +1046,8 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_direct(const
 template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const KArgs& a, cudaStream_t stream) {
   constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   constexpr int TILE = kThreads * VW;
-  constexpr size_t kMaxSmem = (size_t)kStages * Op::kIn * TILE * sizeof(T);
+  constexpr size_t kStageOutBytes = (size_t)StageOut<Op, T, R, Mdl>::planes * TILE * sizeof(T);
+  constexpr size_t kMaxSmem = (size_t)kStages * Op::kIn * TILE * sizeof(T) + kStageOutBytes;
   auto kern = [] {
     if constexpr (kStaged3<R, Mdl>)
       return k_staged3<Op, T, R, Mdl>;
@@ -923,7 +1063,7 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
     if (e != cudaSuccess) return e;
     if (slot >= 0) attr_set[slot].store(1, std::memory_order_relaxed);
   }
-  const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T);
+  const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T) + kStageOutBytes;
   static std::atomic<int> bps_cache[Op::kIn + 1][kMaxDevices];  // blocks per SM for each nin
   const int bps = blocks_per_sm(kern, smem, bps_cache[a.nin]);
   const int64_t ntiles = a.n / TILE;
@@ -941,7 +1081,8 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
 template <class Op, class T, class R, class Mdl = IdealModel>
 cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
   constexpr int TILE = kThreads * OpWidth<Op, T, R, Mdl>::VW;
-  const size_t ring = (size_t)kStages * a.nin * TILE * sizeof(T);
+  const size_t ring = (size_t)kStages * a.nin * TILE * sizeof(T) +
+                      (size_t)StageOut<Op, T, R, Mdl>::planes * TILE * sizeof(T);
   if (!(a.flags & kDirectOnly) && a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn &&
       ring <= (100u << 10))
     return launch_staged<Op, T, R, Mdl>(a, stream);
@@ -961,11 +1102,6 @@ template <int D, class T, class R> cudaError_t dispatch_dim(const LaunchReq& r, 
     case OpKind::Temp: return launch_op<OpTemp<D>, T, R>(a, r.stream);
     default: break;
   }
-  // The inverse characteristic transforms add input components directly
-  // (a1 + a2 + an); in double-word arithmetic such sums of exact inputs are
-  // not accurate relative to their own magnitude, so they always run in the
-  // storage's own IEEE type.
-  using RI = typename std::conditional<std::is_same<R, dw>::value, double, R>::type;
 #define FDBB_DIR_CASES(OPK, OPT, RT)                                                          \
   case OPK:                                                                                   \
     if (d == 0) return launch_op<OPT<D, 0>, T, RT>(a, r.stream);                              \
@@ -991,11 +1127,11 @@ template <int D, class T, class R> cudaError_t dispatch_dim(const LaunchReq& r, 
         if (d == 2) return launch_op<OpRoeChar<D, (D > 2 ? 2 : 0), false>, T, R>(a, r.stream);
       return cudaErrorInvalidValue;
     case OpKind::RoeCharInv:
-      if (d == 0) return launch_op<OpRoeChar<D, 0, true>, T, RI>(a, r.stream);
+      if (d == 0) return launch_op<OpRoeChar<D, 0, true>, T, R>(a, r.stream);
       if constexpr (D > 1)
-        if (d == 1) return launch_op<OpRoeChar<D, (D > 1 ? 1 : 0), true>, T, RI>(a, r.stream);
+        if (d == 1) return launch_op<OpRoeChar<D, (D > 1 ? 1 : 0), true>, T, R>(a, r.stream);
       if constexpr (D > 2)
-        if (d == 2) return launch_op<OpRoeChar<D, (D > 2 ? 2 : 0), true>, T, RI>(a, r.stream);
+        if (d == 2) return launch_op<OpRoeChar<D, (D > 2 ? 2 : 0), true>, T, R>(a, r.stream);
       return cudaErrorInvalidValue;
     case OpKind::CharFwd:
       if (d == 0) return launch_op<OpChar<D, 0, false>, T, R>(a, r.stream);
@@ -1005,11 +1141,11 @@ template <int D, class T, class R> cudaError_t dispatch_dim(const LaunchReq& r, 
         if (d == 2) return launch_op<OpChar<D, (D > 2 ? 2 : 0), false>, T, R>(a, r.stream);
       return cudaErrorInvalidValue;
     case OpKind::CharInv:
-      if (d == 0) return launch_op<OpChar<D, 0, true>, T, RI>(a, r.stream);
+      if (d == 0) return launch_op<OpChar<D, 0, true>, T, R>(a, r.stream);
       if constexpr (D > 1)
-        if (d == 1) return launch_op<OpChar<D, (D > 1 ? 1 : 0), true>, T, RI>(a, r.stream);
+        if (d == 1) return launch_op<OpChar<D, (D > 1 ? 1 : 0), true>, T, R>(a, r.stream);
       if constexpr (D > 2)
-        if (d == 2) return launch_op<OpChar<D, (D > 2 ? 2 : 0), true>, T, RI>(a, r.stream);
+        if (d == 2) return launch_op<OpChar<D, (D > 2 ? 2 : 0), true>, T, R>(a, r.stream);
       return cudaErrorInvalidValue;
     default: break;
   }
@@ -1057,19 +1193,10 @@ template <int D, class T, class R, class Mdl> cudaError_t dispatch_eos_dim(const
     FDBB_EOS_DIR_CASES(OpKind::FluxPrim, OpFluxPrim)
     FDBB_EOS_DIR_CASES(OpKind::JacPrim, OpJacPrim)
     FDBB_EOS_DIR_CASES(OpKind::CharFwd, OpCharFwd)
+    FDBB_EOS_DIR_CASES(OpKind::CharInv, OpCharInv)
     default: break;
   }
 #undef FDBB_EOS_DIR_CASES
-  // the inverse transform adds input components directly: IEEE arithmetic
-  // for double-word, as for the ideal gas
-  using RI = typename std::conditional<std::is_same<R, dw>::value, double, R>::type;
-  if (r.op == OpKind::CharInv) {
-    if (d == 0) return launch_op<OpCharInv<D, 0>, T, RI, Mdl>(a, r.stream);
-    if constexpr (D > 1)
-      if (d == 1) return launch_op<OpCharInv<D, (D > 1 ? 1 : 0)>, T, RI, Mdl>(a, r.stream);
-    if constexpr (D > 2)
-      if (d == 2) return launch_op<OpCharInv<D, (D > 2 ? 2 : 0)>, T, RI, Mdl>(a, r.stream);
-  }
   return cudaErrorInvalidValue;
 }
 

@@ -416,6 +416,28 @@ def test_staged_path_parity(dtype, dw):
     assert capi.device_status() == 0  # no bounded wait ran out
 
 
+def test_staged_fused_with_skipped_flux_planes():
+    """The double-word fused pass moves its 15 flux planes through a
+    shared-memory output stage and bulk copies: NULL flux planes (never
+    copied out) and NULL Jacobian planes leave every other plane correct."""
+    n, D = staged_n(256, 77), 3
+    V, U, W = fields(n, D, seed=515)
+    Ud, _ = quantise(U, torch.float64)
+    Wd, _ = quantise(W, torch.float64)
+    F = blocks._alloc(15, n, torch.float64, DEV)
+    A = blocks._alloc(25, n, torch.float64, DEV)
+    Y = blocks._alloc(5, n, torch.float64, DEV)
+    Fo = [None if k in (0, 3, 7, 14) else f for k, f in enumerate(F)]
+    Ao = [None if k in (1, 24) else x for k, x in enumerate(A)]
+    blocks.euler_fused(Ud, Wd, 2, G, out=(Fo, Ao, Y), dw=True)
+    assert_staged()
+    ref, S = oracle.euler_fused(D, 2, G, U, W, scale=True)
+    keep = [k for k in range(15) if Fo[k] is not None] + [15 + k for k in range(25) if Ao[k] is not None] + \
+        list(range(40, 45))
+    got = host([*F, *A, *Y])
+    check([got[k] for k in keep], [ref[k] for k in keep], [S[k] for k in keep], torch.float64, "staged fused, skips")
+
+
 @pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
 def test_packed_vjp_lanes_are_independent(staged):
     """The double-word flux VJP runs two points per thread as the two lanes of
