@@ -453,7 +453,7 @@ BLOCKS_3D = {
     "v_mag2": (4, 1), "eos": (5, 2), "prim_from_cons": (5, 5), "cons_from_prim": (5, 5),
     "riemann_inv": (5, 2), "flux_x": (5, 5), "flux_all": (5, 15), "flux_jac_x": (5, 25),
     "char_fwd_x": (10, 5), "char_inv_x": (10, 5), "flux_vjp_x": (10, 5), "roe_flux_x": (10, 5),
-    "flux_prim_all": (5, 15), "temperature": (5, 1),
+    "flux_prim_all": (5, 15), "flux_jac_prim_x": (5, 25), "temperature": (5, 1),
 }
 
 
@@ -493,6 +493,7 @@ def run_blocks(n, dev, stream, hbm_peak, steps=10, warmup=3, forms=("f64dw", "f6
             "flux_vjp_x": lambda: blocks.flux_vjp(U, W, 0, GAMMA, out=out[:5], dw=dw),
             "roe_flux_x": lambda: blocks.roe_flux(U, UR, 0, GAMMA, out=out[:5], dw=dw),
             "flux_prim_all": lambda: blocks.flux_prim(V, -1, GAMMA, out=out[:15], dw=dw),
+            "flux_jac_prim_x": lambda: blocks.flux_jac_prim(V, 0, GAMMA, out=out[:25], dw=dw),
             "temperature": lambda: blocks.temperature(U, 2.5, GAMMA, out=out[0], dw=dw),
         }
         es = torch.empty(0, dtype=dt).element_size()

@@ -64,11 +64,9 @@ struct IdealModel {
 
 // Straight from global memory (cnt < VW only in the ragged last chunk).
 template <class T, int VW> struct GlobalSrc {
-  static constexpr int kStageOut = 0;  // outputs go straight to global memory
   const KArgs& a;
   int64_t i0;
   int cnt;
-  template <int W> __device__ __forceinline__ void stage_out(int, const typename Storage<T>::L (&)[W]) const {}
   __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float fill) const {
     load_raw<T, VW>(inp<T>(a, k), i0, cnt, r, fill);
   }
@@ -76,48 +74,22 @@ template <class T, int VW> struct GlobalSrc {
 
 // From the block's shared-memory stage: this thread's VW points of plane k sit
 // at base + k * TILE (the stage stays valid until the block has finished the
-// tile, so a double-word chunk can be re-read for its FP64 fallback).  With
-// NOUT > 0 the first NOUT output planes are written to the block's output
-// stage (this thread's points of plane k at obase + k * TILE), from which
-// thread 0 moves whole tiles to global memory with bulk copies.
-template <class T, int VW, int TILE, int NOUT = 0> struct SmemSrc {
-  static constexpr int kStageOut = NOUT;
+// tile, so a double-word chunk can be re-read for its FP64 fallback).
+template <class T, int VW, int TILE> struct SmemSrc {
   const T* base;
-  T* obase;
   __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float) const {
     ld_sh(base + (size_t)k * TILE, r);
   }
-  template <int W> __device__ __forceinline__ void stage_out(int k, const typename Storage<T>::L (&r)[W]) const {
-#pragma unroll
-    for (int j = 0; j < W; ++j) obase[(size_t)k * TILE + j] = from_r<T>(r[j]);
-  }
 };
 
-// Output plane k of the current VW points: into the source's output stage
-// when it stages plane k, else straight to global memory (a NULL plane is
-// skipped there; a staged NULL plane is simply never copied out).
+// Output plane k of the current VW points (a NULL plane is skipped).
 template <class T, int VW, class R, class Src>
-__device__ __forceinline__ void put(const KArgs& a, const Src& src, int k, int64_t i0, int cnt, const R (&x)[VW]) {
-  if constexpr (Src::kStageOut > 0) {
-    if (k < Src::kStageOut) {
-      typename Storage<T>::L raw[VW];
-#pragma unroll
-      for (int j = 0; j < VW; ++j) raw[j] = to_load(x[j]);
-      src.template stage_out<VW>(k, raw);
-      return;
-    }
-  }
+__device__ __forceinline__ void put(const KArgs& a, const Src&, int k, int64_t i0, int cnt, const R (&x)[VW]) {
   store<T, VW, R>(outp<T>(a, k), i0, cnt, x);
 }
 template <class T, int VW, class Src>
-__device__ __forceinline__ void put_raw(const KArgs& a, const Src& src, int k, int64_t i0, int cnt,
+__device__ __forceinline__ void put_raw(const KArgs& a, const Src&, int k, int64_t i0, int cnt,
                                         const typename Storage<T>::L (&raw)[VW]) {
-  if constexpr (Src::kStageOut > 0) {
-    if (k < Src::kStageOut) {
-      src.template stage_out<VW>(k, raw);
-      return;
-    }
-  }
   store_raw<T, VW>(outp<T>(a, k), i0, cnt, raw);
 }
 
@@ -786,20 +758,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
-// bytes from shared src to global dst as one bulk asynchronous copy of this
-// thread's current bulk group; both 16-byte aligned, bytes % 16 == 0.
-__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// Until every committed bulk group of this thread has finished reading its
-// shared-memory source (the source may then be overwritten) ...
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// ... or has completed entirely.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
 // Wait for the phase with the given parity to complete; false after `limit`
 // polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = kWaitLimit) {
@@ -831,40 +789,23 @@ template <int D, int d> struct OpWidth<OpVjp<D, d>, double, dw, IdealModel> { st
 // The light ideal-gas double-word blocks (few planes and little arithmetic
 // per point; 32-56 registers at one point per thread) take two points per
 // thread: twice the independent work between the staged kernel's barriers
-// and half its per-tile overhead per point.
-#ifndef FDBB_DW_LIGHT_VW
-#define FDBB_DW_LIGHT_VW 2
-#endif
-template <int D> struct OpWidth<OpVMag2<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
-template <int D> struct OpWidth<OpEos<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
-template <int D> struct OpWidth<OpPrim<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
-template <int D> struct OpWidth<OpCons<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
-template <int D> struct OpWidth<OpTemp<D>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+// and half its per-tile overhead per point (A/B at 2^26: v_mag2 0.79 -> 0.94,
+// prim 0.77 -> 0.87, flux 0.73 -> 0.81, temperature 0.60 -> 0.70 of HBM; the
+// all-direction primitive-form flux was slower, 0.83 -> 0.81, and keeps one).
+template <int D> struct OpWidth<OpVMag2<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
+template <int D> struct OpWidth<OpEos<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
+template <int D> struct OpWidth<OpPrim<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
+template <int D> struct OpWidth<OpCons<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
+template <int D> struct OpWidth<OpTemp<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
 template <int D, int d> struct OpWidth<OpRiemann<D, d>, double, dw, IdealModel> {
-  static constexpr int VW = FDBB_DW_LIGHT_VW;
+  static constexpr int VW = 2;
 };
-template <int D, int d> struct OpWidth<OpFlux<D, d>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
-template <int D, int d> struct OpWidth<OpFluxPrim<D, d>, double, dw, IdealModel> {
-  static constexpr int VW = FDBB_DW_LIGHT_VW;
-};
-template <int D, int d> struct OpWidth<OpJac<D, d>, double, dw, IdealModel> { static constexpr int VW = FDBB_DW_LIGHT_VW; };
+template <int D, int d> struct OpWidth<OpFlux<D, d>, double, dw, IdealModel> { static constexpr int VW = 2; };
+template <int D, int d> struct OpWidth<OpJac<D, d>, double, dw, IdealModel> { static constexpr int VW = 2; };
 template <int D, int d> struct OpWidth<OpJacPrim<D, d>, double, dw, IdealModel> {
-  static constexpr int VW = FDBB_DW_LIGHT_VW;
+  static constexpr int VW = 2;
 };
 
-// Output planes that the staged kernel writes through a shared-memory output
-// stage and bulk copies (one 2 KB copy per plane and 256-point tile) instead
-// of per-thread streaming stores: the 15 flux planes of the ideal-gas 3D fused
-// pass in double-word arithmetic.  Its 45 output planes are 82% of its
-// traffic; the stage costs 30 KB per block, which still leaves three blocks
-// per SM beside the 40 KB input ring.
-#ifndef FDBB_FUSED_STAGE_OUT
-#define FDBB_FUSED_STAGE_OUT 15
-#endif
-template <class Op, class T, class R, class Mdl> struct StageOut { static constexpr int planes = 0; };
-template <int dj> struct StageOut<OpFused<3, dj>, double, dw, IdealModel> {
-  static constexpr int planes = FDBB_FUSED_STAGE_OUT;
-};
 
 template <class Op, class T, class R, class Mdl, class K, class Src>
 __device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Src& src, int64_t i0, int cnt) {
@@ -901,12 +842,10 @@ template <class Op, class T, class R, class Mdl>
 __device__ __forceinline__ void staged_body(const KArgs& a) {
   constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   constexpr int TILE = kThreads * VW;
-  constexpr int NOUT = StageOut<Op, T, R, Mdl>::planes;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kStages];
-  T* buf = reinterpret_cast<T*>(smem_raw);  // [kStages][nin][TILE], then the output stage [NOUT][TILE]
+  T* buf = reinterpret_cast<T*>(smem_raw);  // [kStages][nin][TILE]
   const int nin = a.nin;
-  T* obuf = buf + (size_t)kStages * nin * TILE;
   const int tid = threadIdx.x;
   const int64_t ntiles = a.n / TILE;
   const uint32_t plane_bytes = TILE * sizeof(T);
@@ -938,32 +877,17 @@ __device__ __forceinline__ void staged_body(const KArgs& a) {
   int j = 0;
   for (; has_tile(j); ++j) {
     const int s = j % kStages;
-    // the previous tile's bulk stores have read the output stage before the
-    // barrier below lets anyone write it again
-    if constexpr (NOUT > 0)
-      if (tid == 0) bulk_wait_read();
     const bool ok = mbar_wait(&bars[s], (uint32_t)(j / kStages) & 1u, limit);
     if (__syncthreads_or(!ok)) break;
-    const int64_t tile = blockIdx.x + (int64_t)j * gridDim.x;
-    const SmemSrc<T, VW, TILE, NOUT> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW, obuf + (size_t)tid * VW};
-    const int64_t i0 = tile * TILE + (int64_t)tid * VW;
+    const SmemSrc<T, VW, TILE> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW};
+    const int64_t i0 = (blockIdx.x + (int64_t)j * gridDim.x) * TILE + (int64_t)tid * VW;
     apply_chunk<Op, T, R, Mdl>(a, k, src, i0, VW);
-    if constexpr (NOUT > 0) fence_proxy_async();  // this thread's stage writes before the bulk reads
-    __syncthreads();  // the whole block is done with stage s (refill it) and has filled the output stage
-    if (tid == 0) {
-      if constexpr (NOUT > 0) {
-        for (int q = 0; q < NOUT; ++q)
-          if (T* o = outp<T>(a, q)) bulk_s2g(o + tile * TILE, obuf + (size_t)q * TILE, TILE * sizeof(T));
-        bulk_commit();
-      }
-      if (has_tile(j + kStages)) {
-        fence_proxy_async();
-        issue(j + kStages);
-      }
+    __syncthreads();  // the whole block is done with stage s: refill it
+    if (tid == 0 && has_tile(j + kStages)) {
+      fence_proxy_async();
+      issue(j + kStages);
     }
   }
-  if constexpr (NOUT > 0)
-    if (tid == 0) bulk_wait_all();  // the output stage lives until the block exits
   if (has_tile(j)) {
     // A wait ran out: record it, wait (bounded again) for this block's copies
     // still in flight so that none lands after the block exits, and return.
@@ -1046,8 +970,7 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_direct(const
 template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const KArgs& a, cudaStream_t stream) {
   constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
   constexpr int TILE = kThreads * VW;
-  constexpr size_t kStageOutBytes = (size_t)StageOut<Op, T, R, Mdl>::planes * TILE * sizeof(T);
-  constexpr size_t kMaxSmem = (size_t)kStages * Op::kIn * TILE * sizeof(T) + kStageOutBytes;
+  constexpr size_t kMaxSmem = (size_t)kStages * Op::kIn * TILE * sizeof(T);
   auto kern = [] {
     if constexpr (kStaged3<R, Mdl>)
       return k_staged3<Op, T, R, Mdl>;
@@ -1063,7 +986,7 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
     if (e != cudaSuccess) return e;
     if (slot >= 0) attr_set[slot].store(1, std::memory_order_relaxed);
   }
-  const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T) + kStageOutBytes;
+  const size_t smem = (size_t)kStages * a.nin * TILE * sizeof(T);
   static std::atomic<int> bps_cache[Op::kIn + 1][kMaxDevices];  // blocks per SM for each nin
   const int bps = blocks_per_sm(kern, smem, bps_cache[a.nin]);
   const int64_t ntiles = a.n / TILE;
@@ -1081,8 +1004,7 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
 template <class Op, class T, class R, class Mdl = IdealModel>
 cudaError_t launch_op(const KArgs& a, cudaStream_t stream) {
   constexpr int TILE = kThreads * OpWidth<Op, T, R, Mdl>::VW;
-  const size_t ring = (size_t)kStages * a.nin * TILE * sizeof(T) +
-                      (size_t)StageOut<Op, T, R, Mdl>::planes * TILE * sizeof(T);
+  const size_t ring = (size_t)kStages * a.nin * TILE * sizeof(T);
   if (!(a.flags & kDirectOnly) && a.n / TILE >= 4LL * device_sm_count() && a.nin >= 1 && a.nin <= Op::kIn &&
       ring <= (100u << 10))
     return launch_staged<Op, T, R, Mdl>(a, stream);
