@@ -36,6 +36,17 @@ template <> struct Storage<__nv_bfloat16> { using L = float; static constexpr in
 template <class T, class R> struct Width { static constexpr int VW = Storage<T>::VW; };
 template <> struct Width<double, dw> { static constexpr int VW = 1; };
 
+// Register type of one compute value's storage word: Storage<T>::L, except for
+// packed double-word values (two points), whose storage word is a double pair.
+template <class T, class R> struct LoadOf { using type = typename Storage<T>::L; };
+template <> struct LoadOf<double, dw2> { using type = double2; };
+
+// Double-word compute types, scalar or packed (they keep the loaded doubles of
+// the outputs that are exact copies of inputs).
+template <class R> struct IsDw { static constexpr bool value = false; };
+template <> struct IsDw<dw> { static constexpr bool value = true; };
+template <> struct IsDw<dw2> { static constexpr bool value = true; };
+
 __device__ __forceinline__ double to_r(double x) { return x; }
 __device__ __forceinline__ float to_r(float x) { return x; }
 __device__ __forceinline__ float to_r(__half x) { return __half2float(x); }
@@ -155,6 +166,7 @@ struct NoGuard {
 };
 template <class R> struct GuardOf { using type = NoGuard; };
 template <> struct GuardOf<dw> { using type = DwGuard; };
+template <> struct GuardOf<dw2> { using type = DwGuard2; };
 
 // Register value (double or float) -> compute type.
 template <class R, class G> __device__ __forceinline__ R to_compute(double x, G&) { return x; }
@@ -162,10 +174,12 @@ template <class R, class G> __device__ __forceinline__ R to_compute(float x, G&)
 template <> __device__ __forceinline__ dw to_compute<dw, DwGuard>(double x, DwGuard& g) {
   return dw_from_double(x, g);
 }
+template <class R, class G> __device__ __forceinline__ R to_compute(double2 x, G& g) { return dw2_from_double2(x, g); }
 // Compute type -> register value of the storage's load type.
 __device__ __forceinline__ double to_load(double x) { return x; }
 __device__ __forceinline__ float to_load(float x) { return x; }
 __device__ __forceinline__ double to_load(dw x) { return dw_to_double(x); }
+__device__ __forceinline__ double2 to_load(dw2 x) { return dw2_to_double2(x); }
 
 // Load VW points starting at i0 in the storage's load type; cnt < VW only in
 // the ragged last chunk, where the missing lanes get `fill` (a harmless
@@ -204,11 +218,23 @@ __device__ __forceinline__ void store_raw(T* p, int64_t i0, int cnt, const typen
   }
 }
 
+// Store a pair of doubles (the two points of a packed value): cnt of them.
+template <class T, int VW>
+__device__ __forceinline__ void store_raw(T* p, int64_t i0, int cnt, const double2 (&raw)[VW]) {
+  static_assert(VW == 1, "one pair per call");
+  if (p == nullptr) return;
+  if (cnt == 2) {
+    __stcs(reinterpret_cast<double2*>(p + i0), raw[0]);
+  } else if (cnt == 1) {
+    p[i0] = raw[0].x;
+  }
+}
+
 // Store VW points of the compute type; a NULL plane is skipped.
 template <class T, int VW, class R>
 __device__ __forceinline__ void store(T* p, int64_t i0, int cnt, const R (&x)[VW]) {
   if (p == nullptr) return;
-  typename Storage<T>::L raw[VW];
+  typename LoadOf<T, R>::type raw[VW];
 #pragma unroll
   for (int j = 0; j < VW; ++j) raw[j] = to_load(x[j]);
   store_raw<T, VW>(p, i0, cnt, raw);
@@ -270,6 +296,9 @@ template <class R> struct Consts {
 template <class R, int D> struct RawState {};
 template <int D> struct RawState<dw, D> {
   double rho, m[D];
+};
+template <int D> struct RawState<dw2, D> {
+  double2 rho, m[D];
 };
 
 template <class R, int D> struct Pt {

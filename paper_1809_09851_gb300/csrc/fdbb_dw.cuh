@@ -307,6 +307,34 @@ __device__ __forceinline__ dw2 rcp_(dw2 y) {
 
 __device__ __forceinline__ dw2 operator/(dw2 a, dw2 b) { return a * rcp_(b); }
 
+// 1/sqrt(x), lane by lane the scalar rsqrt_ (one Newton step from the
+// hardware approximation, residual by TwoProd and FMA).
+__device__ __forceinline__ dw2 rsqrt_(dw2 x) {
+  const float2 y0 = make_float2(dw_rsqrt_approx(x.hi.x), dw_rsqrt_approx(x.hi.y));
+  const float2 q = p_mul(y0, y0);
+  const float2 qe = p_fma(y0, y0, p_neg(q));
+  float2 m = p_fma(x.hi, q, make_float2(-1.0f, -1.0f));
+  m = p_fma(x.hi, qe, m);
+  m = p_fma(x.lo, q, m);
+  const float2 c = p_fma(make_float2(0.375f, 0.375f), m, make_float2(-0.5f, -0.5f));
+  dw2 z;
+  dw2_fast_two_sum(y0, p_mul(y0, p_mul(m, c)), z.hi, z.lo);
+  return z;
+}
+
+// sqrt(x) = x / sqrt(x), exactly 0 in a lane whose x is 0 (as the scalar sqrt_).
+__device__ __forceinline__ dw2 sqrt_(dw2 x) {
+  const dw2 r = x * rsqrt_(x);
+  const bool zx = x.hi.x == 0.0f, zy = x.hi.y == 0.0f;
+  return dw2(make_float2(zx ? 0.0f : r.hi.x, zy ? 0.0f : r.hi.y), make_float2(zx ? 0.0f : r.lo.x, zy ? 0.0f : r.lo.y));
+}
+
+__device__ __forceinline__ dw2 abs_(dw2 x) {
+  const float sx = x.hi.x < 0.0f ? -1.0f : 1.0f, sy = x.hi.y < 0.0f ? -1.0f : 1.0f;
+  const float2 s = make_float2(sx, sy);
+  return dw2(p_mul(s, x.hi), p_mul(s, x.lo));
+}
+
 // Lanes and their assembly.
 __device__ __forceinline__ dw lane_x(dw2 v) { return dw(v.hi.x, v.lo.x); }
 __device__ __forceinline__ dw lane_y(dw2 v) { return dw(v.hi.y, v.lo.y); }
@@ -321,5 +349,19 @@ struct DwGuard2 : DwGuard {
     check(lane_y(x));
   }
 };
+
+// Two doubles (one per lane) to and from packed double-word, lane by lane the
+// scalar conversions.
+__device__ __forceinline__ dw2 dw2_from_double2(double2 x, DwGuard& g) {
+  return pack2(dw_from_double(x.x, g), dw_from_double(x.y, g));
+}
+__device__ __forceinline__ double2 dw2_to_double2(dw2 x) {
+  return make_double2(dw_to_double(lane_x(x)), dw_to_double(lane_y(x)));
+}
+
+// x^y of each lane through FP64 (the optional entropy output only).
+__device__ __forceinline__ dw2 pow_(dw2 x, dw2 y) {
+  return pack2(pow_(lane_x(x), lane_x(y)), pow_(lane_y(x), lane_y(y)));
+}
 
 }  // namespace fdbb

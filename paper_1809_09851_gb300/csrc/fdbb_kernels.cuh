@@ -52,6 +52,11 @@ template <> __device__ __forceinline__ Consts<dw> consts<dw>(const KArgs& a) {
   return {dw(a.kf[0], a.kl[0]), dw(a.kf[1], a.kl[1]), dw(a.kf[2], a.kl[2]), dw(a.kf[3], a.kl[3]),
           dw(a.kf[4], a.kl[4]), dw(a.kf[5], a.kl[5]), dw(a.kf[6], a.kl[6]), dw(a.kf[7], a.kl[7])};
 }
+// The double-word constants in both lanes of packed values.
+__device__ __forceinline__ Consts<dw2> splat_consts(const Consts<dw>& k) {
+  return {splat2(k.g), splat2(k.a1), splat2(k.g3), splat2(k.ta1),
+          splat2(k.ia1), splat2(k.mg), splat2(k.gia1), splat2(k.tcv)};
+}
 
 // Model tag of the ideal gas (the general-EOS tags are in fdbb_eos.cuh).
 struct IdealModel {
@@ -87,21 +92,20 @@ template <class T, int VW, class R, class Src>
 __device__ __forceinline__ void put(const KArgs& a, const Src&, int k, int64_t i0, int cnt, const R (&x)[VW]) {
   store<T, VW, R>(outp<T>(a, k), i0, cnt, x);
 }
-template <class T, int VW, class Src>
-__device__ __forceinline__ void put_raw(const KArgs& a, const Src&, int k, int64_t i0, int cnt,
-                                        const typename Storage<T>::L (&raw)[VW]) {
+template <class T, int VW, class Src, class L>
+__device__ __forceinline__ void put_raw(const KArgs& a, const Src&, int k, int64_t i0, int cnt, const L (&raw)[VW]) {
   store_raw<T, VW>(outp<T>(a, k), i0, cnt, raw);
 }
 
 // Conservative state of VW points from input planes base..base+D+1.
 template <class T, int VW, int D, class R, class G, class Src>
 __device__ __forceinline__ void load_U(const Src& src, int base, Pt<R, D> (&s)[VW], G& g) {
-  typename Storage<T>::L raw[VW];
+  typename LoadOf<T, R>::type raw[VW];
   src.raw(base, raw, 1.0f);
 #pragma unroll
   for (int j = 0; j < VW; ++j) {
     s[j].rho = to_compute<R, G>(raw[j], g);
-    if constexpr (std::is_same<R, dw>::value) s[j].raw.rho = raw[j];
+    if constexpr (IsDw<R>::value) s[j].raw.rho = raw[j];
   }
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -109,7 +113,7 @@ __device__ __forceinline__ void load_U(const Src& src, int base, Pt<R, D> (&s)[V
 #pragma unroll
     for (int j = 0; j < VW; ++j) {
       s[j].m[i] = to_compute<R, G>(raw[j], g);
-      if constexpr (std::is_same<R, dw>::value) s[j].raw.m[i] = raw[j];
+      if constexpr (IsDw<R>::value) s[j].raw.m[i] = raw[j];
     }
   }
   src.raw(base + D + 1, raw, 1.0f);
@@ -120,7 +124,7 @@ __device__ __forceinline__ void load_U(const Src& src, int base, Pt<R, D> (&s)[V
 // One plane, converted to the compute type.
 template <class T, int VW, class R, class G, class Src>
 __device__ __forceinline__ void load_plane(const Src& src, int k, R (&x)[VW], float fill, G& g) {
-  typename Storage<T>::L raw[VW];
+  typename LoadOf<T, R>::type raw[VW];
   src.raw(k, raw, fill);
 #pragma unroll
   for (int j = 0; j < VW; ++j) x[j] = to_compute<R, G>(raw[j], g);
@@ -139,6 +143,14 @@ __device__ __forceinline__ void load_field(const Src& src, int base, R (&w)[VW][
   }
 }
 
+// Sums of storage words, lane by lane for pairs.
+__device__ __forceinline__ double ladd(double x, double y) { return x + y; }
+__device__ __forceinline__ float ladd(float x, float y) { return x + y; }
+__device__ __forceinline__ double2 ladd(double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); }
+__device__ __forceinline__ double lsub(double x, double y) { return x - y; }
+__device__ __forceinline__ float lsub(float x, float y) { return x - y; }
+__device__ __forceinline__ double2 lsub(double2 x, double2 y) { return make_double2(x.x - y.x, x.y - y.y); }
+
 // Characteristic weights W (planes base..base+NV-1, inputs) for the inverse
 // transform, with the three sums of weights it needs -- w_1 + w_2 + w_nv,
 // w_nv - w_1 and w_1 + w_nv -- formed in the storage's own IEEE type before
@@ -148,7 +160,7 @@ __device__ __forceinline__ void load_field(const Src& src, int base, R (&w)[VW][
 template <class T, int VW, int NV, class R, class G, class Src>
 __device__ __forceinline__ void load_weights_inv(const Src& src, int base, R (&w)[VW][NV], R (&sum)[VW],
                                                  R (&anm1)[VW], R (&a1pn)[VW], G& g) {
-  using L = typename Storage<T>::L;
+  using L = typename LoadOf<T, R>::type;
   L raw[NV][VW];
 #pragma unroll
   for (int c = 0; c < NV; ++c) src.raw(base + c, raw[c], 0.0f);
@@ -157,9 +169,9 @@ __device__ __forceinline__ void load_weights_inv(const Src& src, int base, R (&w
 #pragma unroll
     for (int c = 0; c < NV; ++c) w[j][c] = to_compute<R, G>(raw[c][j], g);
     const L a1 = raw[0][j], a2 = raw[1][j], an = raw[NV - 1][j];
-    sum[j] = to_compute<R, G>(a1 + a2 + an, g);
-    anm1[j] = to_compute<R, G>(an - a1, g);
-    a1pn[j] = to_compute<R, G>(a1 + an, g);
+    sum[j] = to_compute<R, G>(ladd(ladd(a1, a2), an), g);
+    anm1[j] = to_compute<R, G>(lsub(an, a1), g);
+    a1pn[j] = to_compute<R, G>(ladd(a1, an), g);
   }
 }
 
@@ -191,9 +203,9 @@ __device__ __forceinline__ void emit_flux(const KArgs& a, const Src& src, int ba
 #pragma unroll
   for (int c = 0; c < D + 2; ++c) {
     if (!outp<T>(a, base + c)) continue;
-    if constexpr (std::is_same<R, dw>::value) {
+    if constexpr (IsDw<R>::value) {
       if (c == 0) {  // F_d[0] = m_d: the input itself, bit for bit
-        double raw[VW];
+        typename LoadOf<T, R>::type raw[VW];
 #pragma unroll
         for (int j = 0; j < VW; ++j) raw[j] = s[j].raw.m[d];
         put_raw<T, VW>(a, src, base + c, i0, cnt, raw);
@@ -267,8 +279,8 @@ template <int D> struct OpPrim {
     derive_all<VW, D, false>(s, k, g);
     if (!g.ok) return false;
     R x[VW];
-    if constexpr (std::is_same<R, dw>::value) {
-      double raw[VW];
+    if constexpr (IsDw<R>::value) {
+      typename LoadOf<T, R>::type raw[VW];
 #pragma unroll
       for (int j = 0; j < VW; ++j) raw[j] = s[j].raw.rho;
       store_raw<T, VW>(outp<T>(a, 0), i0, cnt, raw);
@@ -299,7 +311,7 @@ template <int D> struct OpCons {
                                                int cnt) {
     typename GuardOf<R>::type g;
     R rho[VW], v[D][VW], p[VW], x[VW];
-    typename Storage<T>::L rho_raw[VW];
+    typename LoadOf<T, R>::type rho_raw[VW];
     src.raw(0, rho_raw, 1.0f);
 #pragma unroll
     for (int j = 0; j < VW; ++j) rho[j] = to_compute<R>(rho_raw[j], g);
@@ -484,51 +496,11 @@ template <int D, int dj> struct OpFused {
   }
 };
 
-// The flux VJP of two points per thread in packed double-word arithmetic
-// (ideal gas, FP64 storage): the two points' doubles are split lane by lane,
-// the algebra runs on dw2 values (one packed FP32x2 instruction per step for
-// both points), and the results are rebuilt lane by lane.  Returns false,
-// like the scalar double-word path, when a value leaves the fast-path range.
-template <int D, int d, class Src>
-__device__ __forceinline__ bool vjp_packed(const KArgs& a, const Consts<dw>& k1, const Src& src, int64_t i0,
-                                           int cnt) {
-  constexpr int nv = D + 2;
-  DwGuard2 g;
-  const Consts<dw2> k = {splat2(k1.g),  splat2(k1.a1),   splat2(k1.g3),   splat2(k1.ta1),
-                         splat2(k1.ia1), splat2(k1.mg), splat2(k1.gia1), splat2(k1.tcv)};
-  double raw[2];
-  auto ld = [&](int q, float fill) {
-    src.raw(q, raw, fill);
-    const dw x0 = dw_from_double(raw[0], g);
-    const dw x1 = dw_from_double(raw[1], g);
-    return pack2(x0, x1);
-  };
-  Pt<dw2, D> s;
-  s.rho = ld(0, 1.0f);
-#pragma unroll
-  for (int i = 0; i < D; ++i) s.m[i] = ld(1 + i, 0.0f);
-  s.rE = ld(D + 1, 1.0f);
-  dw2 gg[nv], y[nv];
-#pragma unroll
-  for (int q = 0; q < nv; ++q) gg[q] = ld(nv + q, 0.0f);
-  derive<false>(s, k, g);
-  if (!g.ok) return false;
-  flux_vjp_pt<D, d>(s, k, gg, y);
-#pragma unroll
-  for (int q = 0; q < nv; ++q) {
-    raw[0] = dw_to_double(lane_x(y[q]));
-    raw[1] = dw_to_double(lane_y(y[q]));
-    store_raw<double, 2>(outp<double>(a, q), i0, cnt, raw);
-  }
-  return true;
-}
-
 template <int D, int d> struct OpVjp {
   static constexpr int kIn = 2 * (D + 2);
   template <class T, int VW, class R, class K, class Src>
   static __device__ __forceinline__ bool apply(const KArgs& a, const K& k, const Src& src, int64_t i0,
                                                int cnt) {
-    if constexpr (std::is_same<R, dw>::value && VW == 2 && K::kIdeal) return vjp_packed<D, d>(a, k, src, i0, cnt);
     constexpr int nv = D + 2;
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
@@ -608,12 +580,12 @@ template <int D, int d, bool INV> struct OpRoeChar {
 // raw.m[i]) for outputs that are copies of them.
 template <class T, int VW, int D, class R, class G, class Src>
 __device__ __forceinline__ void load_V(const Src& src, int base, Pt<R, D> (&s)[VW], G& g) {
-  typename Storage<T>::L raw[VW];
+  typename LoadOf<T, R>::type raw[VW];
   src.raw(base, raw, 1.0f);
 #pragma unroll
   for (int j = 0; j < VW; ++j) {
     s[j].rho = to_compute<R, G>(raw[j], g);
-    if constexpr (std::is_same<R, dw>::value) s[j].raw.rho = raw[j];
+    if constexpr (IsDw<R>::value) s[j].raw.rho = raw[j];
   }
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -621,7 +593,7 @@ __device__ __forceinline__ void load_V(const Src& src, int base, Pt<R, D> (&s)[V
 #pragma unroll
     for (int j = 0; j < VW; ++j) {
       s[j].v[i] = to_compute<R, G>(raw[j], g);
-      if constexpr (std::is_same<R, dw>::value) s[j].raw.m[i] = raw[j];
+      if constexpr (IsDw<R>::value) s[j].raw.m[i] = raw[j];
     }
   }
   src.raw(base + D + 1, raw, 1.0f);
@@ -683,9 +655,9 @@ template <int D, int d> struct OpJacPrim {
       for (int col = 0; col < nv; ++col) {
         T* o = outp<T>(a, row * nv + col);
         if (!o) continue;
-        if constexpr (std::is_same<R, dw>::value) {
+        if constexpr (IsDw<R>::value) {
           if (row == 0 && (col == 0 || col == 1 + d)) {  // u and rho: copies of the inputs
-            double raw[VW];
+            typename LoadOf<T, R>::type raw[VW];
 #pragma unroll
             for (int j = 0; j < VW; ++j) raw[j] = col == 0 ? s[j].raw.m[d] : s[j].raw.rho;
             store_raw<T, VW>(o, i0, cnt, raw);
@@ -780,37 +752,66 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
 // Kernels
 // ---------------------------------------------------------------------------
 
-// Points per thread and plane of an op: the storage's width, except the
-// ideal-gas double-word flux VJP, which takes two points per thread in packed
-// FP32x2 double-word arithmetic (vjp_packed).
-template <class Op, class T, class R, class Mdl> struct OpWidth { static constexpr int VW = Width<T, R>::VW; };
-template <int D, int d> struct OpWidth<OpVjp<D, d>, double, dw, IdealModel> { static constexpr int VW = 2; };
+// Points per thread and plane of an op: the storage's width (one point in
+// double-word arithmetic), except the ideal-gas double-word blocks listed
+// below, which take two points per thread and evaluate them as the two lanes
+// of packed FP32x2 double-word values (dw2): each FP32 step of the
+// double-word algebra is then one FADD2 / FMUL2 / FFMA2 for both points,
+// while the splits and rebuilds of the doubles stay per point.  Each lane
+// performs the scalar double-word operation's FP32 steps, in the same order
+// and with the same roundings, so a point's result does not depend on its
+// partner.
+#ifndef FDBB_DW_PACK
+#define FDBB_DW_PACK 1
+#endif
+#ifndef FDBB_DW_PACK_HEAVY
+#define FDBB_DW_PACK_HEAVY 1
+#endif
+template <class Op> struct DwPair { static constexpr bool value = false; };
+template <int D> struct DwPair<OpVMag2<D>> { static constexpr bool value = true; };
+template <int D> struct DwPair<OpEos<D>> { static constexpr bool value = true; };
+template <int D> struct DwPair<OpPrim<D>> { static constexpr bool value = true; };
+template <int D> struct DwPair<OpCons<D>> { static constexpr bool value = true; };
+template <int D> struct DwPair<OpTemp<D>> { static constexpr bool value = true; };
+template <int D, int d> struct DwPair<OpRiemann<D, d>> { static constexpr bool value = true; };
+template <int D, int d> struct DwPair<OpFlux<D, d>> { static constexpr bool value = true; };
+template <int D, int d> struct DwPair<OpFluxPrim<D, d>> { static constexpr bool value = FDBB_DW_PACK; };
+template <int D, int d> struct DwPair<OpJac<D, d>> { static constexpr bool value = true; };
+template <int D, int d> struct DwPair<OpJacPrim<D, d>> { static constexpr bool value = true; };
+template <int D, int d> struct DwPair<OpVjp<D, d>> { static constexpr bool value = true; };
+template <int D, int d, bool INV> struct DwPair<OpChar<D, d, INV>> { static constexpr bool value = FDBB_DW_PACK_HEAVY; };
+template <int D, int d> struct DwPair<OpFused<D, d>> { static constexpr bool value = FDBB_DW_PACK_HEAVY; };
 
-// The light ideal-gas double-word blocks (few planes and little arithmetic
-// per point; 32-56 registers at one point per thread) take two points per
-// thread: twice the independent work between the staged kernel's barriers
-// and half its per-tile overhead per point (A/B at 2^26: v_mag2 0.79 -> 0.94,
-// prim 0.77 -> 0.87, flux 0.73 -> 0.81, temperature 0.60 -> 0.70 of HBM; the
-// all-direction primitive-form flux was slower, 0.83 -> 0.81, and keeps one).
-template <int D> struct OpWidth<OpVMag2<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
-template <int D> struct OpWidth<OpEos<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
-template <int D> struct OpWidth<OpPrim<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
-template <int D> struct OpWidth<OpCons<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
-template <int D> struct OpWidth<OpTemp<D>, double, dw, IdealModel> { static constexpr int VW = 2; };
-template <int D, int d> struct OpWidth<OpRiemann<D, d>, double, dw, IdealModel> {
-  static constexpr int VW = 2;
-};
-template <int D, int d> struct OpWidth<OpFlux<D, d>, double, dw, IdealModel> { static constexpr int VW = 2; };
-template <int D, int d> struct OpWidth<OpJac<D, d>, double, dw, IdealModel> { static constexpr int VW = 2; };
-template <int D, int d> struct OpWidth<OpJacPrim<D, d>, double, dw, IdealModel> {
-  static constexpr int VW = 2;
+template <class Op, class T, class R, class Mdl> struct OpWidth {
+  static constexpr bool kPacked = FDBB_DW_PACK && std::is_same<T, double>::value && std::is_same<R, dw>::value &&
+                                  std::is_same<Mdl, IdealModel>::value && DwPair<Op>::value;
+  static constexpr int VW = (std::is_same<T, double>::value && std::is_same<R, dw>::value &&
+                             std::is_same<Mdl, IdealModel>::value && DwPair<Op>::value)
+                                ? 2
+                                : Width<T, R>::VW;
 };
 
+// A source of two points per plane presented as one packed value: its storage
+// word is the pair of doubles.
+template <class Src> struct PairSrc {
+  const Src& s;
+  __device__ __forceinline__ void raw(int k, double2 (&r)[1], float fill) const {
+    double t[2];
+    s.raw(k, t, fill);
+    r[0] = make_double2(t[0], t[1]);
+  }
+};
 
 template <class Op, class T, class R, class Mdl, class K, class Src>
 __device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Src& src, int64_t i0, int cnt) {
   constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
-  if constexpr (std::is_same<R, dw>::value) {
+  if constexpr (OpWidth<Op, T, R, Mdl>::kPacked) {
+    // packed double-word fast path (cnt points, 1 or 2); a pair with a value
+    // outside its range runs in native FP64
+    const PairSrc<Src> ps{src};
+    if (!Op::template apply<T, 1, dw2>(a, splat_consts(k), ps, i0, cnt))
+      Op::template apply<T, VW, double>(a, Mdl::template make<double>(a), src, i0, cnt);
+  } else if constexpr (std::is_same<R, dw>::value) {
     // double-word fast path; chunks outside its range run in native FP64
     if (!Op::template apply<T, VW, dw>(a, k, src, i0, cnt))
       Op::template apply<T, VW, double>(a, Mdl::template make<double>(a), src, i0, cnt);
