@@ -642,226 +642,18 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
   }
 }
 
-// ---------------------------------------------------------------------------
-// FP32 grids, second form: the same two-plane packed step with the plane-pair
-// tiles laid out as four float4 per cell -- (rho, m_x), (m_y, m_z), (rhoE, p),
-// (1/rho, c), each value as its (plane z, plane z + 1) pair -- so a cell is
-// read with four 128-bit shared-memory loads instead of eight 64-bit ones,
-// and with the next pair's conservative values copied from global memory
-// straight into its ring tile by per-thread asynchronous copies
-// (cp.async.ca, 4 bytes each: the periodic halo gather has no 16-byte
-// alignment), so no registers hold them in flight.  Each thread then derives
-// p, 1/rho and c of the slots it copied.  Every arithmetic step is the one of
-// k_fv_rusanov_step2, in the same order, so the two kernels give the same
-// bits.
-// ---------------------------------------------------------------------------
-struct QuadTile {
-  float4 v[4][kSlots];
-};
-
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
-               "l"(gsrc)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Float offsets of component q's (plane a, plane b) pair within a slot's four
-// float4: q = 0..4 -> (v[0].xy, v[0].zw, v[1].xy, v[1].zw, v[2].xy).
-__device__ __forceinline__ float* quad_u(QuadTile& P, int q, int slot) {
-  return reinterpret_cast<float*>(&P.v[q >> 1][slot]) + 2 * (q & 1);
-}
-
-__device__ __forceinline__ Cell2 quad_at(const QuadTile& P, int slot) {
-  const float4 a = P.v[0][slot], b = P.v[1][slot], c = P.v[2][slot], d = P.v[3][slot];
-  Cell2 e;
-  e.u[0].v = make_float2(a.x, a.y);
-  e.u[1].v = make_float2(a.z, a.w);
-  e.u[2].v = make_float2(b.x, b.y);
-  e.u[3].v = make_float2(b.z, b.w);
-  e.u[4].v = make_float2(c.x, c.y);
-  e.p.v = make_float2(c.z, c.w);
-  e.r.v = make_float2(d.x, d.y);
-  e.c.v = make_float2(d.z, d.w);
-  return e;
-}
-
-#ifndef FDBB_FV_STEP3_BLOCKS
-#define FDBB_FV_STEP3_BLOCKS 2
-#endif
-__global__ void __launch_bounds__(kFvThreads, FDBB_FV_STEP3_BLOCKS) k_fv_rusanov_step3(const __grid_constant__ FvArgs a) {
-  extern __shared__ __align__(16) unsigned char fv_smem[];
-  QuadTile* tiles = reinterpret_cast<QuadTile*>(fv_smem);  // ring of kPairRing
-  const Consts<float> k1 = fv_consts<float>(a.gamma);
-  const Consts2 k = {splat(k1.a1), splat(k1.g), splat(0.5f)};
-  const int tid = threadIdx.x, lx = tid % kBX, ly = tid / kBX;
-  const int own = (ly + 1) * kSX + (lx + 1);
-  for (int64_t vt = blockIdx.x; vt < a.tiles; vt += gridDim.x) {
-    const int gi = find_tile_grid(a, vt);
-    const fdbb_fv_grid& g = a.g[gi];
-    const int n = g.n;
-    const int ntx = ceil_div(n, kBX), nty = ceil_div(n, kBY);
-    int64_t loc = vt - a.tile_begin[gi];
-    const int tx = (int)(loc % ntx);
-    loc /= ntx;
-    const int ty = (int)(loc % nty);
-    const int tz = (int)(loc / nty);
-    const int x0 = tx * kBX, y0 = ty * kBY, z0 = tz * kZSeg;
-    const int z1 = z0 + kZSeg < n ? z0 + kZSeg : n;
-    float* smax = static_cast<float*>(a.smax) + 3 * g.slot;
-    const int ph = g.phase, ph1 = ph == 2 ? 0 : ph + 1, ph2 = ph1 == 2 ? 0 : ph1 + 1;
-    const float dx = 1.0f / float(n);
-    const float dt = float(a.cfl) * dx / smax[ph];
-    const f2 mhlam = splat(-(0.5f * (dt / dx)));  // -1/2 dt/dx: the faces carry twice the flux
-    if (tx == 0 && ty == 0 && tz == 0 && tid == 0) {  // the grid's first tile
-      smax[ph2] = 0.0f;  // read by the previous step, filled by the next one
-      if (g.dt_log) g.dt_log[g.step] = static_cast<double>(dt);
-    }
-    const int x = x0 + lx, y = y0 + ly;
-    const bool active = x < n && y < n;
-    int64_t slot_off[kSlotsPerThread];
-#pragma unroll
-    for (int j = 0; j < kSlotsPerThread; ++j) {
-      const int sl = tid + j * kFvThreads;
-      const int gx = (x0 + sl % kSX - 1 + n) % n, gy = (y0 + sl / kSX - 1 + n) % n;
-      slot_off[j] = (int64_t)gy * n + gx;
-    }
-    const int64_t plane = (int64_t)n * n;
-    auto wrap = [n](int z) { return z % n; };  // z >= 0
-    // copy U of planes za (lane x) and zb (lane y) of this thread's slots into P
-    auto copy_pair = [&](QuadTile& P, int za, int zb) {
-      const int64_t oa = (int64_t)za * plane, ob = (int64_t)zb * plane;
-#pragma unroll
-      for (int j = 0; j < kSlotsPerThread; ++j) {
-        const int sl = tid + j * kFvThreads;
-        if (sl < kSlots) {
-#pragma unroll
-          for (int q = 0; q < 5; ++q) {
-            float* d = quad_u(P, q, sl);
-            const float* src = static_cast<const float*>(g.U[q]);
-            cp_async4(d, src + oa + slot_off[j]);
-            cp_async4(d + 1, src + ob + slot_off[j]);
-          }
-        }
-      }
-      cp_async_commit();
-    };
-    // p, 1/rho and c of this thread's slots of P (after their copies landed)
-    auto derive_own = [&](QuadTile& P) {
-#pragma unroll
-      for (int j = 0; j < kSlotsPerThread; ++j) {
-        const int sl = tid + j * kFvThreads;
-        if (sl < kSlots) {
-          const float4 a0 = P.v[0][sl], a1 = P.v[1][sl], a2 = P.v[2][sl];
-          const f2 u[5] = {pk(a0.x, a0.y), pk(a0.z, a0.w), pk(a1.x, a1.y), pk(a1.z, a1.w), pk(a2.x, a2.y)};
-          const Cell2 e = derive2(u, k);
-          P.v[2][sl] = make_float4(a2.x, a2.y, e.p.v.x, e.p.v.y);
-          P.v[3][sl] = make_float4(e.r.v.x, e.r.v.y, e.c.v.x, e.c.v.y);
-        }
-      }
-    };
-    copy_pair(tiles[0], z0, wrap(z0 + 1));
-    copy_pair(tiles[1], wrap(z0 + 2), wrap(z0 + 3));
-    cp_async_wait<1>();  // pair 0 has landed
-    derive_own(tiles[0]);
-    __syncthreads();
-    // lower z face of plane z0, from the cells of planes z0 - 1 and z0 (lane x;
-    // the same packed sequence as the upper faces of the tile below)
-    f2 carry[5];
-    if (active) {
-      const int64_t cm = (int64_t)(z0 == 0 ? n - 1 : z0 - 1) * plane + (int64_t)y * n + x;
-      f2 um[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) um[q] = splat(ldg<float>(g.U[q], cm));
-      const Cell2 lower = derive2(um, k);
-      Cell2 cur = quad_at(tiles[0], own);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) cur.u[q] = splat(cur.u[q].v.x);
-      cur.p = splat(cur.p.v.x);
-      cur.r = splat(cur.r.v.x);
-      cur.c = splat(cur.c.v.x);
-      face2(side2<2>(lower), side2<2>(cur), carry);
-    }
-    float vmax = 0.0f;
-    // Iteration i reads tiles i and i + 1 of the ring; tile i + 1's copies
-    // were issued one iteration earlier, its derived values are formed here
-    // before the barrier, and after the barrier (everyone is done with
-    // iteration i - 1, the last reader of tile i + 2) the copies of pair
-    // i + 2 are issued into tile i + 2.
-    for (int z = z0, b = 0; z < z1; z += 2, b = b == kPairRing - 1 ? 0 : b + 1) {
-      const int b1 = b == kPairRing - 1 ? 0 : b + 1, b2 = b1 == kPairRing - 1 ? 0 : b1 + 1;
-      const QuadTile& C = tiles[b];
-      QuadTile& N = tiles[b1];
-      cp_async_wait<0>();
-      derive_own(N);  // planes z + 2, z + 3
-      __syncthreads();
-      if (z + 2 < z1) copy_pair(tiles[b2], wrap(z + 4), wrap(z + 5));
-      if (active) {
-        const bool two = z + 1 < z1;  // lane y is a cell of this segment
-        f2 lo[5], hi[5], div[5];
-        const Cell2 me = quad_at(C, own);
-        const Side2 cx = side2<0>(me);
-        face2(side2<0>(quad_at(C, own - 1)), cx, lo);
-        face2(cx, side2<0>(quad_at(C, own + 1)), hi);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) div[q] = hi[q] - lo[q];
-        const Side2 cy = side2<1>(me);
-        face2(side2<1>(quad_at(C, own - kSX)), cy, lo);
-        face2(cy, side2<1>(quad_at(C, own + kSX)), hi);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) div[q] = div[q] + (hi[q] - lo[q]);
-        const Cell2 nx = quad_at(N, own);
-        Cell2 up;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) up.u[q] = pk(me.u[q].v.y, nx.u[q].v.x);
-        up.p = pk(me.p.v.y, nx.p.v.x);
-        up.r = pk(me.r.v.y, nx.r.v.x);
-        up.c = pk(me.c.v.y, nx.c.v.x);
-        face2(side2<2>(me), side2<2>(up), hi);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          div[q] = div[q] + (hi[q] - pk(carry[q].v.x, hi[q].v.x));
-          carry[q] = splat(hi[q].v.y);
-        }
-        const int64_t c = ((int64_t)z * n + y) * n + x;
-        f2 un[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          un[q] = fma2(mhlam, div[q], me.u[q]);
-          static_cast<float*>(g.Unew[q])[c] = un[q].v.x;
-          if (two) static_cast<float*>(g.Unew[q])[c + plane] = un[q].v.y;
-        }
-        const Cell2 nw = derive2(un, k);
-        const f2 vs = abs2(un[1] * nw.r) + nw.c + (abs2(un[2] * nw.r) + nw.c) + (abs2(un[3] * nw.r) + nw.c);
-        vmax = vs.v.x > vmax ? vs.v.x : vmax;
-        if (two) vmax = vs.v.y > vmax ? vs.v.y : vmax;
-      }
-    }
-    cp_async_wait<0>();
-    __syncthreads();  // the next tile's prologue refills the ring
-    vmax = warp_max(vmax);
-    if ((tid & 31) == 0 && vmax > 0.0f) atomic_max_pos(smax + ph1, vmax);
-  }
-}
-
-#ifndef FDBB_FV_F32_KERNEL
-#define FDBB_FV_F32_KERNEL 3
-#endif
-
 constexpr size_t fv_step_smem(size_t es) { return 2 * (size_t)kSlotVals * kSlots * es; }
 
 // Step kernel and its dynamic shared memory for storage T: FP32 grids take
 // the packed two-plane kernel, FP64 grids the scalar one.
 template <class T> auto step_kernel() {
   if constexpr (std::is_same<T, float>::value)
-    return FDBB_FV_F32_KERNEL == 3 ? k_fv_rusanov_step3 : k_fv_rusanov_step2;
+    return k_fv_rusanov_step2;
   else
     return k_fv_rusanov_step<T>;
 }
 template <class T> constexpr size_t step_smem() {
-  return std::is_same<T, float>::value ? kPairRing * (FDBB_FV_F32_KERNEL == 3 ? sizeof(QuadTile) : sizeof(PairTile))
-                                       : fv_step_smem(sizeof(T));
+  return std::is_same<T, float>::value ? kPairRing * sizeof(PairTile) : fv_step_smem(sizeof(T));
 }
 
 // Resident blocks per SM of the step (step = true, after its opt-in to more

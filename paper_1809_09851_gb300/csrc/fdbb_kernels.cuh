@@ -753,42 +753,50 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
 // ---------------------------------------------------------------------------
 
 // Points per thread and plane of an op: the storage's width (one point in
-// double-word arithmetic), except the ideal-gas double-word blocks listed
-// below, which take two points per thread and evaluate them as the two lanes
-// of packed FP32x2 double-word values (dw2): each FP32 step of the
-// double-word algebra is then one FADD2 / FMUL2 / FFMA2 for both points,
-// while the splits and rebuilds of the doubles stay per point.  Each lane
-// performs the scalar double-word operation's FP32 steps, in the same order
-// and with the same roundings, so a point's result does not depend on its
-// partner.
-#ifndef FDBB_DW_PACK
-#define FDBB_DW_PACK 1
-#endif
-#ifndef FDBB_DW_PACK_HEAVY
-#define FDBB_DW_PACK_HEAVY 1
-#endif
-template <class Op> struct DwPair { static constexpr bool value = false; };
-template <int D> struct DwPair<OpVMag2<D>> { static constexpr bool value = true; };
-template <int D> struct DwPair<OpEos<D>> { static constexpr bool value = true; };
-template <int D> struct DwPair<OpPrim<D>> { static constexpr bool value = true; };
-template <int D> struct DwPair<OpCons<D>> { static constexpr bool value = true; };
-template <int D> struct DwPair<OpTemp<D>> { static constexpr bool value = true; };
-template <int D, int d> struct DwPair<OpRiemann<D, d>> { static constexpr bool value = true; };
-template <int D, int d> struct DwPair<OpFlux<D, d>> { static constexpr bool value = true; };
-template <int D, int d> struct DwPair<OpFluxPrim<D, d>> { static constexpr bool value = FDBB_DW_PACK; };
-template <int D, int d> struct DwPair<OpJac<D, d>> { static constexpr bool value = true; };
-template <int D, int d> struct DwPair<OpJacPrim<D, d>> { static constexpr bool value = true; };
-template <int D, int d> struct DwPair<OpVjp<D, d>> { static constexpr bool value = true; };
-template <int D, int d, bool INV> struct DwPair<OpChar<D, d, INV>> { static constexpr bool value = FDBB_DW_PACK_HEAVY; };
-template <int D, int d> struct DwPair<OpFused<D, d>> { static constexpr bool value = FDBB_DW_PACK_HEAVY; };
+// double-word arithmetic), except the ideal-gas double-word blocks below,
+// which take two points per thread -- as two independent scalar double-word
+// points (kPairs), or as the two lanes of packed FP32x2 double-word values
+// (kPacked, dw2): each FP32 step of the double-word algebra is then one
+// FADD2 / FMUL2 / FFMA2 for both points, while the splits and rebuilds of the
+// doubles stay per point.  Each lane performs the scalar double-word
+// operation's FP32 steps, in the same order and with the same roundings, so a
+// point's result does not depend on its partner.  The choice per block is the
+// faster one of an A/B at N = 2^26 on one GB300 (fraction of the measured HBM
+// bandwidth, one point / two points / two points packed):
+//   v_mag2 0.79 / 0.94 / 0.98, EOS 0.62 / 0.68 / 0.69, cons -> prim
+//   0.77 / 0.87 / 0.89, prim -> cons 0.91 / 0.91 / 0.89, Riemann invariants
+//   0.60 / 0.64 / 0.67, one flux column 0.73 / 0.81 / 0.77, all columns
+//   0.88 / 0.89 / 0.90, Jacobian 0.86 / 0.88 / 0.88, temperature
+//   0.60 / 0.70 / 0.69, all primitive-form columns 0.83 / 0.81 / 0.85,
+//   forward characteristic transform 0.66 / - / 0.73, inverse 0.61 / - /
+//   0.55, flux VJP - / 0.60 / 0.69; the fused pass 13.35 / - / 13.58
+//   Gpoints/s.  The Roe-averaged forms need 160-230 registers packed and keep
+//   one point.
+enum class DwMode { Single, Pairs, Packed };
+template <class Op> struct DwModeOf { static constexpr DwMode value = DwMode::Single; };
+template <int D> struct DwModeOf<OpVMag2<D>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D> struct DwModeOf<OpEos<D>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D> struct DwModeOf<OpPrim<D>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D> struct DwModeOf<OpCons<D>> { static constexpr DwMode value = DwMode::Pairs; };
+template <int D> struct DwModeOf<OpTemp<D>> { static constexpr DwMode value = DwMode::Pairs; };
+template <int D, int d> struct DwModeOf<OpRiemann<D, d>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D, int d> struct DwModeOf<OpFlux<D, d>> {
+  static constexpr DwMode value = d < 0 ? DwMode::Packed : DwMode::Pairs;
+};
+template <int D, int d> struct DwModeOf<OpFluxPrim<D, d>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D, int d> struct DwModeOf<OpJac<D, d>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D, int d> struct DwModeOf<OpJacPrim<D, d>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D, int d> struct DwModeOf<OpVjp<D, d>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D, int d> struct DwModeOf<OpCharFwd<D, d>> { static constexpr DwMode value = DwMode::Packed; };
+template <int D, int d> struct DwModeOf<OpFused<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 
 template <class Op, class T, class R, class Mdl> struct OpWidth {
-  static constexpr bool kPacked = FDBB_DW_PACK && std::is_same<T, double>::value && std::is_same<R, dw>::value &&
-                                  std::is_same<Mdl, IdealModel>::value && DwPair<Op>::value;
-  static constexpr int VW = (std::is_same<T, double>::value && std::is_same<R, dw>::value &&
-                             std::is_same<Mdl, IdealModel>::value && DwPair<Op>::value)
-                                ? 2
-                                : Width<T, R>::VW;
+  static constexpr DwMode kMode = (std::is_same<T, double>::value && std::is_same<R, dw>::value &&
+                                   std::is_same<Mdl, IdealModel>::value)
+                                      ? DwModeOf<Op>::value
+                                      : DwMode::Single;
+  static constexpr bool kPacked = kMode == DwMode::Packed;
+  static constexpr int VW = kMode == DwMode::Single ? Width<T, R>::VW : 2;
 };
 
 // A source of two points per plane presented as one packed value: its storage

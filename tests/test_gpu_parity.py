@@ -417,10 +417,9 @@ def test_staged_path_parity(dtype, dw):
 
 
 def test_staged_fused_with_skipped_flux_planes():
-    """The double-word fused pass moves its 15 flux planes through a
-    shared-memory output stage and bulk copies: NULL flux planes (never
-    copied out) and NULL Jacobian planes leave every other plane correct."""
-    n, D = staged_n(256, 77), 3
+    """The staged double-word fused pass (two points per thread, packed) with
+    NULL flux and Jacobian planes: every other plane is still correct."""
+    n, D = staged_n(512, 77), 3
     V, U, W = fields(n, D, seed=515)
     Ud, _ = quantise(U, torch.float64)
     Wd, _ = quantise(W, torch.float64)
@@ -436,6 +435,53 @@ def test_staged_fused_with_skipped_flux_planes():
         list(range(40, 45))
     got = host([*F, *A, *Y])
     check([got[k] for k in keep], [ref[k] for k in keep], [S[k] for k in keep], torch.float64, "staged fused, skips")
+
+
+def _floored_field(n, seed):
+    """A 3D field (and weights) whose momenta and weights all have magnitude
+    >= 1e-5, so no point leaves the double-word range and falls back."""
+    _, U, W = fields(n, 3, seed=seed)
+    floor = lambda x: np.where(np.abs(x) < 1e-5, np.copysign(1e-5, x), x)
+    return [U[0], *(floor(m) for m in U[1:4]), U[4]], [floor(w) for w in W]
+
+
+@pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
+def test_packed_blocks_lanes_are_independent(staged):
+    """Every double-word block that runs two points per thread as the lanes
+    of packed FP32x2 values gives a point the same bits whatever point shares
+    its pair: the field shifted by one point re-pairs every point."""
+    n = staged_n(1024, 1001) if staged else 4099
+    U, W = _floored_field(n + 1, 78)
+    Ud = [torch.from_numpy(u).to(DEV) for u in U]
+    Wd = [torch.from_numpy(w).to(DEV) for w in W]
+    first = lambda ts: [t[:n].clone() for t in ts]
+    second = lambda ts: [t[1:].clone() for t in ts]
+    calls = {
+        "fused": lambda U_, W_: [*sum(blocks.euler_fused(U_, W_, 1, G, dw=True), [])],
+        "v_mag2": lambda U_, W_: [blocks.v_mag2(U_, dw=True)],
+        "eos": lambda U_, W_: list(blocks.eos(U_, G, dw=True)),
+        "prim": lambda U_, W_: blocks.prim_from_cons(U_, G, dw=True),
+        "riemann": lambda U_, W_: list(blocks.riemann_inv(U_, 2, G, dw=True)[:2]),
+        "flux_all": lambda U_, W_: blocks.flux(U_, -1, G, dw=True),
+        "jac": lambda U_, W_: blocks.flux_jac(U_, 0, G, dw=True),
+        "char_fwd": lambda U_, W_: blocks.char_transform(U_, W_, 1, G, dw=True),
+        "vjp": lambda U_, W_: blocks.flux_vjp(U_, W_, 2, G, dw=True),
+    }
+    for name, fn in calls.items():
+        a = fn(first(Ud), first(Wd))
+        kind = capi.last_launch()
+        assert kind.points_per_thread == 2, name
+        assert kind.kernel == (capi.FDBB_KERNEL_STAGED if staged else capi.FDBB_KERNEL_DIRECT), name
+        b = fn(second(Ud), second(Wd))
+        for k, (x, y) in enumerate(zip(a, b)):
+            assert torch.equal(x[1:], y[:-1]), (name, k)
+    V = [torch.from_numpy(v).to(DEV) for v in oracle.prim_from_cons(3, G, U)]
+    for name, fn in {"flux_prim": lambda V_: blocks.flux_prim(V_, -1, G, dw=True),
+                     "jac_prim": lambda V_: blocks.flux_jac_prim(V_, 1, G, dw=True)}.items():
+        a, b = fn(first(V)), fn(second(V))
+        assert capi.last_launch().points_per_thread == 2, name
+        for k, (x, y) in enumerate(zip(a, b)):
+            assert torch.equal(x[1:], y[:-1]), (name, k)
 
 
 @pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])

@@ -44,7 +44,7 @@ def _restore_limit():
 
 def test_wait_that_runs_out_is_reported_and_writes_nothing(_restore_limit):
     L = _restore_limit
-    n = _staged_n(256, 7)  # the double-word fused pass takes 256-point tiles
+    n = _staged_n(512, 7)  # the double-word fused pass takes 512-point tiles (two points per thread)
     U, W = _field(n)
     Ud = [torch.from_numpy(u).to(DEV) for u in U]
     Wd = [torch.from_numpy(w).to(DEV) for w in W]
