@@ -87,9 +87,11 @@ typedef enum {
  *               derived quantity (v, |v|^2/2, p, H, c^2) is non-zero with
  *               magnitude outside [2^-24, 2^24], or not finite, is computed in
  *               IEEE double instead.  Outputs that are copies of an input are
- *               bit-exact.  The inverse characteristic transforms always use
- *               IEEE double.  On GPUs whose FP64 rate is a small fraction of
- *               the FP32 rate (GB300: 1/64) this is the fast FP64-storage form.
+ *               bit-exact.  The inverse characteristic transforms form their
+ *               sums of input weights (w_1 + w_2 + w_nv, w_nv - w_1, w_1 + w_nv)
+ *               in IEEE double, the rest in double-word.  On GPUs whose FP64
+ *               rate is a small fraction of the FP32 rate (GB300: 1/64) this is
+ *               the fast FP64-storage form.
  */
 typedef enum { FDBB_F64 = 0, FDBB_F32 = 1, FDBB_F16 = 2, FDBB_BF16 = 3, FDBB_F64_DW = 4 } fdbb_dtype;
 
@@ -146,6 +148,22 @@ typedef struct fdbb_launch_info {
   int32_t reserved;
 } fdbb_launch_info;
 FDBB_API fdbb_status fdbb_last_launch(fdbb_launch_info *info);
+
+/*
+ * Index checks of a debug build.  A library compiled with -DFDBB_DEBUG
+ * (libfdbb_debug.so: python -m paper_1809_09851_gb300.build --debug) checks,
+ * inside its kernels, every global-memory index of the point-wise blocks and
+ * the finite-volume steps against the field's size, and every plane index
+ * of the staged kernels' shared-memory ring against the planes staged,
+ * before the access.  A violation is counted, the first offending index
+ * kept, and the access skipped (a load reads a harmless value; nothing
+ * traps).  fdbb_debug_index_faults synchronises with the device, returns the
+ * number of violations since the previous call (and clears it), and stores
+ * the first offending index in *first_index (-1 if none; first_index may be
+ * NULL).  A release build compiles the checks out and returns -1; -2 means
+ * the counters could not be read.
+ */
+FDBB_API int64_t fdbb_debug_index_faults(int64_t *first_index);
 
 /*
  * Where a plane pointer lives, for callers that hand the blocks host memory:

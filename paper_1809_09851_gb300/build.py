@@ -20,6 +20,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBRARY = os.path.join(PKG, "libfdbb.so")
+# The debug build (-DFDBB_DEBUG): every kernel checks its indices before each
+# access and records violations (fdbb_debug_index_faults); slower, for testing.
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIBRARY_DEBUG = os.path.join(PKG, "libfdbb_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
@@ -42,24 +46,28 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIBRARY):
+def up_to_date(debug: bool = False) -> bool:
+    lib = LIBRARY_DEBUG if debug else LIBRARY
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIBRARY)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link libfdbb.so; returns its path."""
-    if not force and up_to_date():
-        return LIBRARY
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    """Compile and link libfdbb.so (debug=True: libfdbb_debug.so, with the
+    kernels' index checks); returns its path."""
+    if not force and up_to_date(debug):
+        return LIBRARY_DEBUG if debug else LIBRARY
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = BUILD_DEBUG if debug else BUILD
+    target = LIBRARY_DEBUG if debug else LIBRARY
+    os.makedirs(bdir, exist_ok=True)
     srcs = _sources()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DFDBB_DEBUG=1"] if debug else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -74,14 +82,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if log:
                 print(log, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = LIBRARY + f".tmp{os.getpid()}"
+    tmp = target + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-Xlinker", "--exclude-libs,ALL", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIBRARY)
-    return LIBRARY
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                debug="--debug" in sys.argv))

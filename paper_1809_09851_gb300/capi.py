@@ -1,6 +1,8 @@
 """ctypes binding of the C ABI in include/fdbb.h (argument marshalling only).
 
-``lib()`` loads ``libfdbb.so`` from the package directory.  There is no
+``lib()`` loads ``libfdbb.so`` from the package directory (with the
+environment variable FDBB_DEBUG=1: ``libfdbb_debug.so``, the build whose
+kernels check every index, see ``fdbb_debug_index_faults``).  There is no
 fallback: if the library has not been built (``paper_1809_09851_gb300.build``)
 every call raises.  The raw functions keep the C names (``fdbb_flux`` ...) and
 take plane-pointer arrays built with :func:`planes`.
@@ -10,7 +12,10 @@ from __future__ import annotations
 import ctypes
 import os
 
-from .build import LIBRARY
+from .build import LIBRARY, LIBRARY_DEBUG
+
+if os.environ.get("FDBB_DEBUG", "0") == "1":
+    LIBRARY = LIBRARY_DEBUG  # noqa: F811 - the debug build replaces the release one
 
 FDBB_OK = 0
 STATUS = {
@@ -143,6 +148,8 @@ def lib():
         L.fdbb_pointer_kind.restype = _i
         L.fdbb_set_wait_limit.argtypes = [_i]
         L.fdbb_set_wait_limit.restype = _i
+        L.fdbb_debug_index_faults.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+        L.fdbb_debug_index_faults.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -192,10 +199,18 @@ def device_status() -> int:
     return lib().fdbb_device_status()
 
 
+def debug_index_faults():
+    """(violations since the last call, first offending index) of a debug
+    build's kernel index checks; (-1, -1) for a release build."""
+    first = ctypes.c_int64(-1)
+    count = lib().fdbb_debug_index_faults(ctypes.byref(first))
+    return int(count), int(first.value)
+
+
 def status_string(status: int) -> str:
     return lib().fdbb_status_string(status).decode()
 
 
 def exported_symbols():
     return ["fdbb_status_string", "fdbb_version", "fdbb_device_status", "fdbb_pointer_kind", "fdbb_set_wait_limit",
-            *SIGNATURES.keys()]
+            "fdbb_debug_index_faults", *SIGNATURES.keys()]

@@ -49,6 +49,29 @@ void record_launch(int kernel, int grid, int block, int smem_bytes, int points_p
 
 int wait_limit_setting() { return g_wait_limit.load(std::memory_order_relaxed); }
 
+#ifdef FDBB_DEBUG
+// Index-check counters of debug builds: violations, first bad index.
+static __device__ unsigned long long g_debug_counters[2];
+
+unsigned long long* debug_counters() {
+  static std::atomic<unsigned long long*> cache[kMaxDevices];
+  const int slot = current_device_slot();
+  if (slot >= 0) {
+    unsigned long long* p = cache[slot].load(std::memory_order_relaxed);
+    if (p) return p;
+  }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_debug_counters) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (slot >= 0) cache[slot].store(static_cast<unsigned long long*>(p), std::memory_order_relaxed);
+  return static_cast<unsigned long long*>(p);
+}
+#else
+unsigned long long* debug_counters() { return nullptr; }
+#endif
+
 }  // namespace fdbb
 
 namespace {
@@ -109,6 +132,9 @@ KArgs make_args(int64_t n, double gamma, double cv = 0.0) {
   a.n = n;
   const int polls = fdbb::wait_limit_setting();
   a.wait_override = polls < 0 ? 0 : polls + 1;
+#ifdef FDBB_DEBUG
+  a.dbg = fdbb::debug_counters();
+#endif
   const double g = gamma, a1 = gamma - 1.0;
   const double tcv = cv > 0.0 ? 1.0 / (a1 * cv) : 1.0;
   const double kd[8] = {g, a1, 3.0 - g, 2.0 / a1, 1.0 / a1, -g, g / a1, tcv};
@@ -340,6 +366,25 @@ fdbb_status fdbb_device_status(void) {
 
 int fdbb_set_wait_limit(int polls) {
   return fdbb::g_wait_limit.exchange(polls < 0 ? -1 : polls, std::memory_order_relaxed);
+}
+
+int64_t fdbb_debug_index_faults(int64_t* first_index) {
+#ifdef FDBB_DEBUG
+  unsigned long long* p = fdbb::debug_counters();
+  if (p == nullptr) return -2;
+  unsigned long long h[2] = {0, 0};
+  if (cudaMemcpy(h, p, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return -2;
+  }
+  const unsigned long long zero[2] = {0, 0};
+  if (h[0] != 0 && cudaMemcpy(p, zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) cudaGetLastError();
+  if (first_index) *first_index = h[0] ? static_cast<int64_t>(h[1]) : -1;
+  return static_cast<int64_t>(h[0]);
+#else
+  if (first_index) *first_index = -1;
+  return -1;
+#endif
 }
 
 fdbb_status fdbb_last_launch(fdbb_launch_info* info) {

@@ -42,6 +42,7 @@ struct FvArgs {
   int64_t vcells;    // virtual cells (sum of padded grid sizes)
   double gamma, cfl;
   void* smax;        // 3 slots per grid, storage type T
+  unsigned long long* dbg;  // debug builds: index-check counters; else NULL
   int64_t tiles;     // step kernel: total tiles
   fdbb_fv_grid g[FDBB_FV_MAX_GRIDS];
   int64_t tile_begin[FDBB_FV_MAX_GRIDS];  // step kernel: first tile of each grid
@@ -83,6 +84,20 @@ __device__ __forceinline__ int find_grid(const FvArgs& a, int64_t vc) {
 
 template <class T> __device__ __forceinline__ T ldg(const void* p, int64_t i) {
   return __ldg(static_cast<const T*>(p) + i);
+}
+// Load element i of a plane of `size` cells (debug builds: checked; an index
+// out of range is recorded and reads 1).
+template <class T>
+__device__ __forceinline__ T ldg_in(unsigned long long* dbg, const void* p, int64_t i, int64_t size) {
+  if (!FDBB_IDX_OK(dbg, i >= 0 && i < size, i)) return T(1);
+  return ldg<T>(p, i);
+}
+// Store element i of a plane of `size` cells (debug builds: checked; an index
+// out of range is recorded and skipped).
+template <class T>
+__device__ __forceinline__ void st_in(unsigned long long* dbg, void* p, int64_t i, int64_t size, T v) {
+  if (!FDBB_IDX_OK(dbg, i >= 0 && i < size, i)) return;
+  static_cast<T*>(p)[i] = v;
 }
 
 // Positive floating-point values order like their bit patterns.
@@ -203,10 +218,11 @@ __device__ __forceinline__ void put_slot(const T (&u)[5], const Consts<T>& k, Pl
 }
 
 template <class T>
-__device__ __forceinline__ void load_cell(const fdbb_fv_grid& g, int x, int y, int z, T (&u)[5]) {
+__device__ __forceinline__ void load_cell(const FvArgs& a, const fdbb_fv_grid& g, int x, int y, int z, T (&u)[5]) {
   const int64_t c = ((int64_t)z * g.n + y) * g.n + x;
+  const int64_t size = (int64_t)g.n * g.n * g.n;
 #pragma unroll
-  for (int q = 0; q < 5; ++q) u[q] = ldg<T>(g.U[q], c);
+  for (int q = 0; q < 5; ++q) u[q] = ldg_in<T>(a.dbg, g.U[q], c, size);
 }
 
 // Conservative values of this thread's (at most two) slots of one plane tile.
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_con
         const int sl = tid + j * kFvThreads;
         if (sl < kSlots) {
 #pragma unroll
-          for (int q = 0; q < 5; ++q) r.u[j][q] = ldg<T>(g.U[q], zoff + slot_off[j]);
+          for (int q = 0; q < 5; ++q) r.u[j][q] = ldg_in<T>(a.dbg, g.U[q], zoff + slot_off[j], plane * n);
         }
       }
     };
@@ -341,7 +357,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_con
     if (active) {
       PlaneTile<T>& P1 = tiles[1];  // its own slot only, as scratch for the face
       T u[5];
-      load_cell<T>(g, x, y, z0 == 0 ? n - 1 : z0 - 1, u);
+      load_cell<T>(a, g, x, y, z0 == 0 ? n - 1 : z0 - 1, u);
       put_slot<T>(u, k, P1, own);
       face<T>(side<T, 2>(P1, own), side<T, 2>(tiles[0], own), zlo);
     }
@@ -379,7 +395,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_con
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           un[q] = fma_(-hlam, div[q], uc[q]);
-          static_cast<T*>(g.Unew[q])[c] = un[q];
+          st_in<T>(a.dbg, g.Unew[q], c, plane * n, un[q]);
         }
         Nw.rho = un[0];
         Nw.m[0] = un[1];
@@ -549,7 +565,8 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
         if (sl < kSlots) {
 #pragma unroll
           for (int q = 0; q < 5; ++q)
-            r.u[j][q] = pk(ldg<float>(g.U[q], oa + slot_off[j]), ldg<float>(g.U[q], ob + slot_off[j]));
+            r.u[j][q] = pk(ldg_in<float>(a.dbg, g.U[q], oa + slot_off[j], plane * n),
+                           ldg_in<float>(a.dbg, g.U[q], ob + slot_off[j], plane * n));
         }
       }
     };
@@ -572,7 +589,7 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
       const int64_t cm = (int64_t)(z0 == 0 ? n - 1 : z0 - 1) * plane + (int64_t)y * n + x;
       f2 um[5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) um[q] = splat(ldg<float>(g.U[q], cm));
+      for (int q = 0; q < 5; ++q) um[q] = splat(ldg_in<float>(a.dbg, g.U[q], cm, plane * n));
       const Cell2 lower = derive2(um, k);
       Cell2 cur = pair_at(tiles[0], own);
 #pragma unroll
@@ -627,8 +644,8 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           un[q] = fma2(mhlam, div[q], me.u[q]);
-          static_cast<float*>(g.Unew[q])[c] = un[q].v.x;
-          if (two) static_cast<float*>(g.Unew[q])[c + plane] = un[q].v.y;
+          st_in<float>(a.dbg, g.Unew[q], c, plane * n, un[q].v.x);
+          if (two) st_in<float>(a.dbg, g.Unew[q], c + plane, plane * n, un[q].v.y);
         }
         const Cell2 nw = derive2(un, k);
         const f2 vs = abs2(un[1] * nw.r) + nw.c + (abs2(un[2] * nw.r) + nw.c) + (abs2(un[3] * nw.r) + nw.c);
@@ -821,6 +838,7 @@ fdbb_status fv_run(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double
   a.gamma = gamma;
   a.cfl = cfl;
   a.smax = smax;
+  a.dbg = debug_counters();
   for (int i = 0; i < ngrids; ++i) a.g[i] = grids[i];
   fv_tiles(a);
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -890,6 +908,7 @@ fdbb_status fv_step_noalloc(int ngrids, const fdbb_fv_grid* grids, int64_t vcell
   const fdbb_status sst = noalloc_scratch(&scratch);
   if (sst != FDBB_OK) return sst;
   a.smax = scratch;
+  a.dbg = debug_counters();
   fv_tiles(a);
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // the slots keep the previous call's contents: clear them first

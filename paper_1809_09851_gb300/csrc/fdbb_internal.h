@@ -27,6 +27,7 @@ struct KArgs {
   int flags;     // launch options (kDirectOnly); not read by the kernels
   int wait_override;  // staged kernels' polls per bounded wait: 0 = the default
                       // limit, k > 0 = k - 1 polls (fdbb_set_wait_limit)
+  unsigned long long* dbg;  // debug builds: index-check counters (count, first bad index); else NULL
   double kd[8];  // gamma, gamma-1, 3-gamma, 2/(gamma-1), 1/(gamma-1), -gamma,
                  // gamma/(gamma-1), 1/((gamma-1) c_v)
   float kf[8];   // the same, rounded once to float
@@ -64,6 +65,25 @@ void record_launch(int kernel, int grid, int block, int smem_bytes, int points_p
 // Poll limit for the staged kernels' bounded waits (fdbb_set_wait_limit;
 // < 0: the kernels' default).
 int wait_limit_setting();
+
+// Debug builds (FDBB_DEBUG): device address of the index-check counters on
+// the current device (NULL if it cannot be looked up); release builds: NULL.
+unsigned long long* debug_counters();
+
+// Device-side index check of debug builds: true if `ok`; otherwise counts the
+// violation in dbg[0], keeps the first bad index in dbg[1] and returns false,
+// so that the caller skips the access.  Release builds compile it to true.
+#ifdef FDBB_DEBUG
+__device__ __forceinline__ bool dbg_check(unsigned long long* dbg, bool ok, int64_t index) {
+  if (!ok && dbg != nullptr) {
+    if (atomicAdd(&dbg[0], 1ull) == 0ull) dbg[1] = static_cast<unsigned long long>(index);
+  }
+  return ok;
+}
+#define FDBB_IDX_OK(dbg, cond, index) ::fdbb::dbg_check((dbg), (cond), (index))
+#else
+#define FDBB_IDX_OK(dbg, cond, index) true
+#endif
 
 // Defined once per storage type (one translation unit each).
 cudaError_t dispatch_f64(const LaunchReq& r, const KArgs& a);

@@ -73,6 +73,11 @@ template <class T, int VW> struct GlobalSrc {
   int64_t i0;
   int cnt;
   __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float fill) const {
+    if (!FDBB_IDX_OK(a.dbg, k >= 0 && k < a.nin && i0 >= 0 && cnt >= 1 && cnt <= VW && i0 + cnt <= a.n, i0)) {
+#pragma unroll
+      for (int j = 0; j < VW; ++j) r[j] = static_cast<typename Storage<T>::L>(fill);
+      return;
+    }
     load_raw<T, VW>(inp<T>(a, k), i0, cnt, r, fill);
   }
 };
@@ -82,18 +87,32 @@ template <class T, int VW> struct GlobalSrc {
 // tile, so a double-word chunk can be re-read for its FP64 fallback).
 template <class T, int VW, int TILE> struct SmemSrc {
   const T* base;
-  __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float) const {
+#ifdef FDBB_DEBUG
+  int nin;  // planes staged in the ring
+  unsigned long long* dbg;
+#endif
+  __device__ __forceinline__ void raw(int k, typename Storage<T>::L (&r)[VW], float fill) const {
+#ifdef FDBB_DEBUG
+    if (!FDBB_IDX_OK(dbg, k >= 0 && k < nin, k)) {
+#pragma unroll
+      for (int j = 0; j < VW; ++j) r[j] = static_cast<typename Storage<T>::L>(fill);
+      return;
+    }
+#endif
     ld_sh(base + (size_t)k * TILE, r);
   }
 };
 
 // Output plane k of the current VW points (a NULL plane is skipped).
+// (cnt counts points: up to VW, or 2 for one packed pair of points.)
 template <class T, int VW, class R, class Src>
 __device__ __forceinline__ void put(const KArgs& a, const Src&, int k, int64_t i0, int cnt, const R (&x)[VW]) {
+  if (!FDBB_IDX_OK(a.dbg, k >= 0 && k < kMaxOut && i0 >= 0 && cnt >= 1 && i0 + cnt <= a.n, i0)) return;
   store<T, VW, R>(outp<T>(a, k), i0, cnt, x);
 }
 template <class T, int VW, class Src, class L>
 __device__ __forceinline__ void put_raw(const KArgs& a, const Src&, int k, int64_t i0, int cnt, const L (&raw)[VW]) {
+  if (!FDBB_IDX_OK(a.dbg, k >= 0 && k < kMaxOut && i0 >= 0 && cnt >= 1 && i0 + cnt <= a.n, i0)) return;
   store_raw<T, VW>(outp<T>(a, k), i0, cnt, raw);
 }
 
@@ -869,6 +888,8 @@ __device__ __forceinline__ void staged_body(const KArgs& a) {
   auto issue = [&](int j) {
     const int s = j % kStages;
     const int64_t tile = blockIdx.x + (int64_t)j * gridDim.x;
+    // (a tile out of range issues nothing; its wait then runs out)
+    if (!FDBB_IDX_OK(a.dbg, tile >= 0 && (tile + 1) * TILE <= a.n && nin >= 1 && nin <= kMaxIn, tile * TILE)) return;
     mbar_expect_tx(&bars[s], nin * plane_bytes);
     for (int q = 0; q < nin; ++q)
       bulk_g2s(buf + ((size_t)s * nin + q) * TILE, inp<T>(a, q) + tile * TILE, plane_bytes, &bars[s]);
@@ -888,7 +909,11 @@ __device__ __forceinline__ void staged_body(const KArgs& a) {
     const int s = j % kStages;
     const bool ok = mbar_wait(&bars[s], (uint32_t)(j / kStages) & 1u, limit);
     if (__syncthreads_or(!ok)) break;
+#ifdef FDBB_DEBUG
+    const SmemSrc<T, VW, TILE> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW, nin, a.dbg};
+#else
     const SmemSrc<T, VW, TILE> src{buf + (size_t)s * nin * TILE + (size_t)tid * VW};
+#endif
     const int64_t i0 = (blockIdx.x + (int64_t)j * gridDim.x) * TILE + (int64_t)tid * VW;
     apply_chunk<Op, T, R, Mdl>(a, k, src, i0, VW);
     __syncthreads();  // the whole block is done with stage s: refill it

@@ -186,3 +186,9 @@ def test_launch_record_and_wait_limit_need_no_device(L):
         assert L.fdbb_set_wait_limit(-1) == -1
     finally:
         L.fdbb_set_wait_limit(prev)
+
+
+def test_release_build_has_no_index_checks(L):
+    """The release library compiles the kernels' index checks out: the debug
+    query answers -1 without touching the device."""
+    assert capi.debug_index_faults() == (-1, -1)
