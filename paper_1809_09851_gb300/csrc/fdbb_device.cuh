@@ -38,8 +38,10 @@ template <> struct Width<double, dw> { static constexpr int VW = 1; };
 
 // Register type of one compute value's storage word: Storage<T>::L, except for
 // packed double-word values (two points), whose storage word is a double pair.
+struct fl2;  // two float points in one packed register pair (below)
 template <class T, class R> struct LoadOf { using type = typename Storage<T>::L; };
 template <> struct LoadOf<double, dw2> { using type = double2; };
+template <class T> struct LoadOf<T, fl2> { using type = float2; };
 
 // Double-word compute types, scalar or packed (they keep the loaded doubles of
 // the outputs that are exact copies of inputs).
@@ -178,11 +180,13 @@ template <> __device__ __forceinline__ dw to_compute<dw, DwGuard>(double x, DwGu
   return dw_from_double(x, g);
 }
 template <class R, class G> __device__ __forceinline__ R to_compute(double2 x, G& g) { return dw2_from_double2(x, g); }
+template <class R, class G> __device__ __forceinline__ R to_compute(float2 x, G&) { return R(x); }
 // Compute type -> register value of the storage's load type.
 __device__ __forceinline__ double to_load(double x) { return x; }
 __device__ __forceinline__ float to_load(float x) { return x; }
 __device__ __forceinline__ double to_load(dw x) { return dw_to_double(x); }
 __device__ __forceinline__ double2 to_load(dw2 x) { return dw2_to_double2(x); }
+__device__ __forceinline__ float2 to_load(const fl2& x);
 
 // Load VW points starting at i0 in the storage's load type; cnt < VW only in
 // the ragged last chunk, where the missing lanes get `fill` (a harmless
@@ -233,6 +237,26 @@ __device__ __forceinline__ void store_raw(T* p, int64_t i0, int cnt, const doubl
   }
 }
 
+// Store pairs of float values (the points of packed float pairs): cnt points
+// (all 2 VW of them, or the first cnt of a ragged last chunk).
+template <class T, int VW>
+__device__ __forceinline__ void store_raw(T* p, int64_t i0, int cnt, const float2 (&raw)[VW]) {
+  if (p == nullptr) return;
+  float x[2 * VW];
+#pragma unroll
+  for (int j = 0; j < VW; ++j) {
+    x[2 * j] = raw[j].x;
+    x[2 * j + 1] = raw[j].y;
+  }
+  if (cnt == 2 * VW) {
+    st_vec(p + i0, x);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 2 * VW; ++j)
+      if (j < cnt) p[i0 + j] = from_r<T>(x[j]);
+  }
+}
+
 // Store VW points of the compute type; a NULL plane is skipped.
 template <class T, int VW, class R>
 __device__ __forceinline__ void store(T* p, int64_t i0, int cnt, const R (&x)[VW]) {
@@ -267,6 +291,39 @@ __device__ __forceinline__ float twice_(float x) { return x + x; }
 __device__ __forceinline__ dw twice_(dw x) { return dw(__fadd_rn(x.hi, x.hi), __fadd_rn(x.lo, x.lo)); }
 __device__ __forceinline__ dw2 half_(dw2 x) { return dw2(p_mul(make_float2(0.5f, 0.5f), x.hi), p_mul(make_float2(0.5f, 0.5f), x.lo)); }
 __device__ __forceinline__ dw2 twice_(dw2 x) { return dw2(p_add(x.hi, x.hi), p_add(x.lo, x.lo)); }
+
+// ---------------------------------------------------------------------------
+// Two float points in one packed FP32x2 register pair (sm_100 and later).  The
+// float-arithmetic blocks (FP32, FP16 and BF16 storage) evaluate the four
+// points of a thread as two such pairs: each addition, multiplication and
+// FMA is one FADD2 / FMUL2 / FFMA2 for both points, rounded to nearest per
+// lane; divisions, square roots, absolute values and powers run per lane.
+// ---------------------------------------------------------------------------
+struct fl2 {
+  float2 v;
+  fl2() = default;
+  __device__ __forceinline__ constexpr fl2(float2 x) : v(x) {}
+  __device__ __forceinline__ fl2(float x) : v(make_float2(x, x)) {}
+  __device__ __forceinline__ fl2(int x) : v(make_float2(static_cast<float>(x), static_cast<float>(x))) {}
+  fl2(double) = delete;
+};
+__device__ __forceinline__ fl2 operator+(fl2 a, fl2 b) { return fl2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ fl2 operator*(fl2 a, fl2 b) { return fl2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ fl2 operator-(fl2 a) { return fl2(make_float2(-a.v.x, -a.v.y)); }
+// a - b as (-1) b + a: the product is exact, so one rounding as in a subtraction
+__device__ __forceinline__ fl2 operator-(fl2 a, fl2 b) {
+  return fl2(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v));
+}
+__device__ __forceinline__ fl2 fma_(fl2 a, fl2 b, fl2 c) { return fl2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ fl2 half_(fl2 x) { return fl2(__fmul2_rn(make_float2(0.5f, 0.5f), x.v)); }
+__device__ __forceinline__ fl2 twice_(fl2 x) { return fl2(__fadd2_rn(x.v, x.v)); }
+__device__ __forceinline__ fl2 rcp_(fl2 x) { return fl2(make_float2(1.0f / x.v.x, 1.0f / x.v.y)); }
+__device__ __forceinline__ fl2 operator/(fl2 a, fl2 b) { return fl2(make_float2(a.v.x / b.v.x, a.v.y / b.v.y)); }
+__device__ __forceinline__ fl2 rsqrt_(fl2 x) { return fl2(make_float2(rsqrtf(x.v.x), rsqrtf(x.v.y))); }
+__device__ __forceinline__ fl2 sqrt_(fl2 x) { return fl2(make_float2(sqrtf(x.v.x), sqrtf(x.v.y))); }
+__device__ __forceinline__ fl2 abs_(fl2 x) { return fl2(make_float2(fabsf(x.v.x), fabsf(x.v.y))); }
+__device__ __forceinline__ fl2 pow_(fl2 x, fl2 y) { return fl2(make_float2(powf(x.v.x, y.v.x), powf(x.v.y, y.v.y))); }
+__device__ __forceinline__ float2 to_load(const fl2& x) { return x.v; }
 
 }  // namespace fdbb
 
@@ -384,6 +441,40 @@ __device__ __forceinline__ void internal_energy(Pt<float, D>& s, float& rhoe) {
   two_sum(s.rE, -qh, d, t);
   rhoe = __fadd_rn(d, __fsub_rn(t, ql));
   s.rq = qh;
+}
+// The same compensated evaluation on packed pairs, each lane step for step
+// the float one above.
+__device__ __forceinline__ float2 pk_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = pk_sub(s, a);
+  e = __fadd2_rn(pk_sub(a, pk_sub(s, bb)), pk_sub(b, bb));
+}
+__device__ __forceinline__ void two_prod2(float2 a, float2 b, float2& p, float2& e) {
+  p = __fmul2_rn(a, b);
+  e = __ffma2_rn(a, b, make_float2(-p.x, -p.y));
+}
+template <int D>
+__device__ __forceinline__ void internal_energy(Pt<fl2, D>& s, fl2& rhoe) {
+  float2 hi, lo;
+  two_prod2(s.m[0].v, s.m[0].v, hi, lo);
+#pragma unroll
+  for (int i = 1; i < D; ++i) {
+    float2 ph, pl, t;
+    two_prod2(s.m[i].v, s.m[i].v, ph, pl);
+    two_sum2(hi, ph, hi, t);
+    lo = __fadd2_rn(lo, __fadd2_rn(t, pl));
+  }
+  const float2 h = make_float2(0.5f, 0.5f);
+  hi = __fmul2_rn(h, hi);  // exact scaling by 1/2
+  lo = __fmul2_rn(h, lo);
+  const float2 qh = __fmul2_rn(hi, s.r.v);
+  const float2 rem = __ffma2_rn(make_float2(-qh.x, -qh.y), s.rho.v, hi);
+  const float2 ql = __fmul2_rn(__fadd2_rn(rem, lo), s.r.v);
+  float2 d, t;
+  two_sum2(s.rE.v, make_float2(-qh.x, -qh.y), d, t);
+  rhoe = fl2(__fadd2_rn(d, pk_sub(t, ql)));
+  s.rq = fl2(qh);
 }
 
 // Conservative -> derived state.  One reciprocal per point.  The guard sees

@@ -52,6 +52,10 @@ template <> __device__ __forceinline__ Consts<dw> consts<dw>(const KArgs& a) {
   return {dw(a.kf[0], a.kl[0]), dw(a.kf[1], a.kl[1]), dw(a.kf[2], a.kl[2]), dw(a.kf[3], a.kl[3]),
           dw(a.kf[4], a.kl[4]), dw(a.kf[5], a.kl[5]), dw(a.kf[6], a.kl[6]), dw(a.kf[7], a.kl[7])};
 }
+// The float constants in both lanes of packed float pairs.
+__device__ __forceinline__ Consts<fl2> splat_consts(const Consts<float>& k) {
+  return {fl2(k.g), fl2(k.a1), fl2(k.g3), fl2(k.ta1), fl2(k.ia1), fl2(k.mg), fl2(k.gia1), fl2(k.tcv)};
+}
 // The double-word constants in both lanes of packed values.
 __device__ __forceinline__ Consts<dw2> splat_consts(const Consts<dw>& k) {
   return {splat2(k.g), splat2(k.a1), splat2(k.g3), splat2(k.ta1),
@@ -169,6 +173,8 @@ __device__ __forceinline__ double2 ladd(double2 x, double2 y) { return make_doub
 __device__ __forceinline__ double lsub(double x, double y) { return x - y; }
 __device__ __forceinline__ float lsub(float x, float y) { return x - y; }
 __device__ __forceinline__ double2 lsub(double2 x, double2 y) { return make_double2(x.x - y.x, x.y - y.y); }
+__device__ __forceinline__ float2 ladd(float2 x, float2 y) { return make_float2(x.x + y.x, x.y + y.y); }
+__device__ __forceinline__ float2 lsub(float2 x, float2 y) { return make_float2(x.x - y.x, x.y - y.y); }
 
 // Characteristic weights W (planes base..base+NV-1, inputs) for the inverse
 // transform, with the three sums of weights it needs -- w_1 + w_2 + w_nv,
@@ -809,6 +815,13 @@ template <int D, int d> struct DwModeOf<OpVjp<D, d>> { static constexpr DwMode v
 template <int D, int d> struct DwModeOf<OpCharFwd<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D, int d> struct DwModeOf<OpFused<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 
+// The float-arithmetic ideal-gas blocks (FP32, FP16, BF16 storage) evaluate a
+// thread's four points as two packed FP32x2 pairs (fl2): the same registers,
+// about half the FP32 instructions.
+#ifndef FDBB_FLOAT_PACK
+#define FDBB_FLOAT_PACK 1
+#endif
+
 template <class Op, class T, class R, class Mdl> struct OpWidth {
   static constexpr DwMode kMode = (std::is_same<T, double>::value && std::is_same<R, dw>::value &&
                                    std::is_same<Mdl, IdealModel>::value)
@@ -816,6 +829,8 @@ template <class Op, class T, class R, class Mdl> struct OpWidth {
                                       : DwMode::Single;
   static constexpr bool kPacked = kMode == DwMode::Packed;
   static constexpr int VW = kMode == DwMode::Single ? Width<T, R>::VW : 2;
+  static constexpr bool kPackedF = FDBB_FLOAT_PACK && std::is_same<R, float>::value &&
+                                   std::is_same<Mdl, IdealModel>::value && VW == 4;
 };
 
 // A source of two points per plane presented as one packed value: its storage
@@ -829,10 +844,26 @@ template <class Src> struct PairSrc {
   }
 };
 
+// Four points per plane presented as two packed float pairs: its storage
+// words are pairs of floats.
+template <class Src> struct QuadSrc {
+  const Src& s;
+  __device__ __forceinline__ void raw(int k, float2 (&r)[2], float fill) const {
+    float t[4];
+    s.raw(k, t, fill);
+    r[0] = make_float2(t[0], t[1]);
+    r[1] = make_float2(t[2], t[3]);
+  }
+};
+
 template <class Op, class T, class R, class Mdl, class K, class Src>
 __device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Src& src, int64_t i0, int cnt) {
   constexpr int VW = OpWidth<Op, T, R, Mdl>::VW;
-  if constexpr (OpWidth<Op, T, R, Mdl>::kPacked) {
+  if constexpr (OpWidth<Op, T, R, Mdl>::kPackedF) {
+    // float arithmetic on two packed pairs (cnt points, up to four)
+    const QuadSrc<Src> qs{src};
+    Op::template apply<T, 2, fl2>(a, splat_consts(k), qs, i0, cnt);
+  } else if constexpr (OpWidth<Op, T, R, Mdl>::kPacked) {
     // packed double-word fast path (cnt points, 1 or 2); a pair with a value
     // outside its range runs in native FP64
     const PairSrc<Src> ps{src};
