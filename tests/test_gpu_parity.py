@@ -484,6 +484,41 @@ def test_packed_blocks_lanes_are_independent(staged):
             assert torch.equal(x[1:], y[:-1]), (name, k)
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
+def test_packed_float_lanes_are_independent(staged, dtype):
+    """The float-arithmetic blocks evaluate a thread's four points as two
+    packed FP32x2 pairs: a point's bits do not depend on which point shares
+    its pair or its thread (the field shifted by one point re-pairs them)."""
+    n = staged_n(1024, 1001) if staged else 4099
+    _, U, W = fields(n + 1, 3, seed=79)
+    Ud = [torch.from_numpy(u).to(DEV).to(dtype) for u in U]
+    Wd = [torch.from_numpy(w).to(DEV).to(dtype) for w in W]
+    first = lambda ts: [t[:n].clone() for t in ts]
+    second = lambda ts: [t[1:].clone() for t in ts]
+    calls = {
+        "fused": lambda U_, W_: [*sum(blocks.euler_fused(U_, W_, 1, G), [])],
+        "eos": lambda U_, W_: list(blocks.eos(U_, G)),
+        "riemann": lambda U_, W_: list(blocks.riemann_inv(U_, 2, G, entropy=True)),
+        "char_inv": lambda U_, W_: blocks.char_transform(U_, W_, 0, G, inverse=True),
+        "vjp": lambda U_, W_: blocks.flux_vjp(U_, W_, 2, G),
+        "roe": lambda U_, W_: blocks.roe_flux(U_, [torch.roll(u, 1) for u in U_], 1, G),
+        "temperature": lambda U_, W_: [blocks.temperature(U_, 2.5, G)],
+    }
+    for name, fn in calls.items():
+        a = fn(first(Ud), first(Wd))
+        assert capi.last_launch().kernel == (capi.FDBB_KERNEL_STAGED if staged else capi.FDBB_KERNEL_DIRECT), name
+        b = fn(second(Ud), second(Wd))
+        for k, (x, y) in enumerate(zip(a, b)):
+            if name == "roe":
+                # U_R is the field rolled by one point: point j of the first
+                # call and point j - 1 of the second see the same (U_L, U_R)
+                # for j >= 2 (away from the roll's seam)
+                assert torch.equal(x[2:], y[1:-1]), (name, k)
+            else:
+                assert torch.equal(x[1:], y[:-1]), (name, k)
+
+
 @pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
 def test_packed_vjp_lanes_are_independent(staged):
     """The double-word flux VJP runs two points per thread as the two lanes of
