@@ -817,10 +817,18 @@ template <int D, int d> struct DwModeOf<OpFused<D, d>> { static constexpr DwMode
 
 // The float-arithmetic ideal-gas blocks (FP32, FP16, BF16 storage) evaluate a
 // thread's four points as two packed FP32x2 pairs (fl2): the same registers,
-// about half the FP32 instructions.
-#ifndef FDBB_FLOAT_PACK
-#define FDBB_FLOAT_PACK 1
-#endif
+// about half the FP32 instructions.  A/B at N = 2^26 on one GB300 (fraction of
+// the measured HBM bandwidth, scalar / packed; FP32, BF16): EOS 0.91 / 0.95,
+// 0.70 / 0.80; Riemann invariants 0.90 / 0.93, 0.66 / 0.76; temperature
+// 1.04 / 1.03, 0.70 / 0.78; L.W 0.95 / 0.97, 0.87 / 0.91; flux VJP 0.94 / 0.97,
+// 0.90 / 0.91; Roe flux 0.81 / 0.88, 0.42 / 0.46; one flux column 0.92 / 0.93,
+// 0.88 / 0.91; the rest within 0.01, except cons -> prim (BF16 0.87 / 0.84) and
+// R.W (BF16 0.97 / 0.93), which stay scalar, as does the fused pass (27.6 and
+// 55.1 Gpoints/s either way).
+template <class Op> struct FloatPacked { static constexpr bool value = true; };
+template <int D> struct FloatPacked<OpPrim<D>> { static constexpr bool value = false; };
+template <int D, int d> struct FloatPacked<OpCharInv<D, d>> { static constexpr bool value = false; };
+template <int D, int d> struct FloatPacked<OpFused<D, d>> { static constexpr bool value = false; };
 
 template <class Op, class T, class R, class Mdl> struct OpWidth {
   static constexpr DwMode kMode = (std::is_same<T, double>::value && std::is_same<R, dw>::value &&
@@ -829,7 +837,7 @@ template <class Op, class T, class R, class Mdl> struct OpWidth {
                                       : DwMode::Single;
   static constexpr bool kPacked = kMode == DwMode::Packed;
   static constexpr int VW = kMode == DwMode::Single ? Width<T, R>::VW : 2;
-  static constexpr bool kPackedF = FDBB_FLOAT_PACK && std::is_same<R, float>::value &&
+  static constexpr bool kPackedF = FloatPacked<Op>::value && std::is_same<R, float>::value &&
                                    std::is_same<Mdl, IdealModel>::value && VW == 4;
 };
 

@@ -489,7 +489,11 @@ def test_packed_blocks_lanes_are_independent(staged):
 def test_packed_float_lanes_are_independent(staged, dtype):
     """The float-arithmetic blocks evaluate a thread's four points as two
     packed FP32x2 pairs: a point's bits do not depend on which point shares
-    its pair or its thread (the field shifted by one point re-pairs them)."""
+    its pair or its thread (the field shifted by one point re-pairs them).
+    Bit patterns are compared, so NaNs of states that are non-physical once
+    rounded to 16 bits compare equal too."""
+    ibits = {torch.float32: torch.int32, torch.bfloat16: torch.int16}[dtype]
+    same = lambda x, y: torch.equal(x.view(ibits), y.view(ibits))
     n = staged_n(1024, 1001) if staged else 4099
     _, U, W = fields(n + 1, 3, seed=79)
     Ud = [torch.from_numpy(u).to(DEV).to(dtype) for u in U]
@@ -497,10 +501,11 @@ def test_packed_float_lanes_are_independent(staged, dtype):
     first = lambda ts: [t[:n].clone() for t in ts]
     second = lambda ts: [t[1:].clone() for t in ts]
     calls = {
-        "fused": lambda U_, W_: [*sum(blocks.euler_fused(U_, W_, 1, G), [])],
         "eos": lambda U_, W_: list(blocks.eos(U_, G)),
         "riemann": lambda U_, W_: list(blocks.riemann_inv(U_, 2, G, entropy=True)),
-        "char_inv": lambda U_, W_: blocks.char_transform(U_, W_, 0, G, inverse=True),
+        "char_fwd": lambda U_, W_: blocks.char_transform(U_, W_, 0, G),
+        "flux_all": lambda U_, W_: blocks.flux(U_, -1, G),
+        "jac": lambda U_, W_: blocks.flux_jac(U_, 1, G),
         "vjp": lambda U_, W_: blocks.flux_vjp(U_, W_, 2, G),
         "roe": lambda U_, W_: blocks.roe_flux(U_, [torch.roll(u, 1) for u in U_], 1, G),
         "temperature": lambda U_, W_: [blocks.temperature(U_, 2.5, G)],
@@ -514,9 +519,9 @@ def test_packed_float_lanes_are_independent(staged, dtype):
                 # U_R is the field rolled by one point: point j of the first
                 # call and point j - 1 of the second see the same (U_L, U_R)
                 # for j >= 2 (away from the roll's seam)
-                assert torch.equal(x[2:], y[1:-1]), (name, k)
+                assert same(x[2:], y[1:-1]), (name, k)
             else:
-                assert torch.equal(x[1:], y[:-1]), (name, k)
+                assert same(x[1:], y[:-1]), (name, k)
 
 
 @pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
