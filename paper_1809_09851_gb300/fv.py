@@ -142,6 +142,40 @@ def new_grid_smooth(n: int, seed: int, slot: int, smax: torch.Tensor, dtype, dev
     return g
 
 
+class FvSnapshot:
+    """A grid's state in host memory: its conservative planes, the steps it
+    has taken and, if it logs them, its time steps so far."""
+
+    def __init__(self, n: int, step: int, U: List[torch.Tensor], dt_log: Optional[torch.Tensor]):
+        self.n, self.step, self.U, self.dt_log = n, step, U, dt_log
+
+
+def snapshot(g: FvGrid, stream=None) -> FvSnapshot:
+    """Copy a grid's state to host memory once the work queued on `stream`
+    (default: the current stream) has run; blocks until the copy is done."""
+    s = stream if stream is not None else torch.cuda.current_stream(g.U[0].device)
+    s.synchronize()
+    U = [u.to("cpu") for u in g.U]
+    dt = g.dt_log.to("cpu") if g.dt_log is not None else None
+    return FvSnapshot(g.n, g.step, U, dt)
+
+
+def restore(snap: FvSnapshot, slot: int, smax: torch.Tensor, gamma: float = 1.4, dt_log_steps: int = 0,
+            stream=None) -> FvGrid:
+    """A grid that resumes from a snapshot: its planes back on the device, its
+    step count, its logged time steps, its wave-speed slot reduced afresh from
+    the state (the exact maximum the step kernel would have left there, so the
+    resumed steps are bit for bit those of an uninterrupted run)."""
+    device = smax.device
+    U = [u.to(device) for u in snap.U]
+    g = grid_from_conservative(U, snap.n, slot, smax, gamma, dt_log_steps=dt_log_steps, stream=stream)
+    g.step = snap.step
+    if g.dt_log is not None and snap.dt_log is not None:
+        k = min(snap.dt_log.numel(), g.dt_log.numel())
+        g.dt_log[:k].copy_(snap.dt_log[:k])
+    return g
+
+
 class _null:
     def __enter__(self):
         return None

@@ -14,7 +14,11 @@ Each request asks for `steps` Rusanov steps on its own periodic n^3 grid
   * retires a request when its last step's event completes, recording its
     completion time on the device clock, and frees its memory and slot.
 Latency = completion - arrival (seconds on the same clock); throughput =
-cell-steps / wall time.  Admission, each batched step and each retirement are
+cell-steps / wall time.  A run can stop after a number of batched steps
+(`max_iterations`): the state of every unfinished request is then copied to
+host memory (fv.snapshot) and returned, and a later run -- of this server or
+another -- resumes those requests from their snapshots (`resume`), bit for bit
+where an uninterrupted run would have been.  Admission, each batched step and each retirement are
 NVTX ranges ("fdbb.admit", "fdbb.step", "fdbb.retire") for profilers that
 show a timeline.  A grid's results do not depend on the other grids
 in its launches (per-cell arithmetic is fixed and the time-step reduction is
@@ -78,6 +82,10 @@ class Report:
     launches: int = 0
     max_active: int = 0
     results: Dict[int, List[torch.Tensor]] = field(default_factory=dict)
+    # a run stopped by max_iterations: the unfinished requests' state, and the
+    # requests it never admitted
+    snapshots: Dict[int, fv.FvSnapshot] = field(default_factory=dict)
+    unstarted: List[int] = field(default_factory=list)
 
     def pct(self, q: float) -> float:
         xs = sorted(self.latencies.values())
@@ -128,11 +136,15 @@ class FVServer:
     def state_bytes(self, n: int) -> int:
         return 2 * 5 * n ** 3 * self.elem
 
-    def _admit(self, req: synth.Request, now: float) -> Job:
+    def _admit(self, req: synth.Request, now: float, resume=None) -> Job:
         nbytes = self.state_bytes(req.n)
         slot = self.free_slots.popleft()
         with torch.cuda.stream(self.stream):
-            if self.initial_state is None:
+            snap = resume.get(req.rid) if resume else None
+            if snap is not None:
+                g = fv.restore(snap, slot, self.smax, self.gamma, dt_log_steps=req.steps if self.log_dt else 0,
+                               stream=self.stream)
+            elif self.initial_state is None:
                 g = fv.new_grid_smooth(req.n, req.seed, slot, self.smax, self.dtype, self.device, self.gamma,
                                        dt_log_steps=req.steps if self.log_dt else 0, stream=self.stream)
             else:
@@ -142,9 +154,13 @@ class FVServer:
         self.used += nbytes
         return Job(req, g, nbytes, now)
 
-    def run(self, requests: List[synth.Request], realtime: bool = True) -> Report:
+    def run(self, requests: List[synth.Request], realtime: bool = True, max_iterations: Optional[int] = None,
+            resume: Optional[Dict[int, fv.FvSnapshot]] = None) -> Report:
         """Serve `requests` (sorted by arrival).  With realtime=False every
-        request is treated as already arrived (a closed batch)."""
+        request is treated as already arrived (a closed batch).  With
+        max_iterations the run stops after that many batched steps and returns
+        the unfinished requests' snapshots; `resume` maps request ids to
+        snapshots from which those requests continue."""
         rep = Report()
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         active: List[Job] = []
@@ -185,7 +201,7 @@ class FVServer:
                     if (self.used + need > self.budget or not self.free_slots
                             or (self.max_active is not None and len(active) >= self.max_active)):
                         break
-                    active.append(self._admit(pending.popleft(), now))
+                    active.append(self._admit(pending.popleft(), now, resume))
                     admitted += 1
             rep.max_active = max(rep.max_active, len(active))
             if not active:
@@ -209,6 +225,17 @@ class FVServer:
             active = [j for j in active if j.grid.step < j.req.steps]
             while len(inflight) > self.max_inflight:
                 retire(inflight.popleft())
+            if max_iterations is not None and rep.iterations >= max_iterations:
+                while inflight:
+                    retire(inflight.popleft())
+                for job in active:
+                    rep.snapshots[job.req.rid] = fv.snapshot(job.grid, self.stream)
+                    self.used -= job.nbytes
+                    self.free_slots.append(job.grid.slot)
+                    job.grid = None
+                active = []
+                rep.unstarted = [r.rid for r in pending]
+                pending.clear()
         while inflight:
             retire(inflight.popleft())
         torch.cuda.synchronize(self.device)

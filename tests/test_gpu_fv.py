@@ -230,3 +230,28 @@ def test_fv_step_hand_values(axis, dtype):
                                    err_msg=name)
         np.testing.assert_allclose(g.U[4].double().cpu().numpy(), 2.5 + 0.5 * u * u * want, rtol=tol,
                                    err_msg=name)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_serving_stops_and_resumes_bit_for_bit(dtype):
+    """A run stopped after a few batched steps copies its unfinished requests'
+    state to host memory; a fresh server resumes them from those snapshots
+    (and starts the ones never admitted).  Every request's final state equals
+    the uninterrupted run's bit for bit: the resumed time step comes from the
+    same exact maximum of the same state."""
+    shapes = [(16, 9), (23, 14), (18, 5), (31, 12), (20, 20), (17, 7), (25, 3)]
+    reqs = [synth.Request(i, 0.0, n, st, 500 + i) for i, (n, st) in enumerate(shapes)]
+    full = serve.FVServer(DEV, dtype, keep_results=True).run(reqs, realtime=False)
+    part = serve.FVServer(DEV, dtype, keep_results=True, max_active=4).run(reqs, realtime=False, max_iterations=6)
+    assert part.snapshots, "the stopped run left no request unfinished"
+    for rid, snap in part.snapshots.items():
+        assert 0 < snap.step < reqs[rid].steps and snap.U[0].device.type == "cpu"
+    rest_ids = set(part.snapshots) | set(part.unstarted)
+    assert not rest_ids & set(part.results)
+    rest = serve.FVServer(DEV, dtype, keep_results=True).run([r for r in reqs if r.rid in rest_ids],
+                                                             realtime=False, resume=part.snapshots)
+    results = {**part.results, **rest.results}
+    assert set(results) == {r.rid for r in reqs}
+    for rid, U in full.results.items():
+        for k, (a, b) in enumerate(zip(U, results[rid])):
+            assert torch.equal(a, b), (rid, k)
