@@ -32,13 +32,15 @@ namespace {
 
 constexpr int kFvThreads = FDBB_FV_TILE;
 
-// Tiles of the step kernel: a 32 x 8 (x, y) column segment of up to 32 planes.
-constexpr int kBX = 32, kBY = 8, kZSeg = 32;
+// Tiles of the step kernel: a 32 x 8 (x, y) column segment of up to zseg
+// planes (FvArgs::zseg, chosen per launch by fv_plan).
+constexpr int kBX = 32, kBY = 8;
 constexpr int kSX = kBX + 2, kSY = kBY + 2, kSlots = kSX * kSY;  // plane tile with a one-cell halo
 constexpr int kSlotVals = 8;  // U[5], p, 1/rho, c
 
 struct FvArgs {
   int ngrids;
+  int zseg;          // step kernel: planes per column segment (even)
   int64_t vcells;    // virtual cells (sum of padded grid sizes)
   double gamma, cfl;
   void* smax;        // 3 slots per grid, storage type T
@@ -56,7 +58,7 @@ void fv_tiles(FvArgs& a) {
   for (int i = 0; i < a.ngrids; ++i) {
     const int n = a.g[i].n;
     a.tile_begin[i] = t;
-    t += (int64_t)ceil_div(n, kBX) * ceil_div(n, kBY) * ceil_div(n, kZSeg);
+    t += (int64_t)ceil_div(n, kBX) * ceil_div(n, kBY) * ceil_div(n, a.zseg);
   }
   a.tiles = t;
 }
@@ -306,8 +308,8 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_con
     loc /= ntx;
     const int ty = (int)(loc % nty);
     const int tz = (int)(loc / nty);
-    const int x0 = tx * kBX, y0 = ty * kBY, z0 = tz * kZSeg;
-    const int z1 = z0 + kZSeg < n ? z0 + kZSeg : n;
+    const int x0 = tx * kBX, y0 = ty * kBY, z0 = tz * a.zseg;
+    const int z1 = z0 + a.zseg < n ? z0 + a.zseg : n;
     T* smax = static_cast<T*>(a.smax) + 3 * g.slot;
     const int ph = g.phase, ph1 = ph == 2 ? 0 : ph + 1, ph2 = ph1 == 2 ? 0 : ph1 + 1;
     const T dx = T(1) / T(n);
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_rusanov_step(const __grid_con
 //
 // A thread updates the same (x, y) cell of planes z and z + 1: lane x of each
 // packed value belongs to plane z, lane y to plane z + 1 (z - z0 even; the
-// segments start at multiples of kZSeg, which is even, so a plane has the same
+// segments start at multiples of the segment length, which is even, so a plane has the same
 // lane in every tile).  Every operation of the faces, the update and the
 // derived state then takes one packed instruction (FFMA2 / FADD2 / FMUL2 of
 // sm_100 and later) for two cells.  Each lane rounds like the scalar FP32
@@ -534,8 +536,8 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
     loc /= ntx;
     const int ty = (int)(loc % nty);
     const int tz = (int)(loc / nty);
-    const int x0 = tx * kBX, y0 = ty * kBY, z0 = tz * kZSeg;
-    const int z1 = z0 + kZSeg < n ? z0 + kZSeg : n;
+    const int x0 = tx * kBX, y0 = ty * kBY, z0 = tz * a.zseg;
+    const int z1 = z0 + a.zseg < n ? z0 + a.zseg : n;
     float* smax = static_cast<float*>(a.smax) + 3 * g.slot;
     const int ph = g.phase, ph1 = ph == 2 ? 0 : ph + 1, ph2 = ph1 == 2 ? 0 : ph1 + 1;
     const float dx = 1.0f / float(n);
@@ -702,6 +704,22 @@ template <class T> int fv_blocks_per_sm(bool step) {
   return b;
 }
 
+// Planes per column segment of the step kernel: the longest of 64, 32 and 16
+// that still gives every resident block at least three tiles.  Longer
+// segments spend less on each tile's prologue (8 grids of 128^3 on one
+// GB300: 16 planes 6.13e10, 32: 6.54e10, 64: 6.93e10, 128: 5.99e10
+// cell-steps/s); shorter ones keep every SM busy when few cells are stepped.
+// The results do not depend on it: every face is the same computation in any
+// segmentation.  Sets a.zseg and the tile table.
+template <class T> void fv_plan(FvArgs& a) {
+  const int64_t cap = (int64_t)device_sm_count() * fv_blocks_per_sm<T>(true);
+  for (int z : {64, 32, 16}) {
+    a.zseg = z;
+    fv_tiles(a);
+    if (a.tiles >= 3 * cap) return;
+  }
+}
+
 template <class T> cudaError_t fv_launch(const FvArgs& a, bool step, cudaStream_t s) {
   const int64_t work = step ? a.tiles : a.vcells / kFvThreads;
   const int64_t cap = (int64_t)device_sm_count() * fv_blocks_per_sm<T>(step);
@@ -840,7 +858,10 @@ fdbb_status fv_run(int ngrids, const fdbb_fv_grid* grids, int64_t vcells, double
   a.smax = smax;
   a.dbg = debug_counters();
   for (int i = 0; i < ngrids; ++i) a.g[i] = grids[i];
-  fv_tiles(a);
+  if (t == FDBB_F64)
+    fv_plan<double>(a);
+  else
+    fv_plan<float>(a);
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const cudaError_t e = t == FDBB_F64 ? fv_launch<double>(a, step, s) : fv_launch<float>(a, step, s);
   return e == cudaSuccess ? FDBB_OK : FDBB_ERR_CUDA;
@@ -909,7 +930,10 @@ fdbb_status fv_step_noalloc(int ngrids, const fdbb_fv_grid* grids, int64_t vcell
   if (sst != FDBB_OK) return sst;
   a.smax = scratch;
   a.dbg = debug_counters();
-  fv_tiles(a);
+  if (t == FDBB_F64)
+    fv_plan<double>(a);
+  else
+    fv_plan<float>(a);
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // the slots keep the previous call's contents: clear them first
   if (cudaMemsetAsync(scratch, 0, sizeof(double) * 3 * (size_t)ngrids, s) != cudaSuccess) {

@@ -66,12 +66,13 @@ def test_fv_fp32_matches_oracle():
 
 @pytest.mark.parametrize("n", [33, 45, 64])
 def test_fv_fp32_across_plane_segments(n):
-    """FP32 grids taller than one 32-plane column segment: the z face between
-    two segments is formed by both tiles (as the upper face of the lower tile's
-    last plane pair and as the carried lower face of the upper tile), and a
-    segment of odd length ends with a half-used plane pair (33 = 32 + 1,
-    45 = 32 + 13, 64 = 32 + 32).  Matches the FP64 oracle to 2e-5 and
-    conserves mass, momentum and energy to float rounding."""
+    """FP32 grids taller than one column segment (a lone small grid is cut
+    into 16-plane segments): the z face between two segments is formed by
+    both tiles (as the upper face of the lower tile's last plane pair and as
+    the carried lower face of the upper tile), and a segment of odd length
+    ends with a half-used plane pair (33 = 2 x 16 + 1, 45 = 2 x 16 + 13).
+    Matches the FP64 oracle to 2e-5 and conserves mass, momentum and energy
+    to float rounding."""
     steps = 3
     U = _initial(n, 6)
     Uq = [u.astype(np.float32).astype(np.float64) for u in U]
@@ -91,7 +92,7 @@ def test_fv_fp32_across_plane_segments(n):
 @pytest.mark.parametrize("n", [12, 45])
 def test_fv_fp32_plane_pairing_is_invisible(n):
     """FP32 grids run two z planes per thread as the lanes of packed FP32x2
-    values, in 32-plane column segments.  Rolling the periodic grid by one
+    values, in column segments of an even number of planes.  Rolling the periodic grid by one
     plane in z re-pairs every plane and moves every segment boundary relative
     to the data, and the result is the rolled result bit for bit: a face is the
     same packed sequence in either lane, and a carried lower face the same as
@@ -255,3 +256,24 @@ def test_serving_stops_and_resumes_bit_for_bit(dtype):
     for rid, U in full.results.items():
         for k, (a, b) in enumerate(zip(U, results[rid])):
             assert torch.equal(a, b), (rid, k)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_fv_segment_length_is_invisible(dtype):
+    """The step kernel cuts columns into segments whose length (64, 32 or 16
+    planes) depends on how many tiles a launch has.  A grid stepped alone
+    (few tiles: short segments) and in a batch with eight 128^3 grids (many
+    tiles: long segments) ends with the same bits."""
+    n, steps = 75, 3
+    U = _dev(_initial(n, 9), dtype)
+    smax = torch.zeros(3 * 9, dtype=dtype, device=DEV)
+    alone = fv.grid_from_conservative(U, n, 0, smax, G_)
+    for _ in range(steps):
+        fv.rusanov_step([alone], smax, G_, 0.4)
+    fillers = [fv.new_grid_smooth(128, 90 + i, 1 + i, smax, dtype, DEV) for i in range(8)]
+    mixed = fv.grid_from_conservative(U, n, 0, smax, G_)
+    for _ in range(steps):
+        fv.rusanov_step([*fillers[:4], mixed, *fillers[4:]], smax, G_, 0.4)
+    torch.cuda.synchronize()
+    for k in range(5):
+        assert torch.equal(alone.U[k], mixed.U[k]), k
