@@ -444,10 +444,12 @@ __device__ __forceinline__ f2 max2(f2 a, f2 b) {
 }
 
 // Plane-pair tile: for each of the kSlots cells of a (32+2) x (8+2) tile,
-// U, p, 1/rho and c of planes z (x) and z + 1 (y); the kernel keeps a ring of
-// three (3 x 21.8 KB).
+// U, p, 1/rho and c of planes z and z + 1, as four float4 per slot --
+// (rho, m_x), (m_y, m_z), (rhoE, p), (1/rho, c), each value as its
+// (plane z, plane z + 1) pair: half the shared-memory instructions of one
+// float2 per value.  The kernel keeps a ring of three (3 x 21.8 KB).
 struct PairTile {
-  float2 v[kSlotVals][kSlots];
+  float4 v[kSlotVals / 2][kSlots];
 };
 constexpr int kPairRing = 3;
 struct Cell2 {
@@ -470,20 +472,24 @@ __device__ __forceinline__ Cell2 derive2(const f2 (&u)[5], const Consts2& k) {
   e.c = pk(fv_sqrt(c2.v.x), fv_sqrt(c2.v.y));
   return e;
 }
+__device__ __forceinline__ float4 q4(f2 a, f2 b) { return make_float4(a.v.x, a.v.y, b.v.x, b.v.y); }
 __device__ __forceinline__ void put_pair(const Cell2& e, PairTile& P, int slot) {
-#pragma unroll
-  for (int q = 0; q < 5; ++q) P.v[q][slot] = e.u[q].v;
-  P.v[5][slot] = e.p.v;
-  P.v[6][slot] = e.r.v;
-  P.v[7][slot] = e.c.v;
+  P.v[0][slot] = q4(e.u[0], e.u[1]);
+  P.v[1][slot] = q4(e.u[2], e.u[3]);
+  P.v[2][slot] = q4(e.u[4], e.p);
+  P.v[3][slot] = q4(e.r, e.c);
 }
 __device__ __forceinline__ Cell2 pair_at(const PairTile& P, int slot) {
+  const float4 a = P.v[0][slot], b = P.v[1][slot], c = P.v[2][slot], d = P.v[3][slot];
   Cell2 e;
-#pragma unroll
-  for (int q = 0; q < 5; ++q) e.u[q].v = P.v[q][slot];
-  e.p.v = P.v[5][slot];
-  e.r.v = P.v[6][slot];
-  e.c.v = P.v[7][slot];
+  e.u[0] = pk(a.x, a.y);
+  e.u[1] = pk(a.z, a.w);
+  e.u[2] = pk(b.x, b.y);
+  e.u[3] = pk(b.z, b.w);
+  e.u[4] = pk(c.x, c.y);
+  e.p = pk(c.z, c.w);
+  e.r = pk(d.x, d.y);
+  e.c = pk(d.z, d.w);
   return e;
 }
 
@@ -557,7 +563,12 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
       slot_off[j] = (int64_t)gy * n + gx;
     }
     const int64_t plane = (int64_t)n * n;
-    auto wrap = [n](int z) { return z % n; };  // z >= 0
+    // z mod n for 0 <= z < n + 6: one compare and subtract (a modulo by the
+    // run-time n is an integer-division sequence; only grids of n <= 5 need it)
+    auto wrap = [n](int z) {
+      const int w = z - n;
+      return z < n ? z : (w < n ? w : w % n);
+    };
     // planes za (lane x) and zb (lane y) of this thread's slots
     auto load_pair = [&](PairRaw& r, int za, int zb) {
       const int64_t oa = (int64_t)za * plane, ob = (int64_t)zb * plane;
