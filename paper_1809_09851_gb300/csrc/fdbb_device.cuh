@@ -188,6 +188,25 @@ __device__ __forceinline__ double to_load(dw x) { return dw_to_double(x); }
 __device__ __forceinline__ double2 to_load(dw2 x) { return dw2_to_double2(x); }
 __device__ __forceinline__ float2 to_load(const fl2& x);
 
+// The same in conversion form C of the double-word types (fdbb_dw.cuh; the
+// default form is the one of to_compute and to_load).
+template <class R, DwConv C, class G, class L> __device__ __forceinline__ R to_compute_c(L x, G& g) {
+  if constexpr (C != DwConv::kClamp && std::is_same<R, dw2>::value)
+    return dw2_from_double2<C>(x, g);
+  else if constexpr (C != DwConv::kClamp && std::is_same<R, dw>::value)
+    return dw_from_double<C>(x, g);
+  else
+    return to_compute<R, G>(x, g);
+}
+template <DwConv C, class R> __device__ __forceinline__ auto to_load_c(const R& x) {
+  if constexpr (C != DwConv::kClamp && std::is_same<R, dw2>::value)
+    return dw2_to_double2<C>(x);
+  else if constexpr (C != DwConv::kClamp && std::is_same<R, dw>::value)
+    return dw_to_double<C>(x);
+  else
+    return to_load(x);
+}
+
 // Load VW points starting at i0 in the storage's load type; cnt < VW only in
 // the ragged last chunk, where the missing lanes get `fill` (a harmless
 // in-range value that is never stored).
@@ -264,6 +283,16 @@ __device__ __forceinline__ void store(T* p, int64_t i0, int cnt, const R (&x)[VW
   typename LoadOf<T, R>::type raw[VW];
 #pragma unroll
   for (int j = 0; j < VW; ++j) raw[j] = to_load(x[j]);
+  store_raw<T, VW>(p, i0, cnt, raw);
+}
+
+// store in conversion form C
+template <class T, int VW, class R, DwConv C>
+__device__ __forceinline__ void store_c(T* p, int64_t i0, int cnt, const R (&x)[VW]) {
+  if (p == nullptr) return;
+  typename LoadOf<T, R>::type raw[VW];
+#pragma unroll
+  for (int j = 0; j < VW; ++j) raw[j] = to_load_c<C>(x[j]);
   store_raw<T, VW>(p, i0, cnt, raw);
 }
 

@@ -144,14 +144,6 @@ __device__ __forceinline__ dw sqrt_(dw x) {
   return x * rsqrt_(x);
 }
 
-__device__ __forceinline__ double dw_to_double(dw x);
-__device__ __forceinline__ dw dw_from_double_unchecked(double x);
-
-// x^y through FP64 (used only for the optional entropy output).
-__device__ __forceinline__ dw pow_(dw x, dw y) {
-  return dw_from_double_unchecked(pow(dw_to_double(x), dw_to_double(y)));
-}
-
 // ---------------------------------------------------------------------------
 // Conversions between IEEE double and double-word, in integer arithmetic.
 // ---------------------------------------------------------------------------
@@ -166,24 +158,48 @@ struct DwGuard {
   }
 };
 
+// Two instruction sequences for each conversion, with the same results up to
+// the sign of a zero and values below 2^-82 (where both stay within |lo| of
+// hi + lo).  They differ in how a zero is handled -- by clamping the exponent
+// arithmetic (kClamp, fewer instructions) or by selects at the end (kSelect)
+// -- and so in how the compiler schedules them: which is faster depends on
+// the register pressure of the kernel (the table at DwConvOf in
+// fdbb_kernels.cuh).
+enum class DwConv { kClamp, kSelect };
+
 // Split a double into hi (its leading 24 significant bits, truncated) and lo
 // (the next 23 bits, exact in float): |x - (hi + lo)| <= 2^-47 |x|.  The
 // guard records whether x is 0 or 2^-24 <= |x| < 2^24 (tested on the double's
 // own exponent field, since outside 2^-102 <= |x| < 2^128 the split itself is
 // meaningless).
+template <DwConv C = DwConv::kClamp>
 __device__ __forceinline__ dw dw_from_double(double x, DwGuard& g) {
   const uint32_t H = static_cast<uint32_t>(__double2hiint(x));
   const uint32_t L = static_cast<uint32_t>(__double2loint(x));
-  const bool zero = ((H << 1) | L) == 0u;
-  const uint32_t E = (H >> 20) & 0x7FFu;
-  g.ok &= zero | ((E - 999u) < 48u);                            // 0 or 2^-24 <= |x| < 2^24
-  const uint32_t sign = H & 0x80000000u;
-  const uint32_t t = (H & 0x7FFFFFFFu) - (896u << 20);        // exponent 1023 -> 127 bias
-  const uint32_t hb = __funnelshift_l(L, t, 3) | sign;          // sign | exp | top 23 mantissa bits
-  const uint32_t base = (hb & 0xFF800000u) - (23u << 23);       // sign | 2^(e-23)
-  const uint32_t yb = base | ((L >> 6) & 0x007FFFFFu);          // 2^(e-23) * (1 + next 23 bits)
-  const float lo = __fsub_rn(__uint_as_float(yb), __uint_as_float(base));
-  return dw(zero ? 0.0f : __uint_as_float(hb), zero ? 0.0f : lo);
+  if constexpr (C == DwConv::kClamp) {
+    const uint32_t mag = H & 0x7FFFFFFFu;
+    const bool zero = (mag | L) == 0u;
+    g.ok &= zero | ((mag - (999u << 20)) < (48u << 20));       // 0 or 2^-24 <= |x| < 2^24
+    // exponent 1023 -> 127 bias, clamped at 0: a zero gives hi = +-0 and
+    // lo = 0 (other values below 2^-127 fail the guard)
+    const int32_t tb = static_cast<int32_t>(mag) - static_cast<int32_t>(896u << 20);
+    const uint32_t t = static_cast<uint32_t>(tb > 0 ? tb : 0);
+    const uint32_t hb = __funnelshift_l(L, t, 3) | (H & 0x80000000u);  // sign | exp | top 23 mantissa bits
+    const uint32_t base = (hb & 0xFF800000u) - (23u << 23);     // sign | 2^(e-23)
+    const uint32_t yb = base | ((L >> 6) & 0x007FFFFFu);        // 2^(e-23) * (1 + next 23 bits)
+    return dw(__uint_as_float(hb), __fsub_rn(__uint_as_float(yb), __uint_as_float(base)));
+  } else {
+    const bool zero = ((H << 1) | L) == 0u;
+    const uint32_t E = (H >> 20) & 0x7FFu;
+    g.ok &= zero | ((E - 999u) < 48u);
+    const uint32_t sign = H & 0x80000000u;
+    const uint32_t t = (H & 0x7FFFFFFFu) - (896u << 20);
+    const uint32_t hb = __funnelshift_l(L, t, 3) | sign;
+    const uint32_t base = (hb & 0xFF800000u) - (23u << 23);
+    const uint32_t yb = base | ((L >> 6) & 0x007FFFFFu);
+    const float lo = __fsub_rn(__uint_as_float(yb), __uint_as_float(base));
+    return dw(zero ? 0.0f : __uint_as_float(hb), zero ? 0.0f : lo);
+  }
 }
 
 __device__ __forceinline__ dw dw_from_double_unchecked(double x) {
@@ -194,26 +210,51 @@ __device__ __forceinline__ dw dw_from_double_unchecked(double x) {
 // hi + lo rounded to a double: the double of hi is built from its bit pattern
 // and lo is added as an integer number of units of 2^(e_hi - 45) (|lo| <
 // 2^(e_hi - 23), so the count fits the float magic-number rounding range).
-// Error <= 2^-46 |x|.  When hi is a power of two and the correction is
-// negative the result lies in the binade below, whose ulp is half as large.
+// Error <= 2^-46 |x| for |x| >= 2^-82; below, where the scale 2^(45 - e_hi)
+// is not a normal float, at most |lo|.  When hi is a power of two and the
+// correction is negative the result lies in the binade below, whose ulp is
+// half as large.
+template <DwConv C = DwConv::kClamp>
 __device__ __forceinline__ double dw_to_double(dw x) {
   const uint32_t f = __float_as_uint(x.hi);
-  const uint32_t mag = f & 0x7FFFFFFFu;
-  const uint32_t sign = f & 0x80000000u;
-  const uint32_t H = ((mag >> 3) + (896u << 20)) | sign;
-  const uint32_t L = f << 29;
-  const int64_t bits = static_cast<int64_t>((static_cast<uint64_t>(H) << 32) | L);
-  const uint32_t ebits = mag & 0x7F800000u;
-  // lo in units of 2^(e_hi - 45); only when |hi| >= 2^-82, where the scale
-  // 2^(45 - e_hi) is a normal float (below that lo is dropped)
-  const float scale = __uint_as_float(((299u << 23) - ebits) | sign);
-  const float k = __fmaf_rn(x.lo, scale, 12582912.0f);  // round to an integer via 1.5 * 2^23
-  const int32_t ki0 = static_cast<int32_t>(__float_as_uint(k)) - 0x4B400000;
-  const int32_t ki = ebits >= (45u << 23) ? ki0 : 0;
-  const int64_t unit = ((mag & 0x007FFFFFu) == 0u && ki < 0) ? 256 : 128;
-  const int64_t out = bits + static_cast<int64_t>(ki) * unit;
-  // |hi| < 2^-126 (zero or subnormal): a signed zero
-  return mag < 0x00800000u ? __hiloint2double(static_cast<int>(sign), 0) : __longlong_as_double(out);
+  if constexpr (C == DwConv::kClamp) {
+    const uint32_t ebits = f & 0x7F800000u;
+    // sign, the 8 exponent bits rebiased by 896 (not for a zero or subnormal
+    // hi, whose double is then 0 or below 2^-1022) and the 23 mantissa bits
+    const uint32_t H = (static_cast<uint32_t>(static_cast<int32_t>(f) >> 3) & 0x8FFFFFFFu) +
+                       (ebits != 0u ? (896u << 20) : 0u);
+    const uint32_t L = f << 29;
+    // the scale is capped at 2^127: for |hi| < 2^-82 less than lo is added,
+    // and a zero hi (with its zero lo) adds nothing
+    const uint32_t sb = min((299u << 23) - ebits, 0x7F000000u);
+    const float k = __fmaf_rn(x.lo, __uint_as_float(sb | (f & 0x80000000u)), 12582912.0f);  // 1.5 * 2^23
+    const int32_t ki = static_cast<int32_t>(__float_as_uint(k)) - 0x4B400000;
+    const int32_t unit = ((f & 0x007FFFFFu) == 0u && ki < 0) ? 256 : 128;
+    const int64_t bits = static_cast<int64_t>((static_cast<uint64_t>(H) << 32) | L);
+    return __longlong_as_double(bits + static_cast<int64_t>(ki) * unit);
+  } else {
+    const uint32_t mag = f & 0x7FFFFFFFu;
+    const uint32_t sign = f & 0x80000000u;
+    const uint32_t H = ((mag >> 3) + (896u << 20)) | sign;
+    const uint32_t L = f << 29;
+    const int64_t bits = static_cast<int64_t>((static_cast<uint64_t>(H) << 32) | L);
+    const uint32_t ebits = mag & 0x7F800000u;
+    // below |hi| = 2^-82 lo is dropped
+    const float scale = __uint_as_float(((299u << 23) - ebits) | sign);
+    const float k = __fmaf_rn(x.lo, scale, 12582912.0f);
+    const int32_t ki0 = static_cast<int32_t>(__float_as_uint(k)) - 0x4B400000;
+    const int32_t ki = ebits >= (45u << 23) ? ki0 : 0;
+    const int64_t unit = ((mag & 0x007FFFFFu) == 0u && ki < 0) ? 256 : 128;
+    const int64_t out = bits + static_cast<int64_t>(ki) * unit;
+    // |hi| < 2^-126 (zero or subnormal): a signed zero
+    return mag < 0x00800000u ? __hiloint2double(static_cast<int>(sign), 0) : __longlong_as_double(out);
+  }
+}
+
+
+// x^y through FP64 (used only for the optional entropy output).
+__device__ __forceinline__ dw pow_(dw x, dw y) {
+  return dw_from_double_unchecked(pow(dw_to_double(x), dw_to_double(y)));
 }
 
 // ---------------------------------------------------------------------------
@@ -352,11 +393,13 @@ struct DwGuard2 : DwGuard {
 
 // Two doubles (one per lane) to and from packed double-word, lane by lane the
 // scalar conversions.
+template <DwConv C = DwConv::kClamp>
 __device__ __forceinline__ dw2 dw2_from_double2(double2 x, DwGuard& g) {
-  return pack2(dw_from_double(x.x, g), dw_from_double(x.y, g));
+  return pack2(dw_from_double<C>(x.x, g), dw_from_double<C>(x.y, g));
 }
+template <DwConv C = DwConv::kClamp>
 __device__ __forceinline__ double2 dw2_to_double2(dw2 x) {
-  return make_double2(dw_to_double(lane_x(x)), dw_to_double(lane_y(x)));
+  return make_double2(dw_to_double<C>(lane_x(x)), dw_to_double<C>(lane_y(x)));
 }
 
 // x^y of each lane through FP64 (the optional entropy output only).

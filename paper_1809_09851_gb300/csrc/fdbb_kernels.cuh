@@ -73,6 +73,7 @@ struct IdealModel {
 
 // Straight from global memory (cnt < VW only in the ragged last chunk).
 template <class T, int VW> struct GlobalSrc {
+  static constexpr DwConv kConv = DwConv::kClamp;
   const KArgs& a;
   int64_t i0;
   int cnt;
@@ -90,6 +91,7 @@ template <class T, int VW> struct GlobalSrc {
 // at base + k * TILE (the stage stays valid until the block has finished the
 // tile, so a double-word chunk can be re-read for its FP64 fallback).
 template <class T, int VW, int TILE> struct SmemSrc {
+  static constexpr DwConv kConv = DwConv::kClamp;
   const T* base;
 #ifdef FDBB_DEBUG
   int nin;  // planes staged in the ring
@@ -107,12 +109,13 @@ template <class T, int VW, int TILE> struct SmemSrc {
   }
 };
 
-// Output plane k of the current VW points (a NULL plane is skipped).
+// Output plane k of the current VW points (a NULL plane is skipped), in the
+// source's conversion form.
 // (cnt counts points: up to VW, or 2 for one packed pair of points.)
 template <class T, int VW, class R, class Src>
 __device__ __forceinline__ void put(const KArgs& a, const Src&, int k, int64_t i0, int cnt, const R (&x)[VW]) {
   if (!FDBB_IDX_OK(a.dbg, k >= 0 && k < kMaxOut && i0 >= 0 && cnt >= 1 && i0 + cnt <= a.n, i0)) return;
-  store<T, VW, R>(outp<T>(a, k), i0, cnt, x);
+  store_c<T, VW, R, Src::kConv>(outp<T>(a, k), i0, cnt, x);
 }
 template <class T, int VW, class Src, class L>
 __device__ __forceinline__ void put_raw(const KArgs& a, const Src&, int k, int64_t i0, int cnt, const L (&raw)[VW]) {
@@ -127,7 +130,7 @@ __device__ __forceinline__ void load_U(const Src& src, int base, Pt<R, D> (&s)[V
   src.raw(base, raw, 1.0f);
 #pragma unroll
   for (int j = 0; j < VW; ++j) {
-    s[j].rho = to_compute<R, G>(raw[j], g);
+    s[j].rho = to_compute_c<R, Src::kConv>(raw[j], g);
     if constexpr (IsDw<R>::value) s[j].raw.rho = raw[j];
   }
 #pragma unroll
@@ -135,13 +138,13 @@ __device__ __forceinline__ void load_U(const Src& src, int base, Pt<R, D> (&s)[V
     src.raw(base + 1 + i, raw, 0.0f);
 #pragma unroll
     for (int j = 0; j < VW; ++j) {
-      s[j].m[i] = to_compute<R, G>(raw[j], g);
+      s[j].m[i] = to_compute_c<R, Src::kConv>(raw[j], g);
       if constexpr (IsDw<R>::value) s[j].raw.m[i] = raw[j];
     }
   }
   src.raw(base + D + 1, raw, 1.0f);
 #pragma unroll
-  for (int j = 0; j < VW; ++j) s[j].rE = to_compute<R, G>(raw[j], g);
+  for (int j = 0; j < VW; ++j) s[j].rE = to_compute_c<R, Src::kConv>(raw[j], g);
 }
 
 // One plane, converted to the compute type.
@@ -150,7 +153,7 @@ __device__ __forceinline__ void load_plane(const Src& src, int k, R (&x)[VW], fl
   typename LoadOf<T, R>::type raw[VW];
   src.raw(k, raw, fill);
 #pragma unroll
-  for (int j = 0; j < VW; ++j) x[j] = to_compute<R, G>(raw[j], g);
+  for (int j = 0; j < VW; ++j) x[j] = to_compute_c<R, Src::kConv>(raw[j], g);
 }
 
 // nv planes of a second input field (W or G) from planes base..base+nv-1,
@@ -192,11 +195,11 @@ __device__ __forceinline__ void load_weights_inv(const Src& src, int base, R (&w
 #pragma unroll
   for (int j = 0; j < VW; ++j) {
 #pragma unroll
-    for (int c = 0; c < NV; ++c) w[j][c] = to_compute<R, G>(raw[c][j], g);
+    for (int c = 0; c < NV; ++c) w[j][c] = to_compute_c<R, Src::kConv>(raw[c][j], g);
     const L a1 = raw[0][j], a2 = raw[1][j], an = raw[NV - 1][j];
-    sum[j] = to_compute<R, G>(ladd(ladd(a1, a2), an), g);
-    anm1[j] = to_compute<R, G>(lsub(an, a1), g);
-    a1pn[j] = to_compute<R, G>(ladd(a1, an), g);
+    sum[j] = to_compute_c<R, Src::kConv>(ladd(ladd(a1, a2), an), g);
+    anm1[j] = to_compute_c<R, Src::kConv>(lsub(an, a1), g);
+    a1pn[j] = to_compute_c<R, Src::kConv>(ladd(a1, an), g);
   }
 }
 
@@ -339,7 +342,7 @@ template <int D> struct OpCons {
     typename LoadOf<T, R>::type rho_raw[VW];
     src.raw(0, rho_raw, 1.0f);
 #pragma unroll
-    for (int j = 0; j < VW; ++j) rho[j] = to_compute<R>(rho_raw[j], g);
+    for (int j = 0; j < VW; ++j) rho[j] = to_compute_c<R, Src::kConv>(rho_raw[j], g);
 #pragma unroll
     for (int i = 0; i < D; ++i) load_plane<T, VW, R>(src, 1 + i, v[i], 0.0f, g);
     load_plane<T, VW, R>(src, D + 1, p, 1.0f, g);
@@ -609,7 +612,7 @@ __device__ __forceinline__ void load_V(const Src& src, int base, Pt<R, D> (&s)[V
   src.raw(base, raw, 1.0f);
 #pragma unroll
   for (int j = 0; j < VW; ++j) {
-    s[j].rho = to_compute<R, G>(raw[j], g);
+    s[j].rho = to_compute_c<R, Src::kConv>(raw[j], g);
     if constexpr (IsDw<R>::value) s[j].raw.rho = raw[j];
   }
 #pragma unroll
@@ -617,13 +620,13 @@ __device__ __forceinline__ void load_V(const Src& src, int base, Pt<R, D> (&s)[V
     src.raw(base + 1 + i, raw, 0.0f);
 #pragma unroll
     for (int j = 0; j < VW; ++j) {
-      s[j].v[i] = to_compute<R, G>(raw[j], g);
+      s[j].v[i] = to_compute_c<R, Src::kConv>(raw[j], g);
       if constexpr (IsDw<R>::value) s[j].raw.m[i] = raw[j];
     }
   }
   src.raw(base + D + 1, raw, 1.0f);
 #pragma unroll
-  for (int j = 0; j < VW; ++j) s[j].p = to_compute<R, G>(raw[j], g);
+  for (int j = 0; j < VW; ++j) s[j].p = to_compute_c<R, Src::kConv>(raw[j], g);
 }
 
 // Inviscid flux from primitive variables V (planes 0..nv-1): column d, or
@@ -816,6 +819,18 @@ template <int D, int d> struct DwModeOf<OpVjp<D, d>> { static constexpr DwMode v
 template <int D, int d> struct DwModeOf<OpCharFwd<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D, int d> struct DwModeOf<OpFused<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 
+// Conversion form (fdbb_dw.cuh) of the packed double-word ops: the clamped
+// sequences, except for the fused pass, whose 45 outputs hold its kernel at
+// the 128-register bound of two blocks per SM and which is faster with the
+// selects.  A/B at N = 2^26 on one GB300, clamp / select (fraction of the
+// measured HBM bandwidth): EOS 0.82 / 0.69, Riemann invariants 0.75 / 0.67,
+// one flux column 0.91 / 0.81, forward characteristic transform 0.83 / 0.73,
+// flux VJP 0.78 / 0.69, temperature 0.77 / 0.70, cons -> prim 0.91 / 0.89,
+// the rest within 0.03; the fused pass 13.47 / 13.55 Gpoints/s (13.28 /
+// 13.38 on a second box).
+template <class Op> struct DwConvOf { static constexpr DwConv value = DwConv::kClamp; };
+template <int D, int d> struct DwConvOf<OpFused<D, d>> { static constexpr DwConv value = DwConv::kSelect; };
+
 // The float-arithmetic ideal-gas blocks (FP32, FP16, BF16 storage) evaluate a
 // thread's four points as two packed FP32x2 pairs (fl2): the same registers,
 // about half the FP32 instructions.  A/B at N = 2^26 on one GB300 (fraction of
@@ -844,7 +859,8 @@ template <class Op, class T, class R, class Mdl> struct OpWidth {
 
 // A source of two points per plane presented as one packed value: its storage
 // word is the pair of doubles.
-template <class Src> struct PairSrc {
+template <class Src, DwConv C = DwConv::kClamp> struct PairSrc {
+  static constexpr DwConv kConv = C;
   const Src& s;
   __device__ __forceinline__ void raw(int k, double2 (&r)[1], float fill) const {
     double t[2];
@@ -856,6 +872,7 @@ template <class Src> struct PairSrc {
 // Four points per plane presented as two packed float pairs: its storage
 // words are pairs of floats.
 template <class Src> struct QuadSrc {
+  static constexpr DwConv kConv = DwConv::kClamp;
   const Src& s;
   __device__ __forceinline__ void raw(int k, float2 (&r)[2], float fill) const {
     float t[4];
@@ -875,7 +892,7 @@ __device__ __forceinline__ void apply_chunk(const KArgs& a, const K& k, const Sr
   } else if constexpr (OpWidth<Op, T, R, Mdl>::kPacked) {
     // packed double-word fast path (cnt points, 1 or 2); a pair with a value
     // outside its range runs in native FP64
-    const PairSrc<Src> ps{src};
+    const PairSrc<Src, DwConvOf<Op>::value> ps{src};
     if (!Op::template apply<T, 1, dw2>(a, splat_consts(k), ps, i0, cnt))
       Op::template apply<T, VW, double>(a, Mdl::template make<double>(a), src, i0, cnt);
   } else if constexpr (std::is_same<R, dw>::value) {
@@ -982,13 +999,28 @@ __global__ void __launch_bounds__(kThreads) k_staged(const __grid_constant__ KAr
 
 // The general-EOS double-word kernels, compiled for three resident blocks per
 // SM (at most 85 registers per thread; left to itself the compiler takes 90
-// and two blocks fit).  The ideal-gas double-word fused pass already fits
-// three blocks and runs 1.2% slower under the bound, so it keeps k_staged.
+// and two blocks fit).
 template <class Op, class T, class R, class Mdl>
 __global__ void __launch_bounds__(kThreads, 3) k_staged3(const __grid_constant__ KArgs a) {
   staged_body<Op, T, R, Mdl>(a);
 }
 template <class R, class Mdl> constexpr bool kStaged3 = std::is_same<R, dw>::value && !std::is_same<Mdl, IdealModel>::value;
+
+// The ideal-gas double-word fused pass, compiled for two resident blocks per
+// SM (at most 128 registers per thread; left to itself the compiler may take
+// more, and then one block fits).
+template <class Op, class T, class R, class Mdl>
+__global__ void __launch_bounds__(kThreads, 2) k_staged2(const __grid_constant__ KArgs a) {
+  staged_body<Op, T, R, Mdl>(a);
+}
+template <class Op> struct IsFusedOp : std::false_type {};
+template <int D, int d> struct IsFusedOp<OpFused<D, d>> : std::true_type {};
+#ifndef FDBB_NO_STAGED2
+template <class Op, class R, class Mdl>
+constexpr bool kStaged2 = IsFusedOp<Op>::value && std::is_same<R, dw>::value && std::is_same<Mdl, IdealModel>::value;
+#else
+template <class Op, class R, class Mdl> constexpr bool kStaged2 = false;
+#endif
 
 // Host: read and clear the timeout count of this translation unit.
 inline unsigned int take_wait_timeouts_tu() {
@@ -1048,6 +1080,8 @@ template <class Op, class T, class R, class Mdl> cudaError_t launch_staged(const
   auto kern = [] {
     if constexpr (kStaged3<R, Mdl>)
       return k_staged3<Op, T, R, Mdl>;
+    else if constexpr (kStaged2<Op, R, Mdl>)
+      return k_staged2<Op, T, R, Mdl>;
     else
       return k_staged<Op, T, R, Mdl>;
   }();

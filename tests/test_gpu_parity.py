@@ -331,6 +331,42 @@ def test_dw_copies_are_bit_exact():
     assert torch.equal(Vo[0], Ud[0])
 
 
+def test_dw_rebuild_across_a_power_of_two():
+    """A double-word result hi + lo whose hi is a power of two and whose lo
+    has the opposite sign lies in the binade below hi, where a double's unit
+    in the last place is half as large; the rebuilt double must still be
+    hi + lo.  Primitive-form flux at rho = u = 1, p = 1 - 2^-26:
+    F_x[1] = rho u^2 + p = 2 - 2^-26 (hi = 2, lo = -2^-26); at rho = 2,
+    u = 1, v = -(1 - 2^-27): F_x[2] = rho u v = -2 + 2^-26 (hi = -2,
+    lo = 2^-26).  Both are doubles and come out of the double-word arithmetic
+    without rounding, so the result is exact to far below the 2^-27 that a
+    rebuild in the wrong binade would be off by.  The fused pass on the
+    conservative form of the first state, at a size where the staged kernel
+    runs, takes the same step against the oracle."""
+    n = 4099
+    V = [np.ones(n), np.ones(n), np.zeros(n), np.zeros(n), np.full(n, 1 - 2.0 ** -26)]
+    V[0][1::2] = 2.0
+    V[2][1::2] = -(1 - 2.0 ** -27)
+    V[4][1::2] = 1.0
+    Vd, _ = quantise(V, torch.float64)
+    for dw in (True, False):
+        F = host(blocks.flux_prim(Vd, 0, G, dw=dw))
+        assert np.all(np.abs(F[1][0::2] - (2 - 2.0 ** -26)) <= 2.0 ** -40), dw
+        assert np.all(np.abs(F[2][1::2] - (-2 + 2.0 ** -26)) <= 2.0 ** -40), dw
+    m = staged_n(512, 7)
+    U1 = oracle.cons_from_prim(3, G, [np.array([v[0]]) for v in V])
+    U = [np.full(m, u[0]) for u in U1]
+    W = synth.char_weights(m, 5, seed=3)
+    Ud, _ = quantise(U, torch.float64)
+    Wd, _ = quantise(W, torch.float64)
+    F, A, Y = blocks.euler_fused(Ud, Wd, 0, G, dw=True)
+    assert_staged()
+    ref, S = oracle.euler_fused(3, 0, G, U, W, scale=True)
+    got = host([*F, *A, *Y])
+    assert abs(ref[1][0] - 2.0) < 2.0 ** -24 and ref[1][0] < 2.0  # the case this test is about
+    check(got, ref, S, torch.float64, "fused at a power of two")
+
+
 # ---------------------------------------------------------------------------
 # full size, in the benchmark's launch configuration
 # ---------------------------------------------------------------------------
