@@ -791,7 +791,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
 // operation's FP32 steps, in the same order and with the same roundings, so a
 // point's result does not depend on its partner.  The choice per block is the
 // faster one of an A/B at N = 2^26 on one GB300 (fraction of the measured HBM
-// bandwidth, one point / two points / two points packed):
+// bandwidth).  With the select form of the conversions (DwConvOf), one point
+// / two points / two points packed:
 //   v_mag2 0.79 / 0.94 / 0.98, EOS 0.62 / 0.68 / 0.69, cons -> prim
 //   0.77 / 0.87 / 0.89, prim -> cons 0.91 / 0.91 / 0.89, Riemann invariants
 //   0.60 / 0.64 / 0.67, one flux column 0.73 / 0.81 / 0.77, all columns
@@ -799,19 +800,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
 //   0.60 / 0.70 / 0.69, all primitive-form columns 0.83 / 0.81 / 0.85,
 //   forward characteristic transform 0.66 / - / 0.73, inverse 0.61 / - /
 //   0.55, flux VJP - / 0.60 / 0.69; the fused pass 13.35 / - / 13.58
-//   Gpoints/s.  The Roe-averaged forms need 160-230 registers packed and keep
-//   one point.
+//   Gpoints/s.  With the clamped form, the kept mode against the other
+//   candidate: EOS packed 0.82 / two points 0.74, Riemann invariants packed
+//   0.75 / two points 0.68, one flux column two points 0.91 / packed 0.89,
+//   prim -> cons two points 0.90 / packed 0.90, temperature packed 0.83 /
+//   two points 0.77, inverse characteristic transform packed 0.74 / one point
+//   0.65.  The Roe-averaged forms need 160-230 registers packed and keep one
+//   point.
 enum class DwMode { Single, Pairs, Packed };
 template <class Op> struct DwModeOf { static constexpr DwMode value = DwMode::Single; };
 template <int D> struct DwModeOf<OpVMag2<D>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D> struct DwModeOf<OpEos<D>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D> struct DwModeOf<OpPrim<D>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D> struct DwModeOf<OpCons<D>> { static constexpr DwMode value = DwMode::Pairs; };
-template <int D> struct DwModeOf<OpTemp<D>> { static constexpr DwMode value = DwMode::Pairs; };
+template <int D> struct DwModeOf<OpTemp<D>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D, int d> struct DwModeOf<OpRiemann<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D, int d> struct DwModeOf<OpFlux<D, d>> {
   static constexpr DwMode value = d < 0 ? DwMode::Packed : DwMode::Pairs;
 };
+template <int D, int d> struct DwModeOf<OpCharInv<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D, int d> struct DwModeOf<OpFluxPrim<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D, int d> struct DwModeOf<OpJac<D, d>> { static constexpr DwMode value = DwMode::Packed; };
 template <int D, int d> struct DwModeOf<OpJacPrim<D, d>> { static constexpr DwMode value = DwMode::Packed; };

@@ -501,6 +501,8 @@ def test_packed_blocks_lanes_are_independent(staged):
         "flux_all": lambda U_, W_: blocks.flux(U_, -1, G, dw=True),
         "jac": lambda U_, W_: blocks.flux_jac(U_, 0, G, dw=True),
         "char_fwd": lambda U_, W_: blocks.char_transform(U_, W_, 1, G, dw=True),
+        "char_inv": lambda U_, W_: blocks.char_transform(U_, W_, 2, G, inverse=True, dw=True),
+        "temperature": lambda U_, W_: [blocks.temperature(U_, 2.5, G, dw=True)],
         "vjp": lambda U_, W_: blocks.flux_vjp(U_, W_, 2, G, dw=True),
     }
     for name, fn in calls.items():
