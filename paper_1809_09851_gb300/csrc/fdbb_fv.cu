@@ -144,16 +144,15 @@ __device__ __forceinline__ void fv_derive(Pt<double, 3>& s, const Consts<double>
   NoGuard g;
   derive(s, k, g);
 }
+// FP32 grids: 1/rho, p = (gamma - 1) (rhoE - |m|^2 / (2 rho)) and c^2 in the
+// packed step kernel's sequence for one lane (derive2), so that the wave-speed
+// maximum reduced from a state here and the one the step kernel reduces agree
+// bit for bit.
 __device__ __forceinline__ void fv_derive(Pt<float, 3>& s, const Consts<float>& k) {
   s.r = fv_rcp(s.rho);
-  s.v[0] = s.m[0] * s.r;
-  s.v[1] = s.m[1] * s.r;
-  s.v[2] = s.m[2] * s.r;
-  s.rq = 0.5f * fmaf(s.m[2], s.v[2], fmaf(s.m[1], s.v[1], s.m[0] * s.v[0]));
-  s.q = s.rq * s.r;
-  s.p = k.a1 * (s.rE - s.rq);
-  s.H = (s.rE + s.p) * s.r;
-  s.c2 = k.g * s.p * s.r;
+  const float m2 = fmaf(s.m[2], s.m[2], fmaf(s.m[1], s.m[1], __fmul_rn(s.m[0], s.m[0])));
+  s.p = __fmul_rn(k.a1, __fsub_rn(s.rE, __fmul_rn(0.5f, __fmul_rn(m2, s.r))));
+  s.c2 = __fmul_rn(__fmul_rn(k.g, s.p), s.r);
 }
 
 // Derived state of the cell at linear index c of the planes P.
@@ -170,6 +169,11 @@ __device__ __forceinline__ void cell_state(void* const* P, int64_t c, const Cons
 template <class T> __device__ __forceinline__ T wave_speed_sum(const Pt<T, 3>& s) {
   const T c = fv_sqrt(s.c2);
   return (abs_(s.v[0]) + c) + (abs_(s.v[1]) + c) + (abs_(s.v[2]) + c);
+}
+// FP32: the sum as the packed step kernel forms it, (|m_x| + |m_y| + |m_z|) / rho + 3 c
+__device__ __forceinline__ float wave_speed_sum(const Pt<float, 3>& s) {
+  const float c = fv_sqrt(s.c2);
+  return fmaf(__fadd_rn(__fadd_rn(fabsf(s.m[0]), fabsf(s.m[1])), fabsf(s.m[2])), s.r, __fmul_rn(3.0f, c));
 }
 
 template <class T> __global__ void __launch_bounds__(kFvThreads) k_fv_max_speed(const __grid_constant__ FvArgs a) {
@@ -465,9 +469,9 @@ __device__ __forceinline__ Cell2 derive2(const f2 (&u)[5], const Consts2& k) {
 #pragma unroll
   for (int q = 0; q < 5; ++q) e.u[q] = u[q];
   e.r = pk(fv_rcp(u[0].v.x), fv_rcp(u[0].v.y));
-  const f2 v0 = u[1] * e.r, v1 = u[2] * e.r, v2 = u[3] * e.r;
-  const f2 rq = k.half * fma2(u[3], v2, fma2(u[2], v1, u[1] * v0));
-  e.p = k.a1 * (u[4] - rq);
+  // p = (gamma - 1) (rhoE - |m|^2 / (2 rho))
+  const f2 m2 = fma2(u[3], u[3], fma2(u[2], u[2], u[1] * u[1]));
+  e.p = k.a1 * (u[4] - k.half * (m2 * e.r));
   const f2 c2 = k.g * e.p * e.r;
   e.c = pk(fv_sqrt(c2.v.x), fv_sqrt(c2.v.y));
   return e;
@@ -503,12 +507,10 @@ template <int d> __device__ __forceinline__ Side2 side2(const Cell2& e) {
 #pragma unroll
   for (int q = 0; q < 5; ++q) x.u[q] = e.u[q];
   x.f[0] = md;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const f2 vi = e.u[1 + i] * e.r;
-    x.f[1 + i] = i == d ? fma2(md, vi, e.p) : md * vi;
-  }
+  // m_i v_d for every momentum component, the pressure added to the normal one
   const f2 vd = md * e.r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x.f[1 + i] = i == d ? fma2(md, vd, e.p) : e.u[1 + i] * vd;
   x.f[4] = vd * (e.u[4] + e.p);
   x.s = abs2(vd) + e.c;
   return x;
@@ -661,7 +663,8 @@ __global__ void __launch_bounds__(kFvThreads, 2) k_fv_rusanov_step2(const __grid
           if (two) st_in<float>(a.dbg, g.Unew[q], c + plane, plane * n, un[q].v.y);
         }
         const Cell2 nw = derive2(un, k);
-        const f2 vs = abs2(un[1] * nw.r) + nw.c + (abs2(un[2] * nw.r) + nw.c) + (abs2(un[3] * nw.r) + nw.c);
+        // sum over d of |v_d| + c as (|m_x| + |m_y| + |m_z|) / rho + 3 c
+        const f2 vs = fma2(abs2(un[1]) + abs2(un[2]) + abs2(un[3]), nw.r, splat(3.0f) * nw.c);
         vmax = vs.v.x > vmax ? vs.v.x : vmax;
         if (two) vmax = vs.v.y > vmax ? vs.v.y : vmax;
       }
