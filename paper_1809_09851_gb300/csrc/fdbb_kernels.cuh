@@ -1022,12 +1022,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_staged2(const __grid_constant__
 }
 template <class Op> struct IsFusedOp : std::false_type {};
 template <int D, int d> struct IsFusedOp<OpFused<D, d>> : std::true_type {};
-#ifndef FDBB_NO_STAGED2
 template <class Op, class R, class Mdl>
 constexpr bool kStaged2 = IsFusedOp<Op>::value && std::is_same<R, dw>::value && std::is_same<Mdl, IdealModel>::value;
-#else
-template <class Op, class R, class Mdl> constexpr bool kStaged2 = false;
-#endif
 
 // Host: read and clear the timeout count of this translation unit.
 inline unsigned int take_wait_timeouts_tu() {
