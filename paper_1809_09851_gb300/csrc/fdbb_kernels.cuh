@@ -217,10 +217,10 @@ __device__ __forceinline__ void store_field(const KArgs& a, const Src& src, int 
   }
 }
 
-template <int VW, int D, bool C2 = true, class R, class K, class G>
+template <int VW, int D, bool C2 = true, bool HQ = true, class R, class K, class G>
 __device__ __forceinline__ void derive_all(Pt<R, D> (&s)[VW], const K& k, G& g) {
 #pragma unroll
-  for (int j = 0; j < VW; ++j) derive<C2>(s[j], k, g);
+  for (int j = 0; j < VW; ++j) derive<C2, HQ>(s[j], k, g);
 }
 
 // Flux column d into output planes base..base+nv-1.  Component 0 is the input
@@ -379,7 +379,7 @@ template <int D> struct OpEos {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
-    derive_all<VW, D>(s, k, g);
+    derive_all<VW, D, true, false>(s, k, g);
     if (!g.ok) return false;
     R x[VW];
     if (T* o = outp<T>(a, 0)) {
@@ -405,7 +405,7 @@ template <int D, int d> struct OpRiemann {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
-    derive_all<VW, D>(s, k, g);
+    derive_all<VW, D, true, false>(s, k, g);
     if (!g.ok) return false;
     R wm[VW], wp[VW];
 #pragma unroll
@@ -434,7 +434,7 @@ template <int D, int d> struct OpFlux {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
-    derive_all<VW, D, false>(s, k, g);
+    derive_all<VW, D, false, false>(s, k, g);
     if (!g.ok) return false;
     if constexpr (d >= 0) {
       emit_flux<T, VW, D, d>(a, src, 0, i0, cnt, s);
@@ -713,7 +713,7 @@ template <int D> struct OpTemp {
     typename GuardOf<R>::type g;
     Pt<R, D> s[VW];
     load_U<T, VW, D>(src, 0, s, g);
-    derive_all<VW, D, false>(s, k, g);
+    derive_all<VW, D, false, false>(s, k, g);
     if (!g.ok) return false;
     R x[VW];
 #pragma unroll
