@@ -516,15 +516,18 @@ __device__ __forceinline__ void internal_energy(Pt<fl2, D>& s, fl2& rhoe) {
 // and phi = dp/drho|_e + Gamma (q - e).
 // C2 = false skips c^2 (and its range check) for blocks that never read it:
 // fluxes, Jacobians, the flux VJP, the Roe forms (which average their own).
-// HQ = false skips H and q (and their checks) for blocks that read neither:
-// EOS, Riemann invariants, the flux columns and the temperature (a general
-// EOS still forms q, for phi).  In double-word arithmetic at N = 2^26 on one
-// GB300 (fraction of the measured HBM bandwidth, with / without): EOS
-// 0.91 / 0.82, Riemann invariants 0.82 / 0.75, temperature 0.93 / 0.83, one
-// flux column 0.94 / 0.91; cons -> prim 0.90 / 0.91 keeps them.
-template <bool C2 = true, bool HQ = true, class R, int D, class K, class G>
+// WH = false skips H and WQ = false skips q (each with its check) for blocks
+// that do not read them: neither for EOS, Riemann invariants, the flux
+// columns and the temperature; H for the forward characteristic transform;
+// q for the two states of the Roe forms (a general EOS still forms q, for
+// phi).  In double-word arithmetic at N = 2^26 on one GB300 (fraction of the
+// measured HBM bandwidth, with / without the skips): EOS 0.91 / 0.82,
+// Riemann invariants 0.82 / 0.75, temperature 0.93 / 0.83, one flux column
+// 0.94 / 0.91, forward characteristic transform 0.88 / 0.84, Roe flux
+// 0.32 / 0.32; cons -> prim 0.90 / 0.91 keeps them.
+template <bool C2 = true, bool WH = true, bool WQ = WH, class R, int D, class K, class G>
 __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
-  constexpr bool kQ = HQ || !K::kIdeal;
+  constexpr bool kQ = WQ || !K::kIdeal;
   s.r = rcp_(s.rho);
 #pragma unroll
   for (int i = 0; i < D; ++i) s.v[i] = s.m[i] * s.r;
@@ -533,14 +536,14 @@ __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
   if constexpr (kQ) s.q = s.rq * s.r;
   if constexpr (K::kIdeal) {
     s.p = k.a1 * rhoe;
-    if constexpr (HQ) s.H = (s.rE + s.p) * s.r;
+    if constexpr (WH) s.H = (s.rE + s.p) * s.r;
     if constexpr (C2) s.c2 = k.g * s.p * s.r;
   } else {
     s.ie = rhoe * s.r;
     const D2<R> P = tangents(k.p_rhoe(arg1(s.rho), arg2(s.ie)));
     s.p = P.v;
     s.G = P.de * s.r;
-    if constexpr (HQ) s.H = (s.rE + s.p) * s.r;
+    if constexpr (WH) s.H = (s.rE + s.p) * s.r;
     if constexpr (C2) s.c2 = fma_(s.G * s.p, s.r, P.dr);
     s.ph = fma_(s.G, s.q - s.ie, P.dr);
     g.check(s.ie);
@@ -551,7 +554,7 @@ __device__ __forceinline__ void derive(Pt<R, D>& s, const K& k, G& g) {
   for (int i = 0; i < D; ++i) g.check(s.v[i]);
   if constexpr (kQ) g.check(s.q);
   g.check(s.p);
-  if constexpr (HQ) g.check(s.H);
+  if constexpr (WH) g.check(s.H);
   if constexpr (C2) g.check(s.c2);
 }
 

@@ -217,10 +217,10 @@ __device__ __forceinline__ void store_field(const KArgs& a, const Src& src, int 
   }
 }
 
-template <int VW, int D, bool C2 = true, bool HQ = true, class R, class K, class G>
+template <int VW, int D, bool C2 = true, bool WH = true, bool WQ = WH, class R, class K, class G>
 __device__ __forceinline__ void derive_all(Pt<R, D> (&s)[VW], const K& k, G& g) {
 #pragma unroll
-  for (int j = 0; j < VW; ++j) derive<C2, HQ>(s[j], k, g);
+  for (int j = 0; j < VW; ++j) derive<C2, WH, WQ>(s[j], k, g);
 }
 
 // Flux column d into output planes base..base+nv-1.  Component 0 is the input
@@ -481,7 +481,7 @@ template <int D, int d, bool INV> struct OpChar {
       for (int j = 0; j < VW; ++j) char_inv_sums<D, d>(s[j], k, w[j], sum[j], anm1[j], a1pn[j], y[j]);
     } else {
       load_field<T, VW, nv>(src, nv, w, g);
-      derive_all<VW, D>(s, k, g);
+      derive_all<VW, D, true, false, true>(s, k, g);
       if (!g.ok) return false;
 #pragma unroll
       for (int j = 0; j < VW; ++j) char_fwd<D, d>(s[j], k, w[j], y[j]);
@@ -555,8 +555,8 @@ template <int D, int d> struct OpRoeFlux {
     Pt<R, D> L[VW], Rt[VW], s[VW];
     load_U<T, VW, D>(src, 0, L, g);
     load_U<T, VW, D>(src, nv, Rt, g);
-    derive_all<VW, D, false>(L, k, g);
-    derive_all<VW, D, false>(Rt, k, g);
+    derive_all<VW, D, false, true, false>(L, k, g);
+    derive_all<VW, D, false, true, false>(Rt, k, g);
 #pragma unroll
     for (int j = 0; j < VW; ++j) roe_state(L[j], Rt[j], k, s[j], g);
     if (!g.ok) return false;
@@ -586,8 +586,8 @@ template <int D, int d, bool INV> struct OpRoeChar {
       load_weights_inv<T, VW, nv>(src, 2 * nv, w, sum, anm1, a1pn, g);
     else
       load_field<T, VW, nv>(src, 2 * nv, w, g);
-    derive_all<VW, D, false>(L, k, g);
-    derive_all<VW, D, false>(Rt, k, g);
+    derive_all<VW, D, false, true, false>(L, k, g);
+    derive_all<VW, D, false, true, false>(Rt, k, g);
 #pragma unroll
     for (int j = 0; j < VW; ++j) roe_state(L[j], Rt[j], k, s[j], g);
     if (!g.ok) return false;
