@@ -56,14 +56,24 @@ FUSED_KERNEL_SOURCES = ("fdbb_device.cuh", "fdbb_dw.cuh", "fdbb_eos.cuh", "fdbb_
                         "kern_f64dw3.cu")
 
 
-def kernel_source_hash() -> str:
-    """Hash of the sources that define the headline (fused, double-word) kernel."""
+def kernel_source_hash(root: str = None) -> str:
+    """Hash of the sources that define the headline (fused, double-word) kernel
+    (under `root`, default this checkout)."""
     h = hashlib.sha256()
-    for p in sorted(os.path.join(ROOT, "paper_1809_09851_gb300", "csrc", f) for f in FUSED_KERNEL_SOURCES):
+    for p in sorted(os.path.join(root or ROOT, "paper_1809_09851_gb300", "csrc", f) for f in FUSED_KERNEL_SOURCES):
         with open(p, "rb") as fh:
             h.update(os.path.basename(p).encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def recorded_traffic(n: int, root: str = None):
+    """DRAM bytes of one headline launch over n points from the recorded ncu
+    capture, or None when the kernel sources are no longer the ones it was
+    taken on."""
+    if not NCU_TRAFFIC["bytes_per_point"] or NCU_TRAFFIC["source_hash"] != kernel_source_hash(root):
+        return None
+    return round(NCU_TRAFFIC["bytes_per_point"] * n)
 
 
 def measured_peaks():
@@ -589,9 +599,7 @@ def run_gpu(args):
     value = job_points * args.steps / t_max / 1e9
     avg_h = sum(per_h) / len(per_h) / 1e3
     achieved = bytes64 / avg_h / 1e9
-    traffic = None
-    if NCU_TRAFFIC["source_hash"] == kernel_source_hash() and NCU_TRAFFIC["bytes_per_point"]:
-        traffic = round(NCU_TRAFFIC["bytes_per_point"] * n)
+    traffic = recorded_traffic(n)
 
     # ---- FP64 storage, IEEE double arithmetic ----------------------------------
     f64_native = None
